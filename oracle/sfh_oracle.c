@@ -1,0 +1,662 @@
+/*
+ * sfh_oracle.c -- plain FP64 CPU oracle for the sum-factorized Hadamard-product
+ * volume term of entropy-conserving flux differencing
+ * (Cicchino & Nadarajah, "Scalable evaluation of Hadamard products with tensor
+ * product basis for entropy-stable high-order methods", arXiv 2306.11665).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  It shares no code,
+ * header, table or constant with the CUDA library: it computes its own nodes,
+ * its own derivative matrix, its own fluxes and its own metric terms.
+ *
+ * Everything here is written for readability, not speed: each function
+ * follows one definition and loops over indices the way the definition reads.
+ *
+ * Conventions (Section 2, the three-dimensional listing):
+ *   n = p + 1 nodes per direction; element node i <-> (a_0, .., a_{d-1}) with
+ *   a_0 (x) running fastest: i = a_0 + n a_1 + n^2 a_2.
+ *   u  [e][var][i]       conservative state (Burgers: 1 var; Euler: d + 2 vars)
+ *   Ja [e][m][k][i]      J dxi_m/dx_k at node i
+ *   r  [e][var][i]       r_i = sum_m sum_j (Q_m o F_m)_ij
+ *   Q_m = (tensor product over axes k of A_k), A_m = W D, A_k = W for k != m
+ *         (Eq. 5; the factor position names the direction, x runs fastest)
+ *   F_m(u_i, u_j) = sum_k fsharp_k(u_i, u_j) (Ja^m_k(i) + Ja^m_k(j))
+ *
+ * Readings where the paper is silent (the paper gives no flux formulas):
+ *   - Burgers: fsharp_k(a, b) = (a^2 + a b + b^2) / 6 in every direction k.
+ *   - Euler: Ranocha's entropy-conserving, kinetic-energy-preserving flux with
+ *     gamma = 1.4, logarithmic means with the near-equal series of Ranocha,
+ *     Schlottke-Lakemper, Winters, Faulhaber, Chan, Gassner (2021) (threshold
+ *     1e-4 on ((a-b)/(a+b))^2).
+ *
+ * Return codes: 0 = ok, 1 = bad argument, 2 = non-positive density or
+ * pressure met (the output is still filled).
+ *
+ * Parity status: every exported function is pinned by the CPU tests
+ * (dense brute force, textbook nodes, SBP identities, Burgers closed form,
+ * free stream, entropy identity, conservation, pressure equilibrium, finite
+ * differences).  No function here is "parity unpinned".
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_GAMMA 1.4
+#define ORC_FLUX_BURGERS 0
+#define ORC_FLUX_EULER 1
+#define ORC_NODES_GLL 0
+#define ORC_NODES_GAUSS 1
+
+/* ------------------------------------------------------------------------ */
+/* 1D collocated Lagrange basis on Gauss-Lobatto or Gauss-Legendre nodes.     */
+/* Eq. 4-5 need the collocated nodal basis; these are the node sets the     */
+/* paper's results use (Gauss-Legendre in Section 3).                       */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre P_k(x), P_k'(x), P_k''(x) for k = q by the three-term recurrence
+ * (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}, and its derivative forms
+ * P'_{k+1} = P'_{k-1} + (2k+1) P_k,  P''_{k+1} = P''_{k-1} + (2k+1) P'_k. */
+static void legendre_eval(int q, long double x, long double *P, long double *dP,
+                          long double *d2P)
+{
+    long double p0 = 1.0L, p1 = x;       /* P_0, P_1 */
+    long double dp0 = 0.0L, dp1 = 1.0L;  /* P_0', P_1' */
+    long double ddp0 = 0.0L, ddp1 = 0.0L;
+    if (q == 0) { *P = 1.0L; *dP = 0.0L; *d2P = 0.0L; return; }
+    for (int k = 1; k < q; ++k) {
+        long double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+        long double dp2 = dp0 + (2 * k + 1) * p1;
+        long double ddp2 = ddp0 + (2 * k + 1) * dp1;
+        p0 = p1; p1 = p2; dp0 = dp1; dp1 = dp2; ddp0 = ddp1; ddp1 = ddp2;
+    }
+    *P = p1; *dP = dp1; *d2P = ddp1;
+}
+
+/* Nodes xi[0..p] (ascending) and weights w[0..p] on [-1, 1].
+ *   Gauss-Lobatto (kind 0): xi = -1, roots of P_p', +1; w = 2 / (p (p+1) P_p(xi)^2).
+ *   Gauss-Legendre (kind 1): roots of P_{p+1}; w = 2 / ((1 - xi^2) P'_{p+1}(xi)^2).
+ * Newton iteration in long double from Chebyshev-like first guesses. */
+int orc_nodes(int p, int kind, double *xi, double *w)
+{
+    int n = p + 1;
+    if (p < 1 || p > 30 || (kind != ORC_NODES_GLL && kind != ORC_NODES_GAUSS)) return 1;
+    if (kind == ORC_NODES_GAUSS) {
+        for (int j = 0; j < n; ++j) {
+            long double x = -cosl(3.14159265358979323846264338327950288L * (j + 0.75L) / (n + 0.5L));
+            for (int it = 0; it < 100; ++it) {
+                long double P, dP, d2P;
+                legendre_eval(n, x, &P, &dP, &d2P);
+                long double dx = P / dP;
+                x -= dx;
+                if (fabsl(dx) < 1e-19L) break;
+            }
+            long double P, dP, d2P;
+            legendre_eval(n, x, &P, &dP, &d2P);
+            xi[j] = (double)x;
+            w[j] = (double)(2.0L / ((1.0L - x * x) * dP * dP));
+        }
+    } else {
+        xi[0] = -1.0; xi[p] = 1.0;
+        for (int j = 1; j < p; ++j) {
+            long double x = -cosl(3.14159265358979323846264338327950288L * j / p);
+            for (int it = 0; it < 100; ++it) {
+                long double P, dP, d2P;
+                legendre_eval(p, x, &P, &dP, &d2P);
+                long double dx = dP / d2P;
+                x -= dx;
+                if (fabsl(dx) < 1e-19L) break;
+            }
+            xi[j] = (double)x;
+        }
+        for (int j = 0; j < n; ++j) {
+            long double P, dP, d2P;
+            legendre_eval(p, (long double)xi[j], &P, &dP, &d2P);
+            w[j] = (double)(2.0L / ((long double)p * (p + 1) * P * P));
+        }
+    }
+    return 0;
+}
+
+/* Collocation derivative D[i*n + j] = l_j'(xi_i) by the barycentric formula
+ * (Berrut & Trefethen 2004): lambda_j = 1 / prod_{k != j} (xi_j - xi_k),
+ * D_ij = (lambda_j / lambda_i) / (xi_i - xi_j) for i != j,
+ * D_ii = -sum_{j != i} D_ij (negative-sum trick: rows sum to zero). */
+void orc_dmat(int n, const double *xi, double *D)
+{
+    long double lam[64];
+    for (int j = 0; j < n; ++j) {
+        long double prod = 1.0L;
+        for (int k = 0; k < n; ++k)
+            if (k != j) prod *= ((long double)xi[j] - xi[k]);
+        lam[j] = 1.0L / prod;
+    }
+    for (int i = 0; i < n; ++i) {
+        long double diag = 0.0L;
+        for (int j = 0; j < n; ++j) {
+            if (j == i) continue;
+            long double dij = (lam[j] / lam[i]) / ((long double)xi[i] - xi[j]);
+            D[i * n + j] = (double)dij;
+            diag -= dij;
+        }
+        D[i * n + i] = (double)diag;
+    }
+}
+
+/* The 1D operators one direction of Eq. 5 needs: nodes, weights, D and the
+ * weighted derivative Q1 = diag(w) D (the "stiffness" factor). */
+int orc_op1d(int p, int kind, double *xi, double *w, double *D, double *Q1)
+{
+    int n = p + 1;
+    if (orc_nodes(p, kind, xi, w)) return 1;
+    orc_dmat(n, xi, D);
+    for (int a = 0; a < n; ++a)
+        for (int b = 0; b < n; ++b)
+            Q1[a * n + b] = w[a] * D[a * n + b];
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Tensor-product index helpers (x fastest).                                  */
+/* ------------------------------------------------------------------------ */
+static int ipow(int b, int e) { int r = 1; while (e-- > 0) r *= b; return r; }
+
+static void node_to_multi(int i, int n, int d, int *a)
+{
+    for (int k = 0; k < d; ++k) { a[k] = i % n; i /= n; }
+}
+
+static int multi_to_node(const int *a, int n, int d)
+{
+    int i = 0;
+    for (int k = d - 1; k >= 0; --k) i = i * n + a[k];
+    return i;
+}
+
+/* Dense Q_m (n^d x n^d, row-major) by the Kronecker-product definition:
+ * Q_m[i][j] = prod_k A_k[a_k(i)][a_k(j)], A_m = Q1, A_k = diag(w) (k != m).
+ * This is the full operator of Eq. 5 whose Hadamard product Eq. 1 evaluates. */
+int orc_qmat_dense(int d, int p, int kind, int m, double *Q)
+{
+    int n = p + 1, nn = ipow(n, d);
+    double xi[64], w[64], D[64 * 64], Q1[64 * 64];
+    if (d < 1 || d > 3 || m < 0 || m >= d) return 1;
+    if (orc_op1d(p, kind, xi, w, D, Q1)) return 1;
+    for (int i = 0; i < nn; ++i) {
+        int ai[3]; node_to_multi(i, n, d, ai);
+        for (int j = 0; j < nn; ++j) {
+            int aj[3]; node_to_multi(j, n, d, aj);
+            double v = 1.0;
+            for (int k = 0; k < d; ++k) {
+                if (k == m) v *= Q1[ai[k] * n + aj[k]];
+                else v *= (ai[k] == aj[k]) ? w[ai[k]] : 0.0;
+            }
+            Q[(long)i * nn + j] = v;
+        }
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Logarithmic mean {a, b}_ln = (a - b) / (ln a - ln b), {a, a}_ln = a.       */
+/* Near a = b: series in u = ((a - b)/(a + b))^2,                           */
+/* {a,b}_ln = (a + b) / (2 + 2u/3 + 2u^2/5 + 2u^3/7)  (Ranocha et al. 2021). */
+/* ------------------------------------------------------------------------ */
+double orc_logmean(double a, double b)
+{
+    double d = a - b, s = a + b;
+    double u = (d * d) / (s * s);
+    if (u < 1e-4)
+        return s / (2.0 + u * (2.0 / 3.0 + u * (2.0 / 5.0 + u * (2.0 / 7.0))));
+    return d / log(a / b);
+}
+
+/* Partial derivatives of {a, b}_ln.
+ * Away from a = b: d/da = (1 - L/a) / ln(a/b).
+ * Near a = b: L = s / P(u), P(u) = 2 sum_k u^k / (2k+1) (seven terms here),
+ * u = t^2, t = (a-b)/(a+b); du/da = 4 t b / s^2, du/db = -4 t a / s^2, so
+ * dL/da = 1/P - s P'(u) du/da / P^2. */
+void orc_logmean_grad(double a, double b, double *dLda, double *dLdb)
+{
+    double d = a - b, s = a + b;
+    double u = (d * d) / (s * s);
+    if (u < 1e-4) {
+        double t = d / s, P = 0.0, dP = 0.0;
+        for (int k = 6; k >= 0; --k) P = P * u + 2.0 / (2 * k + 1);
+        for (int k = 6; k >= 1; --k) dP = dP * u + 2.0 * k / (2 * k + 1);
+        double dudA = 4.0 * t * b / (s * s);
+        double dudB = -4.0 * t * a / (s * s);
+        *dLda = 1.0 / P - s * dP * dudA / (P * P);
+        *dLdb = 1.0 / P - s * dP * dudB / (P * P);
+    } else {
+        double lr = log(a / b);
+        double L = d / lr;
+        *dLda = (1.0 - L / a) / lr;
+        *dLdb = (L / b - 1.0) / lr;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Two-point fluxes contracted with a metric vector nv (d components):       */
+/* F(u_i, u_j; nv) = sum_k fsharp_k(u_i, u_j) nv_k.  The residual passes     */
+/* nv = Ja^m(i) + Ja^m(j) (= 2 avg(J dxi_m/dx)).                            */
+/* ------------------------------------------------------------------------ */
+
+/* Euler primitives from conservative variables; returns 0 if rho, p > 0. */
+static int euler_prim(int d, const double *u, double *rho, double *v, double *p)
+{
+    double ke = 0.0;
+    *rho = u[0];
+    for (int k = 0; k < d; ++k) { v[k] = u[1 + k] / u[0]; ke += u[1 + k] * v[k]; }
+    *p = (ORC_GAMMA - 1.0) * (u[d + 1] - 0.5 * ke);
+    return (*rho > 0.0 && *p > 0.0) ? 0 : 2;
+}
+
+int orc_ec_flux(int d, int flux, const double *ui, const double *uj, const double *nv, double *F)
+{
+    if (flux == ORC_FLUX_BURGERS) {
+        double a = ui[0], b = uj[0], S = 0.0;
+        for (int k = 0; k < d; ++k) S += nv[k];
+        F[0] = (a * a + a * b + b * b) / 6.0 * S;
+        return 0;
+    }
+    double ri, vi[3], pi, rj, vj[3], pj;
+    int st = euler_prim(d, ui, &ri, vi, &pi) | euler_prim(d, uj, &rj, vj, &pj);
+    double rho_ln = orc_logmean(ri, rj);
+    double beta_ln = orc_logmean(ri / pi, rj / pj);
+    double vni = 0.0, vnj = 0.0, vivj = 0.0;
+    for (int k = 0; k < d; ++k) { vni += vi[k] * nv[k]; vnj += vj[k] * nv[k]; vivj += vi[k] * vj[k]; }
+    double f_rho = rho_ln * 0.5 * (vni + vnj);
+    double p_avg = 0.5 * (pi + pj);
+    F[0] = f_rho;
+    for (int l = 0; l < d; ++l) F[1 + l] = f_rho * 0.5 * (vi[l] + vj[l]) + p_avg * nv[l];
+    F[d + 1] = f_rho * (0.5 * vivj + 1.0 / ((ORC_GAMMA - 1.0) * beta_ln)) + 0.5 * (pi * vnj + pj * vni);
+    return st;
+}
+
+/* Jacobian of the contracted two-point flux with respect to the conservative
+ * state of its FIRST argument: J[a*nvar + b] = dF_a / du_i,b.
+ * Chain rule: conservative -> (rho, v, p) -> flux, with the log-mean
+ * derivatives above (beta = rho / p). */
+int orc_ec_flux_jac1(int d, int flux, const double *ui, const double *uj, const double *nv, double *J)
+{
+    if (flux == ORC_FLUX_BURGERS) {
+        double a = ui[0], b = uj[0], S = 0.0;
+        for (int k = 0; k < d; ++k) S += nv[k];
+        J[0] = (2.0 * a + b) / 6.0 * S;
+        return 0;
+    }
+    int nvar = d + 2;
+    double ri, vi[3], pi, rj, vj[3], pj;
+    int st = euler_prim(d, ui, &ri, vi, &pi) | euler_prim(d, uj, &rj, vj, &pj);
+    double bi = ri / pi, bj = rj / pj;
+    double Lr = orc_logmean(ri, rj), Lb = orc_logmean(bi, bj);
+    double dLr, dLr_unused, dLb, dLb_unused;
+    orc_logmean_grad(ri, rj, &dLr, &dLr_unused);
+    orc_logmean_grad(bi, bj, &dLb, &dLb_unused);
+    double vni = 0.0, vnj = 0.0, vivj = 0.0;
+    for (int k = 0; k < d; ++k) { vni += vi[k] * nv[k]; vnj += vj[k] * nv[k]; vivj += vi[k] * vj[k]; }
+    double f_rho = Lr * 0.5 * (vni + vnj);
+    double K = 0.5 * vivj + 1.0 / ((ORC_GAMMA - 1.0) * Lb);
+    double dK_dLb = -1.0 / ((ORC_GAMMA - 1.0) * Lb * Lb);
+
+    /* dF/dw with w = (rho_i, v_i[0..d-1], p_i); dFw[a][c], c in 0..d+1 */
+    double dFw[5][5];
+    memset(dFw, 0, sizeof dFw);
+    double dfrho_drho = dLr * 0.5 * (vni + vnj);
+    double dfrho_dv[3];
+    for (int k = 0; k < d; ++k) dfrho_dv[k] = Lr * 0.5 * nv[k];
+    double dK_drho = dK_dLb * dLb * (1.0 / pi);
+    double dK_dp = dK_dLb * dLb * (-ri / (pi * pi));
+    /* mass */
+    dFw[0][0] = dfrho_drho;
+    for (int k = 0; k < d; ++k) dFw[0][1 + k] = dfrho_dv[k];
+    /* momentum */
+    for (int l = 0; l < d; ++l) {
+        double vavg = 0.5 * (vi[l] + vj[l]);
+        dFw[1 + l][0] = dfrho_drho * vavg;
+        for (int k = 0; k < d; ++k)
+            dFw[1 + l][1 + k] = dfrho_dv[k] * vavg + (k == l ? 0.5 * f_rho : 0.0);
+        dFw[1 + l][d + 1] = 0.5 * nv[l];
+    }
+    /* energy */
+    dFw[d + 1][0] = dfrho_drho * K + f_rho * dK_drho;
+    for (int k = 0; k < d; ++k)
+        dFw[d + 1][1 + k] = dfrho_dv[k] * K + f_rho * 0.5 * vj[k] + 0.5 * pj * nv[k];
+    dFw[d + 1][d + 1] = f_rho * dK_dp + 0.5 * vnj;
+
+    /* dw/du: rho = u0; v_k = u_{1+k}/u0; p = (g-1)(E - |m|^2/(2 rho)) */
+    double dwu[5][5];
+    memset(dwu, 0, sizeof dwu);
+    double v2 = 0.0;
+    for (int k = 0; k < d; ++k) v2 += vi[k] * vi[k];
+    dwu[0][0] = 1.0;
+    for (int k = 0; k < d; ++k) { dwu[1 + k][0] = -vi[k] / ri; dwu[1 + k][1 + k] = 1.0 / ri; }
+    dwu[d + 1][0] = (ORC_GAMMA - 1.0) * 0.5 * v2;
+    for (int k = 0; k < d; ++k) dwu[d + 1][1 + k] = -(ORC_GAMMA - 1.0) * vi[k];
+    dwu[d + 1][d + 1] = ORC_GAMMA - 1.0;
+
+    for (int a = 0; a < nvar; ++a)
+        for (int b = 0; b < nvar; ++b) {
+            double s = 0.0;
+            for (int c = 0; c < nvar; ++c) s += dFw[a][c] * dwu[c][b];
+            J[a * nvar + b] = s;
+        }
+    (void)dLr_unused; (void)dLb_unused;
+    return st;
+}
+
+static int check_args(int d, int p, int kind, int nvar, int flux)
+{
+    if (d < 2 || d > 3 || p < 1 || p > 8) return 1;
+    if (kind != ORC_NODES_GLL && kind != ORC_NODES_GAUSS) return 1;
+    if (flux == ORC_FLUX_BURGERS && nvar != 1) return 1;
+    if (flux == ORC_FLUX_EULER && nvar != d + 2) return 1;
+    if (flux != ORC_FLUX_BURGERS && flux != ORC_FLUX_EULER) return 1;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Volume residual, sum-factorized (Eq. 3 with Eq. 5): for every direction m */
+/* and node i only the n partners j on the m-line through i contribute,     */
+/*   r_i += omega_m(i) Q1[a_m(i)][a_m(j)] F_m(u_i, u_j),                      */
+/*   omega_m(i) = prod_{k != m} w[a_k(i)],                                  */
+/* which is d n^{d+1} flux evaluations per element (Theorem 2.1).           */
+/* ------------------------------------------------------------------------ */
+int orc_volume_sf(int d, int p, int kind, int nvar, int flux, long n_elem,
+                  const double *u, const double *Ja, double *r)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    double xi[16], w[16], D[256], Q1[256];
+    orc_op1d(p, kind, xi, w, D, Q1);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = u + e * nvar * nn;
+        const double *Je = Ja + e * d * d * nn;
+        double *re = r + e * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) re[q] = 0.0;
+        for (int m = 0; m < d; ++m) {
+            for (int i = 0; i < nn; ++i) {
+                int ai[3]; node_to_multi(i, n, d, ai);
+                double omega = 1.0;
+                for (int k = 0; k < d; ++k) if (k != m) omega *= w[ai[k]];
+                double ui[5];
+                for (int v = 0; v < nvar; ++v) ui[v] = ue[v * nn + i];
+                for (int b = 0; b < n; ++b) {
+                    int aj[3]; memcpy(aj, ai, sizeof aj); aj[m] = b;
+                    int j = multi_to_node(aj, n, d);
+                    double uj[5], nv[3], F[5];
+                    for (int v = 0; v < nvar; ++v) uj[v] = ue[v * nn + j];
+                    for (int k = 0; k < d; ++k) nv[k] = Je[(m * d + k) * nn + i] + Je[(m * d + k) * nn + j];
+                    st |= orc_ec_flux(d, flux, ui, uj, nv, F);
+                    for (int v = 0; v < nvar; ++v) re[v * nn + i] += omega * Q1[ai[m] * n + b] * F[v];
+                }
+            }
+        }
+    }
+    return st;
+}
+
+/* Volume residual, dense (Eq. 1): the full n^d x n^d operators Q_m and the
+ * two-point flux over ALL node pairs (i, j), r_i = sum_m sum_j Q_m[i][j] F_m(u_i, u_j).
+ * O(n^{2d}) per element: the brute-force form the sum-factorized one replaces. */
+int orc_volume_dense(int d, int p, int kind, int nvar, int flux, long n_elem,
+                     const double *u, const double *Ja, double *r)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    double *Q = (double *)malloc(sizeof(double) * (size_t)d * nn * nn);
+    if (!Q) return 1;
+    for (int m = 0; m < d; ++m) orc_qmat_dense(d, p, kind, m, Q + (size_t)m * nn * nn);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = u + e * nvar * nn;
+        const double *Je = Ja + e * d * d * nn;
+        double *re = r + e * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) re[q] = 0.0;
+        for (int m = 0; m < d; ++m) {
+            const double *Qm = Q + (size_t)m * nn * nn;
+            for (int i = 0; i < nn; ++i) {
+                double ui[5];
+                for (int v = 0; v < nvar; ++v) ui[v] = ue[v * nn + i];
+                for (int j = 0; j < nn; ++j) {
+                    double uj[5], nv[3], F[5];
+                    for (int v = 0; v < nvar; ++v) uj[v] = ue[v * nn + j];
+                    for (int k = 0; k < d; ++k) nv[k] = Je[(m * d + k) * nn + i] + Je[(m * d + k) * nn + j];
+                    st |= orc_ec_flux(d, flux, ui, uj, nv, F);
+                    for (int v = 0; v < nvar; ++v) re[v * nn + i] += Qm[(size_t)i * nn + j] * F[v];
+                }
+            }
+        }
+    }
+    free(Q);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector-Jacobian product g = (dr/du)^T lambda (Ja is held fixed).           */
+/* From r_i = sum_m sum_j Q_m,ij F_m(u_i, u_j) and F_m symmetric in its two   */
+/* states (nv is symmetric in i, j):                                        */
+/*   g_l = sum_m sum_{j on the m-line of l} (Q_m,lj lambda_l + Q_m,jl lambda_j)^T d1F_m(u_l, u_j). */
+/* ------------------------------------------------------------------------ */
+int orc_vjp_sf(int d, int p, int kind, int nvar, int flux, long n_elem,
+               const double *u, const double *Ja, const double *lam, double *g)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    double xi[16], w[16], D[256], Q1[256];
+    orc_op1d(p, kind, xi, w, D, Q1);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = u + e * nvar * nn;
+        const double *le = lam + e * nvar * nn;
+        const double *Je = Ja + e * d * d * nn;
+        double *ge = g + e * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) ge[q] = 0.0;
+        for (int m = 0; m < d; ++m) {
+            for (int l = 0; l < nn; ++l) {
+                int al[3]; node_to_multi(l, n, d, al);
+                double omega = 1.0;   /* omega_m is the same for l and j */
+                for (int k = 0; k < d; ++k) if (k != m) omega *= w[al[k]];
+                double ul[5];
+                for (int v = 0; v < nvar; ++v) ul[v] = ue[v * nn + l];
+                for (int b = 0; b < n; ++b) {
+                    int aj[3]; memcpy(aj, al, sizeof aj); aj[m] = b;
+                    int j = multi_to_node(aj, n, d);
+                    double uj[5], nv[3], J1[25], c[5];
+                    for (int v = 0; v < nvar; ++v) uj[v] = ue[v * nn + j];
+                    for (int k = 0; k < d; ++k) nv[k] = Je[(m * d + k) * nn + l] + Je[(m * d + k) * nn + j];
+                    st |= orc_ec_flux_jac1(d, flux, ul, uj, nv, J1);
+                    double Qlj = omega * Q1[al[m] * n + b], Qjl = omega * Q1[b * n + al[m]];
+                    for (int v = 0; v < nvar; ++v) c[v] = Qlj * le[v * nn + l] + Qjl * le[v * nn + j];
+                    for (int bb = 0; bb < nvar; ++bb) {
+                        double s = 0.0;
+                        for (int a = 0; a < nvar; ++a) s += c[a] * J1[a * nvar + bb];
+                        ge[bb * nn + l] += s;
+                    }
+                }
+            }
+        }
+    }
+    return st;
+}
+
+/* Dense-form VJP: assemble the element Jacobian dr/du (nvar nn x nvar nn)
+ * from the dense Eq. 1 form, dr_i/du_l = sum_m sum_j Q_m[i][j]
+ * (delta_il d1F(u_i,u_j) + delta_jl d2F(u_i,u_j)), d2F(u_i,u_j) = d1F(u_j,u_i),
+ * then g = (dr/du)^T lambda. */
+int orc_vjp_dense(int d, int p, int kind, int nvar, int flux, long n_elem,
+                  const double *u, const double *Ja, const double *lam, double *g)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0, N = nvar * nn;
+    double *Q = (double *)malloc(sizeof(double) * (size_t)d * nn * nn);
+    double *Jac = (double *)malloc(sizeof(double) * (size_t)N * N);
+    if (!Q || !Jac) { free(Q); free(Jac); return 1; }
+    for (int m = 0; m < d; ++m) orc_qmat_dense(d, p, kind, m, Q + (size_t)m * nn * nn);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = u + e * nvar * nn;
+        const double *le = lam + e * nvar * nn;
+        const double *Je = Ja + e * d * d * nn;
+        double *ge = g + e * nvar * nn;
+        memset(Jac, 0, sizeof(double) * (size_t)N * N);
+        for (int m = 0; m < d; ++m) {
+            const double *Qm = Q + (size_t)m * nn * nn;
+            for (int i = 0; i < nn; ++i)
+                for (int j = 0; j < nn; ++j) {
+                    double qij = Qm[(size_t)i * nn + j];
+                    if (qij == 0.0) continue;     /* exact zeros of the Kronecker product */
+                    double ui[5], uj[5], nv[3], J1[25], J2[25];
+                    for (int v = 0; v < nvar; ++v) { ui[v] = ue[v * nn + i]; uj[v] = ue[v * nn + j]; }
+                    for (int k = 0; k < d; ++k) nv[k] = Je[(m * d + k) * nn + i] + Je[(m * d + k) * nn + j];
+                    st |= orc_ec_flux_jac1(d, flux, ui, uj, nv, J1);
+                    st |= orc_ec_flux_jac1(d, flux, uj, ui, nv, J2);
+                    for (int a = 0; a < nvar; ++a)
+                        for (int b = 0; b < nvar; ++b) {
+                            /* row (a, i); columns (b, i) and (b, j) */
+                            Jac[(size_t)(a * nn + i) * N + (b * nn + i)] += qij * J1[a * nvar + b];
+                            Jac[(size_t)(a * nn + i) * N + (b * nn + j)] += qij * J2[a * nvar + b];
+                        }
+                }
+        }
+        for (int col = 0; col < N; ++col) {
+            double s = 0.0;
+            for (int row = 0; row < N; ++row) s += Jac[(size_t)row * N + col] * le[row];
+            ge[col] = s;
+        }
+    }
+    free(Q); free(Jac);
+    return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Mesh and metric terms for the free-stream and pressure-equilibrium checks. */
+/* Elements of [0,1]^d, N per direction (element e = ex + N ey + N^2 ez),    */
+/* nodes x_k = (e_k + (xi + 1)/2) / N, then every axis is shifted by the same */
+/* scalar amp * prod_l sin(pi x_l).  Metrics from the degree-p interpolant: */
+/*   2D: Ja^0 = (y_eta, -x_eta), Ja^1 = (-y_xi, x_xi);                       */
+/*   3D: conservative curl form (Kopriva 2006),                              */
+/*       Ja^i_n = -[curl_xi (X_l grad_xi X_m)]_i,  (n, m, l) cyclic,         */
+/* which satisfy sum_m D_m Ja^m_k = 0 to round-off.                          */
+/* x [e][k][i], Ja [e][m][k][i].                                             */
+/* ------------------------------------------------------------------------ */
+static void deriv_dir(int d, int n, const double *D, int dir, const double *f, double *out)
+{
+    int nn = ipow(n, d);
+    for (int i = 0; i < nn; ++i) {
+        int a[3]; node_to_multi(i, n, d, a);
+        double s = 0.0;
+        for (int b = 0; b < n; ++b) {
+            int aj[3]; memcpy(aj, a, sizeof aj); aj[dir] = b;
+            s += D[a[dir] * n + b] * f[multi_to_node(aj, n, d)];
+        }
+        out[i] = s;
+    }
+}
+
+int orc_mesh(int d, int p, int kind, int N, double amp, double *x, double *Ja)
+{
+    if (d < 2 || d > 3 || N < 1) return 1;
+    int n = p + 1, nn = ipow(n, d);
+    double xi[16], w[16], D[256], Q1[256];
+    if (orc_op1d(p, kind, xi, w, D, Q1)) return 1;
+    const double pi = 3.14159265358979323846;
+    long n_elem = 1; for (int k = 0; k < d; ++k) n_elem *= N;
+    double *dX = (double *)malloc(sizeof(double) * 9 * nn);   /* dX[(k*3 + j)*nn + i] = d x_k / d xi_j */
+    double *V = (double *)malloc(sizeof(double) * 3 * nn);
+    double *cV = (double *)malloc(sizeof(double) * nn);
+    double *tmp = (double *)malloc(sizeof(double) * nn);
+    for (long e = 0; e < n_elem; ++e) {
+        int ee[3]; long t = e;
+        for (int k = 0; k < d; ++k) { ee[k] = (int)(t % N); t /= N; }
+        double *xe = x + e * d * nn;
+        double *Je = Ja + e * d * d * nn;
+        for (int i = 0; i < nn; ++i) {
+            int a[3]; node_to_multi(i, n, d, a);
+            double x0[3], s = amp;
+            for (int k = 0; k < d; ++k) { x0[k] = (ee[k] + 0.5 * (xi[a[k]] + 1.0)) / N; s *= sin(pi * x0[k]); }
+            for (int k = 0; k < d; ++k) xe[k * nn + i] = x0[k] + s;
+        }
+        for (int k = 0; k < d; ++k)
+            for (int j = 0; j < d; ++j) deriv_dir(d, n, D, j, xe + k * nn, dX + (k * 3 + j) * nn);
+        if (d == 2) {
+            for (int i = 0; i < nn; ++i) {
+                Je[(0 * 2 + 0) * nn + i] = dX[(1 * 3 + 1) * nn + i];    /*  y_eta */
+                Je[(0 * 2 + 1) * nn + i] = -dX[(0 * 3 + 1) * nn + i];   /* -x_eta */
+                Je[(1 * 2 + 0) * nn + i] = -dX[(1 * 3 + 0) * nn + i];   /* -y_xi  */
+                Je[(1 * 2 + 1) * nn + i] = dX[(0 * 3 + 0) * nn + i];    /*  x_xi  */
+            }
+        } else {
+            for (int nc = 0; nc < 3; ++nc) {
+                int mc = (nc + 1) % 3, lc = (nc + 2) % 3;
+                /* V_j = X_l * d X_m / d xi_j */
+                for (int j = 0; j < 3; ++j)
+                    for (int i = 0; i < nn; ++i)
+                        V[j * nn + i] = xe[lc * nn + i] * dX[(mc * 3 + j) * nn + i];
+                for (int ic = 0; ic < 3; ++ic) {
+                    int jc = (ic + 1) % 3, kc = (ic + 2) % 3;
+                    /* (curl V)_i = D_j V_k - D_k V_j */
+                    deriv_dir(3, n, D, jc, V + kc * nn, cV);
+                    deriv_dir(3, n, D, kc, V + jc * nn, tmp);
+                    for (int i = 0; i < nn; ++i) Je[(ic * 3 + nc) * nn + i] = -(cV[i] - tmp[i]);
+                }
+            }
+        }
+    }
+    free(dX); free(V); free(cV); free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The generic Hadamard workload of the paper's Section 3 timing experiment: */
+/* y = (sum_j dl/dxi_j o C) 1 with C = c c^T in 3D, D_j = I x .. x D x .. x I */
+/* (unweighted).  Dense: loop over all n^6 entries of each D_j.  Sum-        */
+/* factorized (Eq. 3): only the n^4 entries on grid lines.                   */
+/* ------------------------------------------------------------------------ */
+static void fig1_ops(int p, double *D)
+{
+    double xi[64], w[64];
+    orc_nodes(p, ORC_NODES_GLL, xi, w);
+    orc_dmat(p + 1, xi, D);
+}
+
+int orc_fig1_dense(int p, const double *c, double *y)
+{
+    int n = p + 1, nn = n * n * n;
+    double D[64 * 64];
+    if (p < 1 || p > 30) return 1;
+    fig1_ops(p, D);
+    for (int i = 0; i < nn; ++i) y[i] = 0.0;
+    for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < nn; ++i) {
+            int ai[3]; node_to_multi(i, n, 3, ai);
+            double s = 0.0;
+            for (int j = 0; j < nn; ++j) {
+                int aj[3]; node_to_multi(j, n, 3, aj);
+                double q = 1.0;
+                for (int k = 0; k < 3; ++k)
+                    q *= (k == m) ? D[ai[k] * n + aj[k]] : (ai[k] == aj[k] ? 1.0 : 0.0);
+                s += q * (c[i] * c[j]);
+            }
+            y[i] += s;
+        }
+    return 0;
+}
+
+int orc_fig1_sf(int p, const double *c, double *y)
+{
+    int n = p + 1, nn = n * n * n;
+    double D[64 * 64];
+    if (p < 1 || p > 30) return 1;
+    fig1_ops(p, D);
+    for (int i = 0; i < nn; ++i) y[i] = 0.0;
+    for (int m = 0; m < 3; ++m)
+        for (int i = 0; i < nn; ++i) {
+            int ai[3]; node_to_multi(i, n, 3, ai);
+            double s = 0.0;
+            for (int b = 0; b < n; ++b) {
+                int aj[3]; memcpy(aj, ai, sizeof aj); aj[m] = b;
+                int j = multi_to_node(aj, n, 3);
+                s += D[ai[m] * n + b] * (c[i] * c[j]);
+            }
+            y[i] += s;
+        }
+    return 0;
+}
