@@ -1,0 +1,373 @@
+#!/usr/bin/env python
+"""Throughput of the sum-factorized Hadamard-product volume term on GB300.
+
+Metric: element-DOF/s of the 3D Euler volume residual (elements x (p+1)^3
+nodes per second per residual evaluation), on the workload
+  3D compressible Euler, Ranocha EC/KEP flux, p = 4 (5 Gauss-Lobatto nodes per
+  direction), 32^3 elements of the warped periodic cube (amplitude 0.1),
+  random-Fourier state; 4,096,000 element-DOF per residual.
+One step = one residual evaluation over the whole batch (stage, line sweeps,
+Hadamard row sums, store), inputs resident in HBM.  The headline `value` is
+the FP32-Kahan residual; FP64, the mixed mode, the adjoint and the serving
+stream are measured after it and reported under "variants".
+
+Launch: `python bench.py [--gpus N --steps K --warmup W]`; for N > 1 under
+torchrun, every rank processes its own 32^3 block (weak scaling, no data-path
+collective), timing is the max over ranks.  `--impl reference` times the FP64
+CPU oracle on the host cores instead (a bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="euler3d_p4_gll_32cubed_warped", d=3, p=4, kind=0, N=32)
+METRIC = "element-DOF/s of 3D Euler volume residual"
+GAMMA_DIAG = 30          # algorithmic flops of one diagonal (physical-flux) term incl. accumulation
+PAIR_FLOPS = 92          # algorithmic flops of one off-diagonal pair (see flops_per_element)
+NODE_FLOPS = 13          # conservative -> primitive per node
+
+
+def flops_per_element(d: int, p: int, kind: int) -> float:
+    """Algorithmic flops of one element's residual, counted once from the
+    formula (add/mul/div/log = 1 flop each), each unordered line pair once:
+      pair: metric sum 3, two log means (series) 24, v.n_a, v.n_b, v_a.v_b 15,
+            mass flux 3, mean pressure 2, momentum 15, energy 10, both
+            accumulations 20  -> 92;
+      diagonal term (only where Q1[a][a] != 0): physical flux + accumulation 30;
+      per node: primitives 13, omega-scaled direction sums 10 per direction."""
+    n = p + 1
+    lines = d * n ** (d - 1)
+    pairs = lines * n * (n - 1) // 2
+    ndiag = 2 if kind == 0 else n          # Gauss-Lobatto: only the two endpoints
+    return pairs * PAIR_FLOPS + lines * ndiag * GAMMA_DIAG + n ** d * (NODE_FLOPS + 10 * d)
+
+
+def bytes_per_node(prec: str, d: int = 3) -> int:
+    """Algorithmic HBM bytes per node: read u and Ja, write r."""
+    nvar = d + 2
+    esz = 8 if prec == "fp64" else 4
+    return 2 * nvar * esz + d * d * 8
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# clocks sampler (nvidia-smi during the timed region)
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle as CPU baseline (threads: ctypes releases the GIL)
+# ---------------------------------------------------------------------------
+def oracle_throughput(u, Ja, d, p, kind, elems, threads):
+    import concurrent.futures as cf
+
+    import oracle as O
+    O.build()
+    E = min(elems, u.shape[0])
+    chunks = np.array_split(np.arange(E), threads)
+
+    def work(ix):
+        if ix.size:
+            O.volume_sf(d, p, kind, O.FLUX_EULER, u[ix[0]:ix[-1] + 1], Ja[ix[0]:ix[-1] + 1])
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(work, chunks))
+    dt = time.perf_counter() - t0
+    return E * (p + 1) ** d / dt, dt, E
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2306_11665_gb300 import inputs as I
+    W = WORKLOAD
+    cores = os.cpu_count() or 1
+    sample_el = 4096                      # a bounded sample of the workload per step
+    x_u, x_J = I.workload(W["d"], W["p"], W["kind"], W["N"], n_elem=sample_el)
+    vals = []
+    for _ in range(args.warmup):
+        oracle_throughput(x_u, x_J, W["d"], W["p"], W["kind"], sample_el, cores)
+    for _ in range(args.steps):
+        v, dt, E = oracle_throughput(x_u, x_J, W["d"], W["p"], W["kind"], sample_el, cores)
+        vals.append(dt)
+    t = sum(vals) / len(vals)
+    value = sample_el * (W["p"] + 1) ** W["d"] / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": W["name"], "sample_elements_per_step": sample_el, "threads": cores},
+            "cpu_baseline": {"value": value, "unit": "element-DOF/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {sample_el} of 32768 elements per step, FP64 oracle, {cores} threads"},
+            "e2e": {"value": value, "unit": "element-DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def timed_launches(fn, steps, warmup, stream, torch):
+    """Run `fn` warmup + steps times on `stream`; returns (total_ms, mean_launch_ms)."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * steps + 2)]
+    ev[0].record(stream)
+    for k in range(steps):
+        ev[1 + 2 * k].record(stream)
+        fn()
+        ev[2 + 2 * k].record(stream)
+    ev[-1].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0].elapsed_time(ev[-1])
+    per = [ev[1 + 2 * k].elapsed_time(ev[2 + 2 * k]) for k in range(steps)]
+    return total, sum(per) / len(per)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--p", type=int, default=None, help="override the degree (exploration only)")
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    from paper_2306_11665_gb300 import _abi as A
+    from paper_2306_11665_gb300 import api
+    from paper_2306_11665_gb300 import build as B
+    from paper_2306_11665_gb300 import inputs as I
+    if local == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+
+    W = dict(WORKLOAD)
+    if args.p is not None:
+        W["p"] = args.p
+        W["name"] = f"euler3d_p{args.p}_gll_32cubed_warped"
+    d, p, kind, N = W["d"], W["p"], W["kind"], W["N"]
+    nn = (p + 1) ** d
+    u64, Ja = I.workload(d, p, kind, N, seed0=2 + 10 * rank)   # each rank its own block
+    E = u64.shape[0]
+    dof = E * nn
+    dev = torch.device("cuda", local)
+    tu64 = torch.from_numpy(u64).to(dev)
+    tu32 = torch.from_numpy(I.to_fp32(u64)).to(dev)
+    tJ = torch.from_numpy(Ja).to(dev)
+    r32 = torch.empty_like(tu32)
+    r64 = torch.empty_like(tu64)
+    ctx = api.Context(d, p, kind, "euler")
+    stream = torch.cuda.current_stream(dev)
+    sh = stream.cuda_stream
+
+    gpu_idx = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local] if \
+        os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
+    sampler = ClockSampler(gpu_idx)
+
+    def step32():
+        A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_KAHAN, sh)
+
+    # ---- headline: FP32-Kahan residual, K steps
+    for _ in range(args.warmup):
+        step32()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.start()
+    time.sleep(0.2)
+    t_total, t_launch = timed_launches(step32, args.steps, 0, stream, torch)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+        tt = torch.tensor([t_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_total = float(tt.item())
+    assert ctx.check() == A.SFH_OK
+    ms_step = t_total / args.steps
+    value = world * dof / (ms_step * 1e-3)
+
+    peaks = load_peaks() or {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    b32 = bytes_per_node("fp32k", d) * dof
+    roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": None,
+                "peak_source": hbm_src, "kernel": "volume_kernel<3,%d,euler,FP32K>" % (p + 1),
+                "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
+    fl = flops_per_element(d, p, kind) * E
+
+    variants = {}
+    if not args.no_variants:
+        # arithmetic peaks (our own microbenchmark)
+        try:
+            fp64_tf, _ = A.sfh_peak_fma(A.SFH_FP64)
+            fp32_tf, _ = A.sfh_peak_fma(A.SFH_FP32_KAHAN)
+        except Exception:
+            fp64_tf = fp32_tf = None
+        nominal64 = 1.25
+        nominal32 = 152 * 128 * 2 * 2.07e9 / 1e12
+        variants["alu_peaks_tflops"] = {"fp64_measured": fp64_tf, "fp32_measured": fp32_tf,
+                                        "fp64_nominal": nominal64, "fp32_nominal": round(nominal32, 1)}
+        variants["fp32k"] = {"element_dof_per_s": value / world, "ms": t_launch,
+                             "flops_per_launch": fl,
+                             "alu_frac_of_nominal": fl / (t_launch * 1e-3) / (nominal32 * 1e12),
+                             "hbm_frac_of_measured": roofline["frac"]}
+
+        def step64():
+            A.sfh_volume_residual(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), r64.data_ptr(), A.SFH_FP64, sh)
+        k64 = max(5, min(50, args.steps // 20))
+        _, t64 = timed_launches(step64, k64, 2, stream, torch)
+        b64 = bytes_per_node("fp64", d) * dof
+        variants["fp64"] = {"element_dof_per_s": dof / (t64 * 1e-3), "ms": t64, "flops_per_launch": fl,
+                            "bound": "alu(fp64)",
+                            "alu_frac_of_nominal": fl / (t64 * 1e-3) / (nominal64 * 1e12),
+                            "alu_frac_of_measured": (fl / (t64 * 1e-3) / (fp64_tf * 1e12)) if fp64_tf else None,
+                            "hbm_frac_of_measured": b64 / (t64 * 1e-3) / 1e9 / hbm_peak}
+
+        def stepmix():
+            A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_MIXED, sh)
+        _, tmix = timed_launches(stepmix, k64, 2, stream, torch)
+        variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix}
+
+        # adjoint on the adjoint configuration (p = 5, 8^3) and on this workload
+        g = torch.empty_like(tu64)
+        lam = torch.from_numpy(I.cotangent(u64.shape, seed=8)).to(dev)
+
+        def stepvjp():
+            A.sfh_vjp(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), lam.data_ptr(), g.data_ptr(), sh)
+        _, tv = timed_launches(stepvjp, k64, 2, stream, torch)
+        variants["vjp_fp64"] = {"element_dof_per_s": dof / (tv * 1e-3), "ms": tv, "forward_fp64_ms": t64}
+        assert ctx.check() == A.SFH_OK
+
+    clocks = sampler.stop()
+
+    # ---- end to end through the host-buffer C-ABI entry point (pinned memory)
+    uh = torch.from_numpy(I.to_fp32(u64)).pin_memory()
+    Jh = torch.from_numpy(Ja).pin_memory()
+    rh = torch.empty_like(uh).pin_memory()
+    ke = max(3, min(20, args.steps // 100))
+    for _ in range(2):
+        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), A.SFH_FP32_KAHAN)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), A.SFH_FP32_KAHAN)
+    te = (time.perf_counter() - t0) / ke
+    if dist:
+        tt = torch.tensor([te], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        te = float(tt.item())
+    e2e = {"value": world * dof / te, "unit": "element-DOF/s",
+           "h2d_bytes_per_step": int(uh.numel() * 4 + Jh.numel() * 8), "d2h_bytes_per_step": int(rh.numel() * 4),
+           "ms_per_step": te * 1e3, "api": "sfh_volume_residual_host (pinned host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        v, dt, Es = oracle_throughput(u64, Ja, d, p, kind, 8192, cores)
+        cpu = {"value": v, "unit": "element-DOF/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {Es} of {E} elements, FP64 oracle, {cores} threads, {dt:.2f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": W["name"], "elements_per_gpu": E, "nodes_per_element": nn,
+                           "precision": "fp32 kahan (FP64 metric input)", "l2": "inputs larger than L2 (459 MB per step)",
+                           "parallelism": f"replicas x{world} (independent element blocks)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": args.steps, "variants": variants}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * sfhad.h -- C ABI of libsfhad, a GB300 (sm_103a) library for the
+ * sum-factorized Hadamard-product volume term of entropy-conserving flux
+ * differencing (Cicchino & Nadarajah, arXiv 2306.11665).
+ *
+ * What it computes (Section 2, Eq. 3 with the operators of Eq. 5): for every
+ * element of a tensor-product mesh with n = p + 1 collocated nodes per
+ * direction,
+ *
+ *     r_i = sum_{m=0}^{d-1} sum_j (Q_m o F_m)_ij,
+ *     Q_m = (W (x) .. (x) W D (x) .. (x) W)  with W D in direction m,
+ *     F_m,ij = sum_k fsharp_k(u_i, u_j) (Ja^m_k(i) + Ja^m_k(j)),
+ *
+ * where only node pairs (i, j) on the same grid line along m contribute, so
+ * each element costs d n^{d+1} two-point fluxes instead of n^{2d}
+ * (Theorem 2.1).  fsharp is Ranocha's entropy-conserving, kinetic-energy-
+ * preserving Euler flux (gamma = 1.4) or the Burgers flux (a^2 + ab + b^2)/6.
+ *
+ * Layouts (all arrays dense, C order, nodes x fastest as in Section 2):
+ *   u, r, lambda, grad_u : [n_elem][nvar][n^d]        (i = a_0 + n a_1 + n^2 a_2)
+ *   Ja                   : [n_elem][d][d][n^d]        Ja[e][m][k][i] = J dxi_m/dx_k
+ *   Euler variables      : (rho, rho v_1, .., rho v_d, E); nvar = d + 2
+ *   Burgers              : nvar = 1
+ *
+ * Ownership: every array is owned by the caller.  Device pointers must stay
+ * valid until the work on `stream` has completed; the library keeps none of
+ * them after that.  The library owns only what a context allocates (the
+ * operator tables and an error word on the device).
+ *
+ * Errors: no call aborts, traps or hangs.  Argument errors are reported
+ * before any device work is issued.  Errors found by the device (a density
+ * or pressure <= 0 in the state) are latched in the context's error word and
+ * reported by sfh_check().  sfh_last_error() returns a thread-local message
+ * for the last failing call of the calling thread.
+ *
+ * Streams: sfh_stream_t is a cudaStream_t; NULL means the legacy default
+ * stream.  Device entry points are asynchronous with respect to the host.
+ */
+#ifndef SFHAD_H
+#define SFHAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sfh_stream_t;
+
+typedef enum {
+    SFH_OK = 0,
+    SFH_EINVAL = 1,        /* bad argument (null pointer, size, enum, misalignment) */
+    SFH_ENOMEM = 2,        /* allocation failed, or a request exceeds a memory budget */
+    SFH_ECUDA = 3,         /* a CUDA runtime call failed (message in sfh_last_error) */
+    SFH_EDOMAIN = 4,       /* the device saw a density or pressure <= 0 (or NaN) */
+    SFH_EBUSY = 5,         /* the server cannot take the request now */
+    SFH_ENOTREADY = 6,     /* a polled request has not completed yet */
+    SFH_ETIMEOUT = 7,      /* a bounded wait gave up */
+    SFH_EUNSUPPORTED = 8   /* valid but not provided (e.g. no CUDA device) */
+} sfh_status;
+
+typedef enum { SFH_NODES_GLL = 0, SFH_NODES_GAUSS = 1 } sfh_nodes;
+
+typedef enum {
+    SFH_FLUX_BURGERS = 0,       /* fsharp_k(a, b) = (a^2 + a b + b^2) / 6 in every direction k */
+    SFH_FLUX_EULER_RANOCHA = 1  /* Ranocha EC/KEP flux with logarithmic means, gamma = 1.4 */
+} sfh_flux;
+
+typedef enum {
+    SFH_FP64 = 0,        /* all arithmetic in FP64; u, r are double */
+    SFH_FP32_KAHAN = 1,  /* FP32 flux arithmetic, compensated line sums; u, r are float */
+    SFH_FP32_MIXED = 2   /* as SFH_FP32_KAHAN, with FP64 metric sums Ja(i)+Ja(j) and an
+                            FP64 logarithmic mean in the near-equal band; u, r are float */
+} sfh_prec;
+
+typedef struct sfh_ctx sfh_ctx;
+
+/* Create a context for one element type (Section 2: d directions, n = p + 1
+ * nodes on each, collocated Lagrange basis; Eq. 5 operators).
+ * d in {2, 3}; p in [1, 8]; nvar must be 1 for SFH_FLUX_BURGERS and d + 2 for
+ * SFH_FLUX_EULER_RANOCHA.  Builds the 1D operator tables (nodes, weights,
+ * D, Q1 = W D) on the host and allocates the device error word on the
+ * current device.  *out is set only on SFH_OK.
+ * Errors: SFH_EINVAL for bad arguments; SFH_ECUDA / SFH_EUNSUPPORTED when no
+ * CUDA device can be used; SFH_ENOMEM. */
+sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_flux flux, sfh_ctx **out);
+
+/* Release a context (waits for nothing: the caller must not destroy a context
+ * whose work is still in flight).  NULL is accepted. */
+sfh_status sfh_destroy(sfh_ctx *ctx);
+
+/* Volume residual r (Eq. 3 with Eq. 5, Section 2, three-step evaluation of
+ * the three-dimensional listing): builds each line's two-point fluxes in
+ * registers and sums the Hadamard product row by row, r overwritten.
+ * u, r: device, [n_elem][nvar][n^d], double for SFH_FP64, float otherwise,
+ *       8-byte (double) or 4-byte (float) aligned; r must not overlap u or Ja.
+ * Ja:   device, [n_elem][d][d][n^d] double (FP64 in every mode), 8-byte aligned.
+ * n_elem >= 0 (0 is a no-op).  Asynchronous on `stream`.
+ * Errors: SFH_EINVAL before any launch; SFH_ECUDA if the launch fails;
+ * domain errors are latched for sfh_check(). */
+sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, const double *Ja,
+                               void *r, sfh_prec prec, sfh_stream_t stream);
+
+/* Vector-Jacobian product of the volume residual with respect to u (FP64):
+ * grad_u = (dr/du)^T lambda with Ja held fixed, i.e.
+ *   g_l = sum_m sum_{j on the m-line of l} (Q_m,lj lambda_l + Q_m,jl lambda_j)^T d1F_m(u_l, u_j),
+ * which follows from Eq. 3 and the symmetry of F_m in its two states.
+ * u, lambda, grad_u: device double [n_elem][nvar][n^d]; Ja as above.
+ * grad_u is overwritten and must not overlap the inputs.  Asynchronous. */
+sfh_status sfh_vjp(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *Ja,
+                   const double *lambda, double *grad_u, sfh_stream_t stream);
+
+/* Synchronize `stream`, then read and clear the context's device error word.
+ * Returns SFH_EDOMAIN if any kernel of this context saw rho <= 0 or p <= 0
+ * (or a NaN) since the last check, SFH_ECUDA on a CUDA error, else SFH_OK. */
+sfh_status sfh_check(sfh_ctx *ctx, sfh_stream_t stream);
+
+/* Host-buffer form of sfh_volume_residual: u_host, Ja_host, r_host are host
+ * pointers (page-locked memory gives full copy bandwidth; pageable memory
+ * works but is staged by the CUDA runtime).  The elements are processed in
+ * chunks on two internal streams so that host->device copies, kernels and
+ * device->host copies overlap; the device staging buffers belong to the
+ * context (allocated on first use, grown when needed, freed by
+ * sfh_destroy).  Synchronous: returns when r_host is filled, and also
+ * reports device domain errors (as sfh_check would).
+ * Errors: SFH_EINVAL, SFH_ENOMEM, SFH_ECUDA, SFH_EDOMAIN. */
+sfh_status sfh_volume_residual_host(sfh_ctx *ctx, int64_t n_elem, const void *u_host,
+                                    const double *Ja_host, void *r_host, sfh_prec prec);
+
+/* Describe a context: any output pointer may be NULL.  n_nodes = (p+1)^d. */
+sfh_status sfh_ctx_info(const sfh_ctx *ctx, int *d, int *p, int *nodes, int *nvar, int *flux,
+                        int *n_nodes);
+
+/* The 1D operator tables of one element type, computed on the host (no
+ * device needed): nodes xi[n] (ascending on [-1, 1]), quadrature weights
+ * w[n], collocation derivative D[n*n] (D[i*n + j] = l_j'(xi_i)) and the
+ * weighted derivative Q1 = W D [n*n] of Eq. 5, n = p + 1, FP64, row-major.
+ * Gauss-Lobatto: endpoints and the roots of P_p'; Gauss-Legendre: roots of
+ * P_{p+1}.  Any output pointer may be NULL.  Errors: SFH_EINVAL. */
+sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, double *w, double *D, double *Q1);
+
+/* Thread-local message describing the last error of the calling thread
+ * ("" if none).  Never NULL. */
+const char *sfh_last_error(void);
+
+/* Library version as major * 10000 + minor * 100 + patch. */
+int sfh_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Arithmetic-peak microbenchmarks (the denominators of the ALU rooflines).
+ * Runs a register-resident chain of fused multiply-adds on every SM of the
+ * current device and reports the achieved rate.  prec: SFH_FP64 (DFMA) or
+ * SFH_FP32_KAHAN (FFMA).  *tflops receives 2 * FMAs / second / 1e12, *ms the
+ * measured kernel time.  Synchronous.
+ * ------------------------------------------------------------------------- */
+sfh_status sfh_peak_fma(sfh_prec prec, double *tflops, double *ms);
+
+/* ---------------------------------------------------------------------------
+ * Serving: batched residual and VJP requests of mixed degree p, element
+ * count and precision on one device (3D Euler, Ranocha flux).  Requests are
+ * admitted in FIFO order against an HBM budget and a limit on requests in
+ * flight; admitted work is cut into element tiles and executed by persistent
+ * CTAs that pull tiles from a device queue, so tiles of requests that arrive
+ * while others run are interleaved with them on the GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct sfh_server sfh_server;
+
+typedef struct {
+    size_t hbm_budget_bytes;   /* admission budget for resident request data (u, Ja, out, lambda) */
+    int max_inflight;          /* requests admitted at once (>= 1) */
+    int timeout_ms;            /* bound on every wait of the server (device and host) */
+    int n_workers;             /* persistent CTAs; 0 = one per SM */
+} sfh_server_opts;
+
+typedef enum { SFH_REQ_RESIDUAL = 0, SFH_REQ_VJP = 1 } sfh_req_kind;
+
+typedef struct {
+    int kind;            /* sfh_req_kind */
+    int p;               /* 2..8 */
+    int nodes;           /* sfh_nodes */
+    int prec;            /* sfh_prec for residuals; VJP requests are FP64 */
+    int64_t n_elem;
+    const void *u;       /* device, resident; double (FP64, VJP) or float (FP32 modes) */
+    const double *Ja;    /* device, resident */
+    const double *lambda;/* device, VJP only */
+    void *out;           /* device: r (residual) or grad_u (VJP), overwritten */
+} sfh_request;
+
+typedef struct {
+    int status;          /* sfh_status of the request */
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;   /* host CLOCK_MONOTONIC timestamps */
+} sfh_result;
+
+/* Create a server on the current device; starts its persistent kernel and
+ * its host admission thread.  Errors: SFH_EINVAL, SFH_ENOMEM, SFH_ECUDA. */
+sfh_status sfh_server_create(const sfh_server_opts *opts, sfh_server **out);
+
+/* Queue a request (thread-safe).  SFH_ENOMEM if the request alone exceeds
+ * the budget, SFH_EINVAL for bad fields; otherwise the request is queued
+ * FIFO and *ticket identifies it.  The arrays must stay valid and unchanged
+ * until sfh_serve_poll reports the request done. */
+sfh_status sfh_serve_submit(sfh_server *srv, const sfh_request *req, uint64_t *ticket);
+
+/* Non-blocking: SFH_OK and *out filled when the request is done (out->status
+ * holds its own result), SFH_ENOTREADY while it is pending, SFH_EINVAL for an
+ * unknown ticket.  A ticket can be polled done once. */
+sfh_status sfh_serve_poll(sfh_server *srv, uint64_t ticket, sfh_result *out);
+
+/* Block until every submitted request is done or timeout_ms passes
+ * (SFH_ETIMEOUT). */
+sfh_status sfh_serve_drain(sfh_server *srv, int timeout_ms);
+
+/* Stop the server: drains (bounded by timeout_ms), stops the persistent
+ * kernel, joins the admission thread and frees the server. NULL accepted. */
+sfh_status sfh_server_destroy(sfh_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFHAD_H */

@@ -1,0 +1,110 @@
+"""Torch-facing helpers over the C ABI: contexts, residual, VJP, autograd.
+
+PyTorch provides device memory and streams only; every step of the volume
+term runs in libsfhad's kernels.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _abi as A
+
+NODES = {"gll": A.SFH_NODES_GLL, "gauss": A.SFH_NODES_GAUSS}
+FLUX = {"burgers": A.SFH_FLUX_BURGERS, "euler": A.SFH_FLUX_EULER_RANOCHA}
+PREC = {"fp64": A.SFH_FP64, "fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED}
+PREC_DTYPE = {A.SFH_FP64: torch.float64, A.SFH_FP32_KAHAN: torch.float32, A.SFH_FP32_MIXED: torch.float32}
+
+
+def _enum(table, v):
+    return table[v] if isinstance(v, str) else int(v)
+
+
+class Context:
+    """One element type: dimension d, degree p, node set, flux (owns an sfh_ctx)."""
+
+    def __init__(self, d: int, p: int, nodes="gll", flux="euler"):
+        self.d, self.p = d, p
+        self.nodes = _enum(NODES, nodes)
+        self.flux = _enum(FLUX, flux)
+        self.nvar = 1 if self.flux == A.SFH_FLUX_BURGERS else d + 2
+        self.n_nodes = (p + 1) ** d
+        self.handle = A.sfh_create(d, p, self.nodes, self.nvar, self.flux)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            A.sfh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, stream=None) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return A.sfh_check(self.handle, s.cuda_stream)
+
+    def _shape_check(self, u: torch.Tensor, Ja: torch.Tensor, dtype):
+        E = u.shape[0]
+        if u.shape != (E, self.nvar, self.n_nodes):
+            raise ValueError(f"u must be [n_elem, {self.nvar}, {self.n_nodes}], got {tuple(u.shape)}")
+        if Ja.shape != (E, self.d, self.d, self.n_nodes):
+            raise ValueError(f"Ja must be [n_elem, {self.d}, {self.d}, {self.n_nodes}], got {tuple(Ja.shape)}")
+        if u.dtype != dtype or Ja.dtype != torch.float64:
+            raise TypeError(f"u must be {dtype} and Ja float64")
+        if not (u.is_cuda and Ja.is_cuda and u.is_contiguous() and Ja.is_contiguous()):
+            raise ValueError("u and Ja must be contiguous CUDA tensors")
+
+    def volume_residual(self, u: torch.Tensor, Ja: torch.Tensor, prec="fp64", out: torch.Tensor | None = None):
+        """r = sum_m (Q_m o F_m) 1 on the current stream (new tensor unless `out`)."""
+        pr = _enum(PREC, prec)
+        self._shape_check(u, Ja, PREC_DTYPE[pr])
+        r = torch.empty_like(u) if out is None else out
+        A.sfh_volume_residual(self.handle, u.shape[0], u.data_ptr(), Ja.data_ptr(), r.data_ptr(), pr,
+                              torch.cuda.current_stream(u.device).cuda_stream)
+        return r
+
+    def vjp(self, u: torch.Tensor, Ja: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None):
+        """(dr/du)^T lambda (FP64) on the current stream."""
+        self._shape_check(u, Ja, torch.float64)
+        if lam.shape != u.shape or lam.dtype != torch.float64 or not lam.is_contiguous() or not lam.is_cuda:
+            raise ValueError("lambda must be a contiguous float64 CUDA tensor shaped like u")
+        g = torch.empty_like(u) if out is None else out
+        A.sfh_vjp(self.handle, u.shape[0], u.data_ptr(), Ja.data_ptr(), lam.data_ptr(), g.data_ptr(),
+                  torch.cuda.current_stream(u.device).cuda_stream)
+        return g
+
+    def volume_residual_host(self, u, Ja, prec="fp64"):
+        """Host-buffer entry point: u, Ja CPU tensors (pinned for full speed); returns r on the host."""
+        pr = _enum(PREC, prec)
+        if u.is_cuda or Ja.is_cuda:
+            raise ValueError("host entry point takes CPU tensors")
+        r = torch.empty_like(u, pin_memory=u.is_pinned())
+        st = A.sfh_volume_residual_host(self.handle, u.shape[0], u.data_ptr(), Ja.data_ptr(), r.data_ptr(), pr)
+        if st != A.SFH_OK:
+            raise A.SfhError(st, "sfh_volume_residual_host", A.sfh_last_error())
+        return r
+
+
+class SFHVolume(torch.autograd.Function):
+    """r = volume_residual(u; Ja) with the hand-written adjoint as backward.
+    FP64 only; Ja receives no gradient (it is geometry, held fixed)."""
+
+    @staticmethod
+    def forward(ctx_, u, Ja, context: Context):
+        u = u.contiguous()
+        ctx_.save_for_backward(u, Ja)
+        ctx_.context = context
+        return context.volume_residual(u, Ja, "fp64")
+
+    @staticmethod
+    def backward(ctx_, grad_r):
+        u, Ja = ctx_.saved_tensors
+        g = ctx_.context.vjp(u, Ja, grad_r.contiguous())
+        return g, None, None
+
+
+def volume(u: torch.Tensor, Ja: torch.Tensor, context: Context) -> torch.Tensor:
+    """Differentiable FP64 volume residual (autograd through sfh_vjp)."""
+    return SFHVolume.apply(u, Ja, context)

@@ -1,0 +1,465 @@
+// sfh_api.cu -- host side of libsfhad: operator tables, contexts, argument
+// validation, launches, the host-buffer pipeline and the peak benchmarks.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+
+#include "../../include/sfhad.h"
+#include "sfh_internal.h"
+
+// ---------------------------------------------------------------------------
+// thread-local error message
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512];
+
+static sfh_status fail(sfh_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+static sfh_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(SFH_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+static void clear_err() { g_err[0] = '\0'; }
+
+extern "C" const char *sfh_last_error(void) { return g_err; }
+extern "C" int sfh_version(void) { return 10000; }
+
+// ---------------------------------------------------------------------------
+// 1D operator tables (Eq. 5 needs the collocated Lagrange basis on the nodes).
+// Long-double Newton iterations:
+//   Gauss-Legendre: roots of P_n, derivative P_n' = n (x P_n - P_{n-1}) / (x^2 - 1);
+//   Gauss-Lobatto:  interior roots of P_{p+1} - P_{p-1} (whose roots are +-1 and
+//                   the zeros of P_p'), derivative (2p + 1) P_p.
+// Weights: 2 / ((1 - x^2) P_n'(x)^2) and 2 / (p (p+1) P_p(x)^2).
+// D_ij = l_j'(x_i) = (c_i / c_j) / (x_i - x_j), c_i = prod_{k != i} (x_i - x_k),
+// D_ii = sum_{k != i} 1 / (x_i - x_k).
+// ---------------------------------------------------------------------------
+namespace {
+
+void legendre2(int k, long double x, long double &Pk, long double &Pkm1) {
+    long double a = 1.0L, b = x;   // P_0, P_1
+    if (k == 0) { Pk = 1.0L; Pkm1 = 0.0L; return; }
+    for (int j = 1; j < k; ++j) {
+        long double c = ((2 * j + 1) * x * b - j * a) / (j + 1);
+        a = b;
+        b = c;
+    }
+    Pk = b;
+    Pkm1 = a;
+}
+
+bool make_tables(int p, int kind, long double *x, long double *w, long double *D) {
+    const int n = p + 1;
+    const long double PI = 3.141592653589793238462643383279502884L;
+    if (p < 1 || p > sfh::NMAX - 1) return false;
+    if (kind == SFH_NODES_GAUSS) {
+        for (int j = 0; j < n; ++j) {
+            long double xx = -cosl(PI * (4 * j + 3) / (4 * n + 2));
+            for (int it = 0; it < 64; ++it) {
+                long double P, Pm;
+                legendre2(n, xx, P, Pm);
+                const long double dP = n * (xx * P - Pm) / (xx * xx - 1.0L);
+                const long double step = P / dP;
+                xx -= step;
+                if (fabsl(step) < 1e-21L) break;
+            }
+            long double P, Pm;
+            legendre2(n, xx, P, Pm);
+            const long double dP = n * (xx * P - Pm) / (xx * xx - 1.0L);
+            x[j] = xx;
+            w[j] = 2.0L / ((1.0L - xx * xx) * dP * dP);
+        }
+    } else {
+        x[0] = -1.0L;
+        x[p] = 1.0L;
+        for (int j = 1; j < p; ++j) {
+            long double xx = -cosl(PI * j / p);
+            for (int it = 0; it < 64; ++it) {
+                long double Pp1, Pp, Ppm1, tmp;
+                legendre2(p + 1, xx, Pp1, Pp);
+                legendre2(p - 1, xx, Ppm1, tmp);
+                const long double q = Pp1 - Ppm1, dq = (2 * p + 1) * Pp;
+                const long double step = q / dq;
+                xx -= step;
+                if (fabsl(step) < 1e-21L) break;
+            }
+            x[j] = xx;
+        }
+        for (int j = 0; j < n; ++j) {
+            long double P, Pm;
+            legendre2(p, x[j], P, Pm);
+            w[j] = 2.0L / ((long double)p * (p + 1) * P * P);
+        }
+    }
+    std::sort(x, x + n);   // Gauss guesses run from -1 up already; keep ascending in any case
+    // both node sets are symmetric about 0: enforce it exactly (the middle
+    // node of an odd set becomes exactly 0)
+    for (int j = 0; j < n / 2; ++j) {
+        const long double h = 0.5L * (x[n - 1 - j] - x[j]);
+        x[j] = -h;
+        x[n - 1 - j] = h;
+        const long double wh = 0.5L * (w[j] + w[n - 1 - j]);
+        w[j] = wh;
+        w[n - 1 - j] = wh;
+    }
+    if (n % 2) x[n / 2] = 0.0L;
+    for (int i = 0; i < n; ++i) {
+        long double ci = 1.0L, dii = 0.0L;
+        for (int k = 0; k < n; ++k)
+            if (k != i) { ci *= (x[i] - x[k]); dii += 1.0L / (x[i] - x[k]); }
+        for (int j = 0; j < n; ++j) {
+            if (j == i) {
+                // Gauss-Lobatto interior nodes and the middle node of an odd
+                // symmetric set have D_ii = 0 exactly; keep it exact so that the
+                // kernels can skip zero diagonal entries
+                const bool zero = (n % 2 && i == n / 2) ||
+                                  (kind == SFH_NODES_GLL && i > 0 && i < n - 1);
+                D[i * n + j] = zero ? 0.0L : dii;
+                continue;
+            }
+            long double cj = 1.0L;
+            for (int k = 0; k < n; ++k)
+                if (k != j) cj *= (x[j] - x[k]);
+            D[i * n + j] = (ci / cj) / (x[i] - x[j]);
+        }
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, double *w, double *D,
+                                          double *Q1) {
+    clear_err();
+    if (p < 1 || p > sfh::NMAX - 1) return fail(SFH_EINVAL, "p must be in [1, %d], got %d", sfh::NMAX - 1, p);
+    if (nodes != SFH_NODES_GLL && nodes != SFH_NODES_GAUSS) return fail(SFH_EINVAL, "bad node set %d", (int)nodes);
+    long double x[sfh::NMAX], ww[sfh::NMAX], DD[sfh::NMAX * sfh::NMAX];
+    if (!make_tables(p, nodes, x, ww, DD)) return fail(SFH_EINVAL, "table construction failed");
+    const int n = p + 1;
+    for (int i = 0; i < n; ++i) {
+        if (xi) xi[i] = (double)x[i];
+        if (w) w[i] = (double)ww[i];
+        for (int j = 0; j < n; ++j) {
+            if (D) D[i * n + j] = (double)DD[i * n + j];
+            if (Q1) Q1[i * n + j] = (double)(ww[i] * DD[i * n + j]);
+        }
+    }
+    return SFH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct sfh_ctx {
+    int d, p, n, nodes, nvar, flux, device;
+    int *d_err;
+    sfh::OpTab<double> tab_d;
+    sfh::OpTab<float> tab_f;
+    // staging of the host-buffer entry point
+    std::mutex host_mu;
+    cudaStream_t hs[2];
+    void *stage[2];
+    size_t stage_bytes;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int mode_of(sfh_prec prec) { return (int)prec; }
+size_t elem_size(sfh_prec prec) { return prec == SFH_FP64 ? sizeof(double) : sizeof(float); }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+    const char *pa = (const char *)a, *pb = (const char *)b;
+    return pa < pb + nb && pb < pa + na;
+}
+
+cudaError_t launch_volume(sfh_ctx *c, sfh_prec prec, int64_t n_elem, const void *u, const double *Ja, void *r,
+                          cudaStream_t s) {
+    using namespace sfh;
+    if (prec == SFH_FP64)
+        return c->d == 3 ? volume_fp64_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_d, c->d_err, s)
+                         : volume_fp64_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_d, c->d_err, s);
+    if (prec == SFH_FP32_KAHAN)
+        return c->d == 3 ? volume_fp32k_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s)
+                         : volume_fp32k_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
+    return c->d == 3 ? volume_mixed_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s)
+                     : volume_mixed_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
+}
+
+}  // namespace
+
+extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_flux flux, sfh_ctx **out) {
+    clear_err();
+    if (!out) return fail(SFH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (d != 2 && d != 3) return fail(SFH_EINVAL, "d must be 2 or 3, got %d", d);
+    if (p < 1 || p > sfh::NMAX - 1) return fail(SFH_EINVAL, "p must be in [1, %d], got %d", sfh::NMAX - 1, p);
+    if (nodes != SFH_NODES_GLL && nodes != SFH_NODES_GAUSS) return fail(SFH_EINVAL, "bad node set %d", (int)nodes);
+    if (flux != SFH_FLUX_BURGERS && flux != SFH_FLUX_EULER_RANOCHA) return fail(SFH_EINVAL, "bad flux %d", (int)flux);
+    const int want = flux == SFH_FLUX_BURGERS ? 1 : d + 2;
+    if (nvar != want) return fail(SFH_EINVAL, "nvar must be %d for this flux and d = %d, got %d", want, d, nvar);
+
+    double xi[sfh::NMAX], w[sfh::NMAX], D[sfh::NMAX * sfh::NMAX], Q1[sfh::NMAX * sfh::NMAX];
+    sfh_status st = sfh_operator_tables(p, nodes, xi, w, D, Q1);
+    if (st != SFH_OK) return st;
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(SFH_EUNSUPPORTED, "no CUDA device: %s", cudaGetErrorString(e));
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+
+    sfh_ctx *c = new (std::nothrow) sfh_ctx();
+    if (!c) return fail(SFH_ENOMEM, "host allocation failed");
+    c->d = d; c->p = p; c->n = p + 1; c->nodes = nodes; c->nvar = nvar; c->flux = flux; c->device = dev;
+    c->hs[0] = c->hs[1] = nullptr;
+    c->stage[0] = c->stage[1] = nullptr;
+    c->stage_bytes = 0;
+    const int n = p + 1;
+    memset(&c->tab_d, 0, sizeof c->tab_d);
+    memset(&c->tab_f, 0, sizeof c->tab_f);
+    long double x[sfh::NMAX], ww[sfh::NMAX], DD[sfh::NMAX * sfh::NMAX];
+    make_tables(p, nodes, x, ww, DD);
+    for (int a = 0; a < n; ++a) {
+        c->tab_d.w[a] = (double)ww[a];
+        c->tab_f.w[a] = (float)ww[a];
+        for (int b = 0; b < n; ++b) {
+            const long double q = ww[a] * DD[a * n + b];
+            c->tab_d.Q1[a * n + b] = (double)q;
+            c->tab_f.Q1[a * n + b] = (float)q;
+        }
+    }
+    if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
+    if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) {
+        cudaFree(c->d_err); delete c; return cuda_fail(e, "cudaMemset(error word)");
+    }
+    *out = c;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_destroy(sfh_ctx *c) {
+    clear_err();
+    if (!c) return SFH_OK;
+    DeviceGuard g(c->device);
+    for (int k = 0; k < 2; ++k) {
+        if (c->hs[k]) { cudaStreamSynchronize(c->hs[k]); cudaStreamDestroy(c->hs[k]); }
+        if (c->stage[k]) cudaFree(c->stage[k]);
+    }
+    if (c->d_err) cudaFree(c->d_err);
+    delete c;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_ctx_info(const sfh_ctx *c, int *d, int *p, int *nodes, int *nvar, int *flux, int *n_nodes) {
+    clear_err();
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (d) *d = c->d;
+    if (p) *p = c->p;
+    if (nodes) *nodes = c->nodes;
+    if (nvar) *nvar = c->nvar;
+    if (flux) *flux = c->flux;
+    if (n_nodes) *n_nodes = sfh::ipow(c->n, c->d);
+    return SFH_OK;
+}
+
+static sfh_status check_common(const sfh_ctx *c, int64_t n_elem, const void *u, const double *Ja, const void *out,
+                               size_t esz) {
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (n_elem < 0) return fail(SFH_EINVAL, "n_elem must be >= 0, got %lld", (long long)n_elem);
+    if (n_elem == 0) return SFH_OK;
+    if (!u || !Ja || !out) return fail(SFH_EINVAL, "null array pointer");
+    if (((uintptr_t)u % esz) || ((uintptr_t)out % esz) || ((uintptr_t)Ja % sizeof(double)))
+        return fail(SFH_EINVAL, "misaligned array pointer");
+    const int64_t nn = sfh::ipow(c->n, c->d);
+    if (n_elem > (int64_t)1 << 40) return fail(SFH_EINVAL, "n_elem too large");
+    const size_t ub = (size_t)(n_elem * c->nvar * nn) * esz;
+    const size_t jb = (size_t)(n_elem * c->d * c->d * nn) * sizeof(double);
+    if (overlap(out, ub, u, ub) || overlap(out, ub, Ja, jb)) return fail(SFH_EINVAL, "output overlaps an input");
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_volume_residual(sfh_ctx *c, int64_t n_elem, const void *u, const double *Ja, void *r,
+                                          sfh_prec prec, sfh_stream_t stream) {
+    clear_err();
+    if (prec != SFH_FP64 && prec != SFH_FP32_KAHAN && prec != SFH_FP32_MIXED)
+        return fail(SFH_EINVAL, "bad precision mode %d", (int)prec);
+    sfh_status st = check_common(c, n_elem, u, Ja, r, elem_size(prec));
+    if (st != SFH_OK || n_elem == 0) return st;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    cudaError_t e = launch_volume(c, prec, n_elem, u, Ja, r, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "volume kernel launch");
+    (void)mode_of;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_vjp(sfh_ctx *c, int64_t n_elem, const double *u, const double *Ja, const double *lambda,
+                              double *grad_u, sfh_stream_t stream) {
+    clear_err();
+    sfh_status st = check_common(c, n_elem, u, Ja, grad_u, sizeof(double));
+    if (st != SFH_OK || n_elem == 0) return st;
+    if (!lambda) return fail(SFH_EINVAL, "lambda is NULL");
+    if ((uintptr_t)lambda % sizeof(double)) return fail(SFH_EINVAL, "misaligned lambda");
+    const size_t ub = (size_t)(n_elem * c->nvar * sfh::ipow(c->n, c->d)) * sizeof(double);
+    if (overlap(grad_u, ub, lambda, ub)) return fail(SFH_EINVAL, "grad_u overlaps lambda");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    cudaError_t e = c->d == 3 ? sfh::vjp_d3(c->n, c->flux, u, Ja, lambda, grad_u, n_elem, c->tab_d, c->d_err, (cudaStream_t)stream)
+                              : sfh::vjp_d2(c->n, c->flux, u, Ja, lambda, grad_u, n_elem, c->tab_d, c->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "vjp kernel launch");
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_check(sfh_ctx *c, sfh_stream_t stream) {
+    clear_err();
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int h = 0;
+    if ((e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "read error word");
+    if (h) {
+        if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "clear error word");
+        return fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state");
+    }
+    return SFH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// host-buffer pipeline: chunks alternate between two streams; on each stream
+// H2D(u, Ja) -> kernel -> D2H(r), so the copies of one chunk overlap the
+// kernel of the other.
+// ---------------------------------------------------------------------------
+extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const void *u_host,
+                                               const double *Ja_host, void *r_host, sfh_prec prec) {
+    clear_err();
+    if (prec != SFH_FP64 && prec != SFH_FP32_KAHAN && prec != SFH_FP32_MIXED)
+        return fail(SFH_EINVAL, "bad precision mode %d", (int)prec);
+    const size_t esz = elem_size(prec);
+    sfh_status st = check_common(c, n_elem, u_host, Ja_host, r_host, esz);
+    if (st != SFH_OK || n_elem == 0) return st;
+    std::lock_guard<std::mutex> lk(c->host_mu);
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    const size_t nn = (size_t)sfh::ipow(c->n, c->d);
+    const size_t ub_e = c->nvar * nn * esz, jb_e = (size_t)c->d * c->d * nn * sizeof(double);
+    const size_t per_elem = 2 * ub_e + jb_e;
+    int64_t chunk = std::max<int64_t>(64, (int64_t)((48u << 20) / per_elem));
+    chunk = std::min<int64_t>(chunk, n_elem);
+    const size_t need = (size_t)chunk * per_elem + 3 * 256;   // three 256-byte-aligned sub-buffers
+    cudaError_t e;
+    for (int k = 0; k < 2; ++k) {
+        if (!c->hs[k] && (e = cudaStreamCreateWithFlags(&c->hs[k], cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+    }
+    if (c->stage_bytes < need) {
+        for (int k = 0; k < 2; ++k) {
+            if (c->stage[k]) { cudaFree(c->stage[k]); c->stage[k] = nullptr; }
+        }
+        c->stage_bytes = 0;
+        for (int k = 0; k < 2; ++k)
+            if ((e = cudaMalloc(&c->stage[k], need)) != cudaSuccess) {
+                if (c->stage[0]) { cudaFree(c->stage[0]); c->stage[0] = nullptr; }
+                return fail(SFH_ENOMEM, "staging allocation of %zu bytes failed", need);
+            }
+        c->stage_bytes = need;
+    }
+    const char *uh = (const char *)u_host;
+    const char *jh = (const char *)Ja_host;
+    char *rh = (char *)r_host;
+    int64_t k = 0;
+    for (int64_t e0 = 0; e0 < n_elem; e0 += chunk, ++k) {
+        const int64_t ne = std::min<int64_t>(chunk, n_elem - e0);
+        const int b = (int)(k & 1);
+        cudaStream_t s = c->hs[b];
+        char *base = (char *)c->stage[b];
+        char *du = base;
+        char *dj = base + ((ne * ub_e + 255) / 256) * 256;
+        char *dr = dj + ((ne * jb_e + 255) / 256) * 256;
+        if ((e = cudaMemcpyAsync(du, uh + e0 * ub_e, ne * ub_e, cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(dj, jh + e0 * jb_e, ne * jb_e, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "host-to-device copy");
+        if ((e = launch_volume(c, prec, ne, du, (const double *)dj, dr, s)) != cudaSuccess) return cuda_fail(e, "volume kernel launch");
+        if ((e = cudaMemcpyAsync(rh + e0 * ub_e, dr, ne * ub_e, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "device-to-host copy");
+    }
+    for (int b = 0; b < 2; ++b)
+        if ((e = cudaStreamSynchronize(c->hs[b])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return sfh_check(c, c->hs[0]);
+}
+
+// ---------------------------------------------------------------------------
+// peak microbenchmarks: independent FMA chains per thread, every SM busy
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void fma_chain_kernel(T *out, int iters, T a, T b) {
+    T x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (T)(threadIdx.x + k);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = x[k] * a + b;   // contracted to one FMA
+    }
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += x[k];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+static sfh_status peak_impl(int iters, double *tflops, double *ms) {
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return cuda_fail(e, "attr");
+    const int threads = 256, blocks = sms * 8;
+    T *out = nullptr;
+    if ((e = cudaMalloc(&out, sizeof(T) * threads * blocks)) != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    fma_chain_kernel<T><<<blocks, threads>>>(out, iters / 8, (T)0.9999999, (T)1e-7);   // warm-up
+    cudaEventRecord(t0);
+    fma_chain_kernel<T><<<blocks, threads>>>(out, iters, (T)0.9999999, (T)1e-7);
+    cudaEventRecord(t1);
+    e = cudaEventSynchronize(t1);
+    float elapsed = 0.0f;
+    cudaEventElapsedTime(&elapsed, t0, t1);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    cudaFree(out);
+    if (e != cudaSuccess) return cuda_fail(e, "peak kernel");
+    const double fmas = (double)blocks * threads * iters * 8.0;
+    if (ms) *ms = elapsed;
+    if (tflops) *tflops = 2.0 * fmas / (elapsed * 1e-3) / 1e12;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_peak_fma(sfh_prec prec, double *tflops, double *ms) {
+    clear_err();
+    if (prec == SFH_FP64) return peak_impl<double>(1 << 12, tflops, ms);
+    if (prec == SFH_FP32_KAHAN) return peak_impl<float>(1 << 16, tflops, ms);
+    return fail(SFH_EINVAL, "prec must be SFH_FP64 or SFH_FP32_KAHAN");
+}

@@ -1,0 +1,185 @@
+// sfh_device.cuh -- device building blocks of libsfhad: element shapes,
+// logarithmic means, two-point fluxes and compensated sums.
+//
+// Notation follows Section 2 of arXiv 2306.11665: n = p + 1 nodes per
+// direction, element node i = a_0 + n a_1 + n^2 a_2 (x fastest), Q1 = W D the
+// weighted 1D derivative of Eq. 5, and omega_m(i) = prod_{k != m} w[a_k(i)]
+// the product of the diagonal factors in Eq. 3.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfh {
+
+constexpr int NMAX = 9;              // p <= 8
+constexpr double kGamma = 1.4;
+constexpr int kFluxBurgers = 0;
+constexpr int kFluxEuler = 1;
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// 1D operator table passed by value as a kernel parameter: compile-time
+// indices then become constant-bank operands of the arithmetic instructions.
+template <typename T>
+struct OpTab {
+    T Q1[NMAX * NMAX];   // packed n x n, row-major, Q1[a*n + b] = w_a D_ab
+    T w[NMAX];
+};
+
+// ---------------------------------------------------------------------------
+// Precision modes.
+//   T  : type of u, r and the flux arithmetic
+//   TJ : type in which the metric sum Ja(i) + Ja(j) is formed
+// ---------------------------------------------------------------------------
+struct ModeFP64 { using T = double; using TJ = double; static constexpr bool kahan = false; static constexpr bool mixed = false; };
+struct ModeFP32K { using T = float; using TJ = float; static constexpr bool kahan = true; static constexpr bool mixed = false; };
+struct ModeMixed { using T = float; using TJ = double; static constexpr bool kahan = true; static constexpr bool mixed = true; };
+
+// ---------------------------------------------------------------------------
+// Element shape and CTA geometry.  One CTA handles EPB consecutive elements;
+// in the line phase one thread owns one grid line of one element.
+// Shared memory per node: primitives (NP values of T), the residual
+// accumulator (NVAR of T), the metric row of the current direction (D of TJ)
+// and, for the mixed mode, an FP64 copy of beta = rho / p.
+// ---------------------------------------------------------------------------
+template <int D, int N, int FLUX, class M>
+struct Shape {
+    using T = typename M::T;
+    using TJ = typename M::TJ;
+    static constexpr int NN = ipow(N, D);
+    static constexpr int NLINE = ipow(N, D - 1);
+    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
+    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;   // rho, v[D], p, beta | u
+    static constexpr int NODE_BYTES = (int)sizeof(T) * (NP + NVAR) + (int)sizeof(TJ) * D
+                                      + ((M::mixed && FLUX == kFluxEuler) ? 8 : 0);
+    static constexpr int SMEM_BUDGET = 96 * 1024;
+    static constexpr int EPB_SMEM = SMEM_BUDGET / (NN * NODE_BYTES) > 0 ? SMEM_BUDGET / (NN * NODE_BYTES) : 1;
+    static constexpr int TARGET_LINES = NLINE >= 48 ? 256 : 128;
+    static constexpr int EPB_LINES = TARGET_LINES / NLINE > 0 ? TARGET_LINES / NLINE : 1;
+    static constexpr int EPB = EPB_SMEM < EPB_LINES ? EPB_SMEM : EPB_LINES;
+    static constexpr int THREADS = ((EPB * NLINE + 31) / 32) * 32;
+    static constexpr size_t SMEM = (size_t)EPB * NN * NODE_BYTES;
+};
+
+// ---------------------------------------------------------------------------
+// Logarithmic mean {a,b}_ln = (a - b) / (ln a - ln b), a, b > 0.
+// With s = a + b, t = (a - b)/s, u = t^2 (so 0 <= u < 1):
+//   ln a - ln b = 2 artanh(t) = 2 t sum_k u^k / (2k + 1),
+//   {a,b}_ln   = (s / 2) S(u),   S(u) = sqrt(u) / artanh(sqrt(u)),
+//   1/{a,b}_ln = (2 / s) P(u),   P(u) = sum_k u^k / (2k + 1).
+// The Taylor coefficients of S (1, -1/3, -4/45, -44/945, -428/14175, ...) come
+// from inverting the series of P.  Inside the band u < 1e-2 (|a-b| < 0.1 (a+b))
+// the truncated series below are accurate to the working precision (FP64:
+// 8 and 9 terms, next term < 2e-18; FP32: 4 terms, next term < 1e-9); outside
+// it the quotient uses the logarithm of the ratio, whose relative error is
+// then at most a few ulp / |ln(a/b)| <= a few ulp / 0.2.
+// ---------------------------------------------------------------------------
+constexpr double kLnBand = 1e-2;
+
+__device__ __forceinline__ double series_S(double u) {
+    return 1.0 + u * (-1.0 / 3.0 + u * (-4.0 / 45.0 + u * (-44.0 / 945.0 + u * (-428.0 / 14175.0
+           + u * (-10196.0 / 467775.0 + u * (-10719068.0 / 638512875.0 + u * (-25865068.0 / 1915538625.0)))))));
+}
+__device__ __forceinline__ double series_dS(double u) {   // S'(u)
+    return -1.0 / 3.0 + u * (2.0 * -4.0 / 45.0 + u * (3.0 * -44.0 / 945.0 + u * (4.0 * -428.0 / 14175.0
+           + u * (5.0 * -10196.0 / 467775.0 + u * (6.0 * -10719068.0 / 638512875.0
+           + u * (7.0 * -25865068.0 / 1915538625.0))))));
+}
+__device__ __forceinline__ double series_P(double u) {
+    return 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0 + u * (1.0 / 9.0 + u * (1.0 / 11.0
+           + u * (1.0 / 13.0 + u * (1.0 / 15.0 + u * (1.0 / 17.0))))))));
+}
+__device__ __forceinline__ float series_S(float u) {
+    return 1.0f + u * (-1.0f / 3.0f + u * (-4.0f / 45.0f + u * (-44.0f / 945.0f)));
+}
+__device__ __forceinline__ float series_P(float u) {
+    return 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
+}
+
+__device__ __forceinline__ double ln_mean(double a, double b) {
+    const double d = a - b, s = a + b;
+    if (d * d < kLnBand * (s * s)) {
+        const double t = d / s;
+        return 0.5 * s * series_S(t * t);
+    }
+    return d / log(a / b);
+}
+__device__ __forceinline__ double inv_ln_mean(double a, double b) {
+    const double d = a - b, s = a + b;
+    if (d * d < kLnBand * (s * s)) {
+        const double rs = 1.0 / s;
+        const double t = d * rs;
+        return 2.0 * rs * series_P(t * t);
+    }
+    return log(a / b) / d;
+}
+__device__ __forceinline__ float ln_mean(float a, float b) {
+    const float d = a - b, s = a + b;
+    if (d * d < (float)kLnBand * (s * s)) {
+        const float t = __fdividef(d, s);
+        return 0.5f * s * series_S(t * t);
+    }
+    return __fdividef(d, logf(__fdividef(a, b)));
+}
+__device__ __forceinline__ float inv_ln_mean(float a, float b) {
+    const float d = a - b, s = a + b;
+    if (d * d < (float)kLnBand * (s * s)) {
+        const float rs = __fdividef(1.0f, s);
+        const float t = d * rs;
+        return 2.0f * rs * series_P(t * t);
+    }
+    return __fdividef(logf(__fdividef(a, b)), d);
+}
+
+// Value and both partial derivatives of {a,b}_ln (FP64, for the adjoint).
+// Band: L = (s/2) S(u), du/da = 4 t b / s^2, du/db = -4 t a / s^2, so
+//   dL/da = S/2 + 2 t b S'(u) / s,  dL/db = S/2 - 2 t a S'(u) / s.
+// Outside: dL/da = (1 - L/a) / ln(a/b),  dL/db = (L/b - 1) / ln(a/b).
+__device__ __forceinline__ void ln_mean_grad(double a, double b, double &L, double &La, double &Lb) {
+    const double d = a - b, s = a + b;
+    if (d * d < kLnBand * (s * s)) {
+        const double rs = 1.0 / s;
+        const double t = d * rs, u = t * t;
+        const double S = series_S(u), dS = series_dS(u);
+        L = 0.5 * s * S;
+        La = 0.5 * S + 2.0 * t * b * dS * rs;
+        Lb = 0.5 * S - 2.0 * t * a * dS * rs;
+    } else {
+        const double lr = log(a / b);
+        L = d / lr;
+        La = (1.0 - L / a) / lr;
+        Lb = (L / b - 1.0) / lr;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Compensated (Kahan) accumulation.  Every step is an explicitly rounded
+// intrinsic so the compiler can neither contract nor reassociate it away:
+//   y = q*f - c (one rounding, fused), t = s + y, c = (t - s) - y, s = t.
+// The represented value is s - c.
+// ---------------------------------------------------------------------------
+struct KahanF {
+    float s, c;
+    __device__ __forceinline__ void zero() { s = 0.0f; c = 0.0f; }
+    __device__ __forceinline__ void add_prod(float q, float f) {
+        const float y = __fmaf_rn(q, f, -c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ float value() const { return __fsub_rn(s, c); }
+};
+
+struct PlainD {
+    double s;
+    __device__ __forceinline__ void zero() { s = 0.0; }
+    __device__ __forceinline__ void add_prod(double q, double f) { s = fma(q, f, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <class M> struct AccOf { using type = PlainD; };
+template <> struct AccOf<ModeFP32K> { using type = KahanF; };
+template <> struct AccOf<ModeMixed> { using type = KahanF; };
+
+}  // namespace sfh

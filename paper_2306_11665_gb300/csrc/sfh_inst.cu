@@ -1,0 +1,66 @@
+// sfh_inst.cu -- kernel instantiation unit.  Compiled once per (mode, d):
+//   -DSFH_INST_D=<2|3> and one of -DSFH_INST_FP64 / -DSFH_INST_FP32K /
+//   -DSFH_INST_MIXED / -DSFH_INST_VJP.
+// Splitting the instances over several objects keeps the build parallel.
+#include "sfh_internal.h"
+#include "sfh_volume.cuh"
+#include "sfh_vjp.cuh"
+
+#ifndef SFH_INST_D
+#error "SFH_INST_D must be defined"
+#endif
+
+#define SFH_CAT2(a, b) a##b
+#define SFH_CAT(a, b) SFH_CAT2(a, b)
+
+namespace sfh {
+
+#if defined(SFH_INST_VJP)
+
+cudaError_t SFH_CAT(vjp_d, SFH_INST_D)(int n, int flux, const double *u, const double *Ja,
+                                       const double *lam, double *g, int64_t n_elem,
+                                       const OpTab<double> &tab, int *err, cudaStream_t stream) {
+    constexpr int D = SFH_INST_D;
+#define SFH_CASE(N)                                                                                     \
+    case N:                                                                                             \
+        return flux == kFluxEuler ? launch_vjp<D, N, kFluxEuler>(u, Ja, lam, g, n_elem, tab, err, stream) \
+                                  : launch_vjp<D, N, kFluxBurgers>(u, Ja, lam, g, n_elem, tab, err, stream);
+    switch (n) {
+        SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SFH_CASE
+}
+
+#else
+
+#if defined(SFH_INST_FP64)
+using Mode = ModeFP64;
+#define SFH_FN SFH_CAT(volume_fp64_d, SFH_INST_D)
+#elif defined(SFH_INST_FP32K)
+using Mode = ModeFP32K;
+#define SFH_FN SFH_CAT(volume_fp32k_d, SFH_INST_D)
+#elif defined(SFH_INST_MIXED)
+using Mode = ModeMixed;
+#define SFH_FN SFH_CAT(volume_mixed_d, SFH_INST_D)
+#else
+#error "no instantiation mode"
+#endif
+
+cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,
+                   const OpTab<typename Mode::T> &tab, int *err, cudaStream_t stream) {
+    constexpr int D = SFH_INST_D;
+#define SFH_CASE(N)                                                                                              \
+    case N:                                                                                                      \
+        return flux == kFluxEuler ? launch_volume<D, N, kFluxEuler, Mode>(u, Ja, r, n_elem, tab, err, stream)     \
+                                  : launch_volume<D, N, kFluxBurgers, Mode>(u, Ja, r, n_elem, tab, err, stream);
+    switch (n) {
+        SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SFH_CASE
+}
+
+#endif
+
+}  // namespace sfh

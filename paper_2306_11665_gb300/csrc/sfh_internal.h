@@ -1,0 +1,36 @@
+// sfh_internal.h -- declarations shared by the host API and the kernel
+// instantiation units of libsfhad (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sfh_device.cuh"
+
+namespace sfh {
+
+// One entry point per (precision mode, dimension) instantiation unit; each
+// dispatches on n = p + 1 (2..9) and the flux.
+#define SFH_DECL_VOLUME(name, T)                                                                   \
+    cudaError_t name(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,     \
+                     const OpTab<T> &tab, int *err, cudaStream_t stream);
+SFH_DECL_VOLUME(volume_fp64_d2, double)
+SFH_DECL_VOLUME(volume_fp64_d3, double)
+SFH_DECL_VOLUME(volume_fp32k_d2, float)
+SFH_DECL_VOLUME(volume_fp32k_d3, float)
+SFH_DECL_VOLUME(volume_mixed_d2, float)
+SFH_DECL_VOLUME(volume_mixed_d3, float)
+#undef SFH_DECL_VOLUME
+
+#define SFH_DECL_VJP(name)                                                                          \
+    cudaError_t name(int n, int flux, const double *u, const double *Ja, const double *lam, double *g, \
+                     int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);
+SFH_DECL_VJP(vjp_d2)
+SFH_DECL_VJP(vjp_d3)
+#undef SFH_DECL_VJP
+
+// Elements per CTA of the forward kernel for a (d, n, flux, mode): the unit
+// in which the serving runtime cuts requests into tiles.
+int volume_epb(int mode, int d, int n, int flux);
+
+}  // namespace sfh

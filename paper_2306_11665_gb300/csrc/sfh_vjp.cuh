@@ -1,0 +1,238 @@
+// sfh_vjp.cuh -- adjoint of the volume residual (FP64).
+//
+// From r_i = sum_m sum_j Q_m,ij F_m(u_i, u_j) (Eq. 3) with F_m symmetric in
+// its two states, the cotangent lambda pulls back to
+//   g_l = sum_m sum_{j on the m-line of l} c_lj^T d1F_m(u_l, u_j),
+//   c_lj = Q_m,lj lambda_l + Q_m,jl lambda_j   (= c_jl),
+// so each unordered line pair (a, b) needs the gradient of the single scalar
+// phi = c_ab^T F(u_a, u_b) with respect to both states.  The kernel evaluates
+// it in reverse mode through the flux formula, accumulates the adjoints of
+// the node primitives (rho, v, p, beta) in shared memory over all pairs and
+// directions, and applies the primitive -> conservative chain rule once per
+// node at the end.  Q_m,ab = omega Q1[a][b] with omega constant on the line,
+// so lambda is pre-scaled by omega.
+#pragma once
+
+#include "sfh_device.cuh"
+
+namespace sfh {
+
+template <int D, int N, int FLUX>
+struct VjpShape {
+    static constexpr int NN = ipow(N, D);
+    static constexpr int NLINE = ipow(N, D - 1);
+    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
+    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;
+    static constexpr int NODE_BYTES = 8 * (2 * NP + NVAR + D);
+    static constexpr int EPB_SMEM = (96 * 1024) / (NN * NODE_BYTES) > 0 ? (96 * 1024) / (NN * NODE_BYTES) : 1;
+    static constexpr int EPB_LINES = 128 / NLINE > 0 ? 128 / NLINE : 1;
+    static constexpr int EPB = EPB_SMEM < EPB_LINES ? EPB_SMEM : EPB_LINES;
+    static constexpr int THREADS = ((EPB * NLINE + 31) / 32) * 32;
+    static constexpr size_t SMEM = (size_t)EPB * NN * NODE_BYTES;
+};
+
+// Reverse mode of the contracted Ranocha flux: adds d(c^T F)/d(prim) of both
+// states.  prim order: rho, v[0..D-1], p, beta.
+template <int D>
+__device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *PB, const double *n,
+                                               const double *c, double *ga, double *gb) {
+    const double ra = PA[0], rb = PB[0], pa = PA[D + 1], pb = PB[D + 1];
+    double vna = 0.0, vnb = 0.0, vv = 0.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) { vna += PA[1 + k] * n[k]; vnb += PB[1 + k] * n[k]; vv += PA[1 + k] * PB[1 + k]; }
+    double Lr, Lra, Lrb, Lb, Lba, Lbb;
+    ln_mean_grad(ra, rb, Lr, Lra, Lrb);
+    ln_mean_grad(PA[D + 2], PB[D + 2], Lb, Lba, Lbb);
+    const double iLb = 1.0 / Lb;
+    const double h = 0.5 * (vna + vnb);
+    const double frho = Lr * h;
+    const double K = 0.5 * vv + iLb * (1.0 / (kGamma - 1.0));
+    const double cE = c[D + 1];
+    double frho_bar = c[0] + cE * K, pavg_bar = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        const double vavg = 0.5 * (PA[1 + l] + PB[1 + l]);
+        frho_bar += c[1 + l] * vavg;
+        pavg_bar += c[1 + l] * n[l];
+        const double vavg_bar = c[1 + l] * frho;
+        ga[1 + l] += 0.5 * vavg_bar;
+        gb[1 + l] += 0.5 * vavg_bar;
+    }
+    const double K_bar = cE * frho;
+    const double Lr_bar = frho_bar * h, h_bar = frho_bar * Lr;
+    const double vna_bar = 0.5 * cE * pb + 0.5 * h_bar;
+    const double vnb_bar = 0.5 * cE * pa + 0.5 * h_bar;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        ga[1 + k] += 0.5 * K_bar * PB[1 + k] + vna_bar * n[k];
+        gb[1 + k] += 0.5 * K_bar * PA[1 + k] + vnb_bar * n[k];
+    }
+    ga[D + 1] += 0.5 * pavg_bar + 0.5 * cE * vnb;
+    gb[D + 1] += 0.5 * pavg_bar + 0.5 * cE * vna;
+    ga[0] += Lr_bar * Lra;
+    gb[0] += Lr_bar * Lrb;
+    const double Lb_bar = -(K_bar * (1.0 / (kGamma - 1.0))) * iLb * iLb;
+    ga[D + 2] += Lb_bar * Lba;
+    gb[D + 2] += Lb_bar * Lbb;
+}
+
+template <int D, int N, int FLUX>
+__global__ void __launch_bounds__(VjpShape<D, N, FLUX>::THREADS)
+vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const double *__restrict__ lam,
+           double *__restrict__ g, int64_t n_elem, const __grid_constant__ OpTab<double> tab,
+           int *__restrict__ err) {
+    using S = VjpShape<D, N, FLUX>;
+    constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *sP = reinterpret_cast<double *>(smem_raw);   // [EPB][NP][NN]
+    double *sA = sP + EPB * NP * NN;                       // [EPB][NP][NN] adjoints of primitives
+    double *sL = sA + EPB * NP * NN;                       // [EPB][NVAR][NN] lambda
+    double *sJ = sL + EPB * NVAR * NN;                     // [EPB][D][NN]
+
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int ne = (int)((n_elem - e0) < EPB ? (n_elem - e0) : EPB);
+    const double *ub = u + e0 * NVAR * NN;
+    const double *lb = lam + e0 * NVAR * NN;
+
+    bool bad = false;
+    for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
+        const int el = s / NN, i = s - el * NN;
+        const double *ue = ub + (int64_t)el * NVAR * NN + i;
+        double *pe = sP + el * NP * NN + i;
+        if constexpr (FLUX == kFluxEuler) {
+            const double rho = ue[0], E = ue[(D + 1) * NN], irho = 1.0 / rho;
+            double ke = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double mk = ue[(1 + k) * NN], vk = mk * irho;
+                pe[(1 + k) * NN] = vk;
+                ke += mk * vk;
+            }
+            const double p = (kGamma - 1.0) * (E - 0.5 * ke);
+            pe[0] = rho;
+            pe[(D + 1) * NN] = p;
+            pe[(D + 2) * NN] = rho / p;
+            bad |= !(rho > 0.0 && p > 0.0);
+        } else {
+            pe[0] = ue[0];
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) sA[(el * NP + q) * NN + i] = 0.0;
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) sL[(el * NVAR + v) * NN + i] = lb[((int64_t)el * NVAR + v) * NN + i];
+    }
+    if (bad) atomicOr(err, 1);
+
+    const double *Jb = Ja + e0 * D * D * NN;
+#pragma unroll 1
+    for (int m = 0; m < D; ++m) {
+        __syncthreads();
+        for (int s = threadIdx.x; s < ne * D * NN; s += blockDim.x) {
+            const int el = s / (D * NN), rem = s - el * D * NN;
+            sJ[s] = Jb[((int64_t)el * D * D + m * D) * NN + rem];
+        }
+        __syncthreads();
+        const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
+        for (int L = threadIdx.x; L < ne * NLINE; L += blockDim.x) {
+            const int el = L / NLINE, l = L - el * NLINE;
+            int base;
+            double omega;
+            if constexpr (D == 3) {
+                const int o0 = l % N, o1 = l / N;
+                base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
+                omega = tab.w[o0] * tab.w[o1];
+            } else {
+                base = m == 0 ? N * l : l;
+                omega = tab.w[l];
+            }
+#pragma unroll 1
+            for (int a = 0; a < N; ++a) {
+                const int ia = base + a * stride;
+                double PA[NP], JA[D], LA[NVAR], GA[NP];
+#pragma unroll
+                for (int q = 0; q < NP; ++q) { PA[q] = sP[(el * NP + q) * NN + ia]; GA[q] = 0.0; }
+#pragma unroll
+                for (int k = 0; k < D; ++k) JA[k] = sJ[(el * D + k) * NN + ia];
+#pragma unroll
+                for (int v = 0; v < NVAR; ++v) LA[v] = omega * sL[(el * NVAR + v) * NN + ia];
+#pragma unroll 1
+                for (int b = a; b < N; ++b) {
+                    const int ib = base + b * stride;
+                    const double qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
+                    if (b == a && qab == 0.0) continue;
+                    double PB[NP], n[D], c[NVAR], GB[NP];
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) { PB[q] = sP[(el * NP + q) * NN + ib]; GB[q] = 0.0; }
+#pragma unroll
+                    for (int k = 0; k < D; ++k) n[k] = JA[k] + sJ[(el * D + k) * NN + ib];
+                    if (b == a) {
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) c[v] = qab * LA[v];
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) c[v] = qab * LA[v] + qba * (omega * sL[(el * NVAR + v) * NN + ib]);
+                    }
+                    if constexpr (FLUX == kFluxEuler) {
+                        euler_pair_vjp<D>(PA, PB, n, c, GA, GB);
+                    } else {
+                        double S = 0.0;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) S += n[k];
+                        GA[0] += c[0] * (2.0 * PA[0] + PB[0]) * (1.0 / 6.0) * S;
+                        GB[0] += c[0] * (PA[0] + 2.0 * PB[0]) * (1.0 / 6.0) * S;
+                    }
+                    // the diagonal pair depends on u_a through both arguments
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) sA[(el * NP + q) * NN + ib] += GB[q];
+                }
+#pragma unroll
+                for (int q = 0; q < NP; ++q) sA[(el * NP + q) * NN + ia] += GA[q];
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. primitive adjoints -> conservative adjoints; write g
+    double *gbp = g + e0 * NVAR * NN;
+    for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
+        const int el = s / NN, i = s - el * NN;
+        const double *pe = sP + el * NP * NN + i;
+        const double *ae = sA + el * NP * NN + i;
+        double *ge = gbp + (int64_t)el * NVAR * NN + i;
+        if constexpr (FLUX == kFluxEuler) {
+            const double rho = pe[0], p = pe[(D + 1) * NN];
+            const double bbar = ae[(D + 2) * NN];
+            const double rbar = ae[0] + bbar / p;
+            const double pbar = ae[(D + 1) * NN] - bbar * rho / (p * p);
+            double g0 = rbar, v2 = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const double vk = pe[(1 + k) * NN], vbar = ae[(1 + k) * NN];
+                g0 -= vbar * vk / rho;
+                v2 += vk * vk;
+                ge[(1 + k) * NN] = vbar / rho - pbar * (kGamma - 1.0) * vk;
+            }
+            ge[0] = g0 + pbar * (kGamma - 1.0) * 0.5 * v2;
+            ge[(D + 1) * NN] = pbar * (kGamma - 1.0);
+        } else {
+            ge[0] = ae[0];
+        }
+    }
+}
+
+template <int D, int N, int FLUX>
+cudaError_t launch_vjp(const double *u, const double *Ja, const double *lam, double *g, int64_t n_elem,
+                       const OpTab<double> &tab, int *err, cudaStream_t stream) {
+    using S = VjpShape<D, N, FLUX>;
+    auto kern = vjp_kernel<D, N, FLUX>;
+    static_assert(S::SMEM <= 227 * 1024, "shared memory");
+    if (S::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (n_elem + S::EPB - 1) / S::EPB;
+    kern<<<(unsigned)blocks, S::THREADS, S::SMEM, stream>>>(u, Ja, lam, g, n_elem, tab, err);
+    return cudaGetLastError();
+}
+
+}  // namespace sfh

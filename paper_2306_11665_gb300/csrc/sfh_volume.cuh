@@ -1,0 +1,272 @@
+// sfh_volume.cuh -- the volume-residual kernel (forward), all precisions.
+//
+// r_i = sum_m omega_m(i) sum_{j on the m-line of i} Q1[a_m(i)][a_m(j)] F_m(u_i, u_j),
+// F_m(u_i, u_j) = sum_k fsharp_k(u_i, u_j) (Ja^m_k(i) + Ja^m_k(j)),
+// i.e. Eq. 3 with the Eq. 5 operators: per element and direction, n^{d-1}
+// independent lines, each a dense n x n Hadamard product of Q1 with the line's
+// two-point-flux matrix.  The paper stores both factors as n^d x n arrays
+// (its sparsity-pattern and basis-assembly listings); here neither is stored:
+// the pattern is index arithmetic, the basis entry is a kernel-parameter
+// constant, and the flux matrix lives in registers for one line at a time.
+//
+// Work decomposition (one CTA = EPB consecutive elements):
+//   1. stage: every node's conservative state -> primitives (rho, v, p,
+//      beta = rho/p) in shared memory, coalesced global reads; domain check;
+//   2. for each direction m: stage the metric row Ja^m of every node, then
+//      one thread per grid line loads its n nodes into registers and forms
+//      each unordered pair's flux once (F is symmetric), adding Q1[a][b] F to
+//      node a and Q1[b][a] F to node b; diagonal terms only where Q1[a][a] != 0;
+//      the line sums are scaled by omega (constant along the line) and added
+//      to the node's residual in shared memory;
+//   3. write r with coalesced stores.
+#pragma once
+
+#include "sfh_device.cuh"
+
+namespace sfh {
+
+template <typename T, typename TJ, int D>
+struct EulerNode {
+    T rho, v[D], p, beta;
+    TJ J[D];
+    double beta_d;   // mixed mode only (FP64 copy of rho / p)
+};
+
+template <typename T, typename TJ, int D>
+struct BurgersNode {
+    T u;
+    TJ S;            // sum_k Ja^m_k
+};
+
+// Two-point Euler flux contracted with n = Ja^m(a) + Ja^m(b) (Ranocha).
+template <class M, int D>
+__device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
+                                                const EulerNode<typename M::T, typename M::TJ, D> &B,
+                                                typename M::T F[D + 2]) {
+    using T = typename M::T;
+    T n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = (T)(A.J[k] + B.J[k]);   // TJ sum, then rounded to T
+    T vna = A.v[0] * n[0], vnb = B.v[0] * n[0], vv = A.v[0] * B.v[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) { vna += A.v[k] * n[k]; vnb += B.v[k] * n[k]; vv += A.v[k] * B.v[k]; }
+    T Lr, iLb;
+    if constexpr (M::mixed) {
+        // FP64 logarithmic mean inside the near-equal band, FP32 outside
+        const float dr = A.rho - B.rho, sr = A.rho + B.rho;
+        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = (float)ln_mean((double)A.rho, (double)B.rho);
+        else Lr = ln_mean(A.rho, B.rho);
+        const float db = A.beta - B.beta, sb = A.beta + B.beta;
+        if (db * db < (float)kLnBand * (sb * sb)) iLb = (float)inv_ln_mean(A.beta_d, B.beta_d);
+        else iLb = inv_ln_mean(A.beta, B.beta);
+    } else {
+        Lr = ln_mean(A.rho, B.rho);
+        iLb = inv_ln_mean(A.beta, B.beta);
+    }
+    const T half = (T)0.5;
+    const T frho = Lr * (half * (vna + vnb));
+    const T pavg = half * (A.p + B.p);
+    F[0] = frho;
+#pragma unroll
+    for (int l = 0; l < D; ++l) F[1 + l] = frho * (half * (A.v[l] + B.v[l])) + pavg * n[l];
+    F[D + 1] = frho * (half * vv + iLb * (T)(1.0 / (kGamma - 1.0))) + half * (A.p * vnb + B.p * vna);
+}
+
+// Physical Euler flux f(u_a) . (2 Ja^m(a)) = the two-point flux at (u_a, u_a).
+template <class M, int D>
+__device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
+                                                typename M::T F[D + 2]) {
+    using T = typename M::T;
+    T n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = (T)(A.J[k] + A.J[k]);
+    T vn = A.v[0] * n[0], v2 = A.v[0] * A.v[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) { vn += A.v[k] * n[k]; v2 += A.v[k] * A.v[k]; }
+    const T frho = A.rho * vn;
+    F[0] = frho;
+#pragma unroll
+    for (int l = 0; l < D; ++l) F[1 + l] = frho * A.v[l] + A.p * n[l];
+    // (E + p) v.n = rho v.n (|v|^2/2 + p/((gamma-1) rho)) + p v.n
+    F[D + 1] = frho * ((T)0.5 * v2) + A.p * vn * (T)(kGamma / (kGamma - 1.0));
+}
+
+template <int D, int N, int FLUX, class M>
+__global__ void __launch_bounds__(Shape<D, N, FLUX, M>::THREADS)
+volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
+              typename M::T *__restrict__ r, int64_t n_elem,
+              const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err) {
+    using S = Shape<D, N, FLUX, M>;
+    using T = typename M::T;
+    using TJ = typename M::TJ;
+    using Acc = typename AccOf<M>::type;
+    constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // layout: [beta_d (mixed)] [J: EPB][D][NN] TJ  [P: EPB][NP][NN] T  [R: EPB][NVAR][NN] T
+    double *sBd = reinterpret_cast<double *>(smem_raw);
+    constexpr int BD_COUNT = (M::mixed && FLUX == kFluxEuler) ? EPB * NN : 0;
+    TJ *sJ = reinterpret_cast<TJ *>(smem_raw + sizeof(double) * BD_COUNT);
+    T *sP = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sJ) + sizeof(TJ) * EPB * D * NN);
+    T *sR = sP + EPB * NP * NN;
+
+    const int64_t e0 = (int64_t)blockIdx.x * EPB;
+    const int ne = (int)((n_elem - e0) < EPB ? (n_elem - e0) : EPB);
+    const T *ub = u + e0 * NVAR * NN;
+
+    // ---- 1. stage primitives, zero the residual
+    bool bad = false;
+    for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
+        const int el = s / NN, i = s - el * NN;
+        const T *ue = ub + (int64_t)el * NVAR * NN + i;
+        T *pe = sP + el * NP * NN + i;
+        if constexpr (FLUX == kFluxEuler) {
+            const T rho = ue[0];
+            const T E = ue[(D + 1) * NN];
+            const T irho = (T)1 / rho;
+            T ke = (T)0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const T mk = ue[(1 + k) * NN];
+                const T vk = mk * irho;
+                pe[(1 + k) * NN] = vk;
+                ke += mk * vk;
+            }
+            const T p = (T)(kGamma - 1.0) * (E - (T)0.5 * ke);
+            pe[0] = rho;
+            pe[(D + 1) * NN] = p;
+            pe[(D + 2) * NN] = rho / p;
+            if constexpr (M::mixed) sBd[el * NN + i] = (double)rho / (double)p;
+            bad |= !(rho > (T)0 && p > (T)0);
+        } else {
+            pe[0] = ue[0];
+        }
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) sR[(el * NVAR + v) * NN + i] = (T)0;
+    }
+    if (bad) atomicOr(err, 1);
+
+    const double *Jb = Ja + e0 * D * D * NN;
+#pragma unroll 1
+    for (int m = 0; m < D; ++m) {
+        // ---- 2a. stage the metric row of direction m: Ja[e][m][k][i] -> sJ[el][k][i]
+        __syncthreads();
+        for (int s = threadIdx.x; s < ne * D * NN; s += blockDim.x) {
+            const int el = s / (D * NN), rem = s - el * D * NN;
+            sJ[s] = (TJ)Jb[((int64_t)el * D * D + m * D) * NN + rem];
+        }
+        __syncthreads();
+
+        // ---- 2b. line sweeps
+        const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
+        for (int L = threadIdx.x; L < ne * NLINE; L += blockDim.x) {
+            const int el = L / NLINE, l = L - el * NLINE;
+            int base;
+            T omega;
+            if constexpr (D == 3) {
+                const int o0 = l % N, o1 = l / N;   // the two other indices, lower axis first
+                base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
+                omega = tab.w[o0] * tab.w[o1];
+            } else {
+                base = m == 0 ? N * l : l;
+                omega = tab.w[l];
+            }
+            const int nb = el * NN + base;
+
+            Acc acc[N][NVAR];
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int v = 0; v < NVAR; ++v) acc[a][v].zero();
+
+            if constexpr (FLUX == kFluxEuler) {
+                EulerNode<T, TJ, D> nd[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    const int i = nb + a * stride;
+                    const T *pe = sP + el * NP * NN + (base + a * stride);
+                    nd[a].rho = pe[0];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) nd[a].v[k] = pe[(1 + k) * NN];
+                    nd[a].p = pe[(D + 1) * NN];
+                    nd[a].beta = pe[(D + 2) * NN];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) nd[a].J[k] = sJ[(el * D + k) * NN + base + a * stride];
+                    if constexpr (M::mixed) nd[a].beta_d = sBd[i];
+                    else nd[a].beta_d = 0.0;
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < N; ++b) {
+                        T F[D + 2];
+                        euler_pair_flux<M, D>(nd[a], nd[b], F);
+                        const T qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) { acc[a][v].add_prod(qab, F[v]); acc[b][v].add_prod(qba, F[v]); }
+                    }
+                    const T qaa = tab.Q1[a * N + a];
+                    if (qaa != (T)0) {
+                        T F[D + 2];
+                        euler_diag_flux<M, D>(nd[a], F);
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) acc[a][v].add_prod(qaa, F[v]);
+                    }
+                }
+            } else {
+                BurgersNode<T, TJ, D> nd[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    nd[a].u = sP[el * NN + base + a * stride];
+                    TJ S = sJ[(el * D + 0) * NN + base + a * stride];
+#pragma unroll
+                    for (int k = 1; k < D; ++k) S += sJ[(el * D + k) * NN + base + a * stride];
+                    nd[a].S = S;
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < N; ++b) {
+                        const T ua = nd[a].u, ub2 = nd[b].u;
+                        const T F = (ua * ua + ua * ub2 + ub2 * ub2) * (T)(1.0 / 6.0) * (T)(nd[a].S + nd[b].S);
+                        acc[a][0].add_prod(tab.Q1[a * N + b], F);
+                        acc[b][0].add_prod(tab.Q1[b * N + a], F);
+                    }
+                    const T qaa = tab.Q1[a * N + a];
+                    if (qaa != (T)0) {
+                        const T ua = nd[a].u;
+                        acc[a][0].add_prod(qaa, ua * ua * (T)nd[a].S);
+                    }
+                }
+            }
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int v = 0; v < NVAR; ++v) sR[(el * NVAR + v) * NN + base + a * stride] += omega * acc[a][v].value();
+        }
+    }
+    __syncthreads();
+
+    // ---- 3. write r (layout [el][v][i] matches the global layout)
+    T *rb = r + e0 * NVAR * NN;
+    for (int s = threadIdx.x; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
+}
+
+// Host-side launcher for one (D, N, FLUX, mode) instance.
+template <int D, int N, int FLUX, class M>
+cudaError_t launch_volume(const void *u, const double *Ja, void *r, int64_t n_elem,
+                          const OpTab<typename M::T> &tab, int *err, cudaStream_t stream) {
+    using S = Shape<D, N, FLUX, M>;
+    auto kern = volume_kernel<D, N, FLUX, M>;
+    static_assert(S::SMEM <= 227 * 1024, "shared memory");
+    if (S::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (n_elem + S::EPB - 1) / S::EPB;
+    kern<<<(unsigned)blocks, S::THREADS, S::SMEM, stream>>>(
+        static_cast<const typename M::T *>(u), Ja, static_cast<typename M::T *>(r), n_elem, tab, err);
+    return cudaGetLastError();
+}
+
+}  // namespace sfh

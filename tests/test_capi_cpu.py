@@ -1,0 +1,70 @@
+"""The C-ABI library on the CPU: it loads, exports every symbol the header
+declares, computes its operator tables on the host (checked against the
+oracle's independent construction) and rejects bad arguments before touching
+a device."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from tests._helpers import ROOT, header_functions
+
+
+@pytest.fixture(scope="module")
+def A():
+    from paper_2306_11665_gb300 import build
+    build.build()
+    from paper_2306_11665_gb300 import _abi
+    return _abi
+
+
+def test_exports_every_header_symbol(A):
+    names = header_functions()
+    assert len(names) >= 16
+    lib = ctypes.CDLL(A.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding wraps each of them under the same name
+    for n in names:
+        assert hasattr(A, n), n
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_operator_tables_vs_oracle(A, kind, p):
+    xi, w, D, Q1 = A.sfh_operator_tables(p, kind)
+    oxi, ow, oD, oQ1 = O.op1d(p, kind)
+    assert np.abs(xi - oxi).max() < 2e-16
+    assert np.abs(w - ow).max() < 1e-15
+    assert np.abs(D - oD).max() < 1e-14 * max(1, np.abs(oD).max())
+    assert np.abs(Q1 - oQ1).max() < 1e-15 * max(1, np.abs(oQ1).max())
+    # exact symmetry of the node set
+    assert np.array_equal(xi, -xi[::-1])
+
+
+def test_bad_arguments_rejected(A):
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_create(4, 3, 0, 6, 1)
+    assert e.value.status == A.SFH_EINVAL
+    for args in [(3, 0, 0, 5, 1), (3, 9, 0, 5, 1), (3, 3, 2, 5, 1), (3, 3, 0, 4, 1), (2, 3, 0, 2, 0), (3, 3, 0, 5, 7)]:
+        with pytest.raises(A.SfhError) as e:
+            A.sfh_create(*args)
+        assert e.value.status == A.SFH_EINVAL, args
+        assert A.sfh_last_error()
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual(0, 10, 1, 1, 1, 0, 0)
+    assert e.value.status == A.SFH_EINVAL
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_operator_tables(0, 0)
+    assert e.value.status == A.SFH_EINVAL
+
+
+def test_no_device_is_reported_not_crashed(A):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a device is present")
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_create(3, 4, 0, 5, 1)
+    assert e.value.status in (A.SFH_EUNSUPPORTED, A.SFH_ECUDA)

@@ -1,0 +1,201 @@
+"""GPU parity of sfh_volume_residual against the FP64 oracle.
+
+Bars (relative, max norm, per variable, worst variable):
+  FP64 1e-12; FP32 modes 2e-5 against the oracle on the FP64 state;
+  entropy identity 1e-10 (FP64) and 1e-4 (FP32).
+Small cases span several CTAs and a ragged tail; the full-size workloads
+(3D Euler p=4 Gauss-Lobatto 32^3, p=7 Gauss 16^3) are checked on sampled
+elements the oracle recomputes one by one, in the launch configuration the
+benchmark times.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2306_11665_gb300 import _abi as A
+from paper_2306_11665_gb300 import api
+from paper_2306_11665_gb300 import inputs as I
+from tests._entropy import identity_residual
+from tests._helpers import rel_err_per_var
+
+pytestmark = pytest.mark.gpu
+
+FLUXES = {"burgers": O.FLUX_BURGERS, "euler": O.FLUX_EULER}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2306_11665_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def run_gpu(ctx, u, Ja, prec):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ut = torch.from_numpy(np.ascontiguousarray(u, dtype=np.float64)).to(dt).cuda()
+    Jt = torch.from_numpy(Ja).cuda()
+    r = ctx.volume_residual(ut, Jt, prec)
+    st = ctx.check()
+    return r.double().cpu().numpy(), st
+
+
+def small_case(d, p, kind, flux):
+    N = 3 if d == 3 else 5
+    if d == 3 and p >= 7:
+        N = 2
+    amp = 0.0 if (flux == "burgers" and d == 2) else 0.1
+    return I.workload(d, p, kind, N, flux=flux, amp=amp)
+
+
+CASES = [(3, "euler"), (2, "burgers"), (2, "euler"), (3, "burgers")]
+
+
+@pytest.mark.parametrize("d, flux", CASES)
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("p", range(1, 9))
+def test_fp64_parity_small(d, flux, kind, p):
+    u, Ja = small_case(d, p, kind, flux)
+    ref = O.volume_sf(d, p, kind, FLUXES[flux], u, Ja)
+    ctx = api.Context(d, p, kind, flux)
+    got, st = run_gpu(ctx, u, Ja, "fp64")
+    assert st == A.SFH_OK
+    assert rel_err_per_var(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("d, flux", CASES)
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 4, 7, 8])
+@pytest.mark.parametrize("prec", ["fp32k", "fp32mix"])
+def test_fp32_parity_small(d, flux, kind, p, prec):
+    u, Ja = small_case(d, p, kind, flux)
+    ref = O.volume_sf(d, p, kind, FLUXES[flux], u, Ja)
+    u32 = I.to_fp32(u)
+    ref_w = O.volume_sf(d, p, kind, FLUXES[flux], u32.astype(np.float64), Ja)
+    ctx = api.Context(d, p, kind, flux)
+    got, st = run_gpu(ctx, u32, Ja, prec)
+    assert st == A.SFH_OK
+    assert rel_err_per_var(got, ref) <= 2e-5
+    assert rel_err_per_var(got, ref_w) <= 2e-5
+
+
+def test_burgers_2d_full_config_fp64():
+    """2D Burgers, p=3 Gauss-Lobatto, 8x8 affine: all elements, against the
+    sum-factorized and the dense oracle."""
+    u, Ja = I.workload(2, 3, 0, 8, flux="burgers", amp=0.0)
+    ctx = api.Context(2, 3, "gll", "burgers")
+    got, st = run_gpu(ctx, u, Ja, "fp64")
+    assert st == A.SFH_OK
+    assert rel_err_per_var(got, O.volume_sf(2, 3, 0, O.FLUX_BURGERS, u, Ja)) <= 1e-12
+    assert rel_err_per_var(got, O.volume_dense(2, 3, 0, O.FLUX_BURGERS, u, Ja)) <= 1e-12
+
+
+def _sampled(d, p, kind, N, precs, n_sample, seed):
+    u, Ja = I.workload(d, p, kind, N)
+    E = u.shape[0]
+    rng = np.random.default_rng(seed)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, size=n_sample, replace=False)]))
+    ref = O.volume_sf(d, p, kind, O.FLUX_EULER, u[idx], Ja[idx])
+    ctx = api.Context(d, p, kind, "euler")
+    out = {}
+    for prec in precs:
+        src = u if prec == "fp64" else I.to_fp32(u)
+        got, st = run_gpu(ctx, src, Ja, prec)
+        assert st == A.SFH_OK
+        out[prec] = rel_err_per_var(got[idx], ref)
+    return out, u, Ja, idx, ctx
+
+
+def test_euler_p4_32cubed_sampled():
+    errs, *_ = _sampled(3, 4, 0, 32, ["fp64", "fp32k", "fp32mix"], 96, 21)
+    assert errs["fp64"] <= 1e-12
+    assert errs["fp32k"] <= 2e-5
+    assert errs["fp32mix"] <= 2e-5
+
+
+def test_euler_p7_gauss_16cubed_sampled():
+    errs, *_ = _sampled(3, 7, 1, 16, ["fp64", "fp32k", "fp32mix"], 24, 22)
+    assert errs["fp64"] <= 1e-12
+    assert errs["fp32k"] <= 2e-5
+    assert errs["fp32mix"] <= 2e-5
+
+
+@pytest.mark.parametrize("p, kind, N", [(4, 0, 8), (7, 1, 4)])
+def test_entropy_identity_on_gpu_results(p, kind, N):
+    d = 3
+    u, Ja = I.workload(d, p, kind, N)
+    ctx = api.Context(d, p, kind, "euler")
+    r64, _ = run_gpu(ctx, u, Ja, "fp64")
+    r32, _ = run_gpu(ctx, I.to_fp32(u), Ja, "fp32k")
+    for e in (0, u.shape[0] // 2, u.shape[0] - 1):
+        assert identity_residual(d, p, kind, O.FLUX_EULER, u[e], Ja[e], r64[e]) <= 1e-10
+        assert identity_residual(d, p, kind, O.FLUX_EULER, u[e], Ja[e], r32[e]) <= 1e-4
+
+
+def test_edge_cases():
+    ctx = api.Context(3, 4, "gll", "euler")
+    # n_elem = 0 is a no-op
+    A.sfh_volume_residual(ctx.handle, 0, 0, 0, 0, A.SFH_FP64, 0)
+    # one element
+    u, Ja = I.workload(3, 4, 0, 2, n_elem=1)
+    got, st = run_gpu(ctx, u, Ja, "fp64")
+    assert st == A.SFH_OK
+    assert rel_err_per_var(got, O.volume_sf(3, 4, 0, O.FLUX_EULER, u, Ja)) <= 1e-12
+    # every element count 1..12 (ragged tails of the 5-element CTAs)
+    u, Ja = I.workload(3, 4, 0, 3)
+    for E in range(1, 13):
+        got, _ = run_gpu(ctx, u[:E], Ja[:E], "fp64")
+        assert rel_err_per_var(got, O.volume_sf(3, 4, 0, O.FLUX_EULER, u[:E], Ja[:E])) <= 1e-12
+    # misaligned / overlapping arguments are rejected before any launch
+    ut = torch.from_numpy(u).cuda()
+    Jt = torch.from_numpy(Ja).cuda()
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual(ctx.handle, 2, ut.data_ptr(), Jt.data_ptr(), ut.data_ptr(), A.SFH_FP64, 0)
+    assert e.value.status == A.SFH_EINVAL
+    with pytest.raises(A.SfhError) as e:
+        r2 = torch.empty_like(ut)
+        A.sfh_volume_residual(ctx.handle, 2, ut.data_ptr() + 4, Jt.data_ptr(), r2.data_ptr(), A.SFH_FP64, 0)
+    assert e.value.status == A.SFH_EINVAL
+
+
+def test_domain_error_is_reported_and_cleared():
+    ctx = api.Context(3, 3, "gll", "euler")
+    u, Ja = I.workload(3, 3, 0, 2)
+    bad = u.copy()
+    bad[3, 0, 7] = -1.0         # negative density in element 3
+    got, st = run_gpu(ctx, bad, Ja, "fp64")
+    assert st == A.SFH_EDOMAIN
+    assert ctx.check() == A.SFH_OK    # cleared by the check
+    # elements without the bad node are unaffected
+    ref = O.volume_sf(3, 3, 0, O.FLUX_EULER, u, Ja)
+    keep = [e for e in range(u.shape[0]) if e != 3]
+    assert rel_err_per_var(got[keep], ref[keep]) <= 1e-12
+    # the FP32 path reports it too
+    _, st = run_gpu(ctx, I.to_fp32(bad), Ja, "fp32k")
+    assert st == A.SFH_EDOMAIN
+
+
+def test_deterministic_and_stream():
+    ctx = api.Context(3, 5, "gauss", "euler")
+    u, Ja = I.workload(3, 5, 1, 3)
+    a, _ = run_gpu(ctx, u, Ja, "fp64")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b, _ = run_gpu(ctx, u, Ja, "fp64")
+    assert np.array_equal(a, b)
+    c, _ = run_gpu(ctx, I.to_fp32(u), Ja, "fp32k")
+    d_, _ = run_gpu(ctx, I.to_fp32(u), Ja, "fp32k")
+    assert np.array_equal(c, d_)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+def test_host_entry_point_matches_device(prec):
+    ctx = api.Context(3, 4, "gll", "euler")
+    u, Ja = I.workload(3, 4, 0, 6)
+    src = u if prec == "fp64" else I.to_fp32(u)
+    dev, _ = run_gpu(ctx, src, Ja, prec)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    uh = torch.from_numpy(np.ascontiguousarray(src)).to(dt).pin_memory()
+    Jh = torch.from_numpy(Ja).pin_memory()
+    host = ctx.volume_residual_host(uh, Jh, prec).double().numpy()
+    assert np.array_equal(host, dev)
