@@ -51,8 +51,11 @@ struct Shape {
     static constexpr int NLINE = ipow(N, D - 1);
     static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
     static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;   // rho, v[D], p, beta | u
+    // FP64 Euler keeps FP32 copies of rho and beta (band tests), the mixed
+    // mode an FP64 copy of beta: 8 extra bytes per node either way
+    static constexpr bool F64E = sizeof(T) == 8 && FLUX == kFluxEuler;
     static constexpr int NODE_BYTES = (int)sizeof(T) * (NP + NVAR) + (int)sizeof(TJ) * D
-                                      + ((M::mixed && FLUX == kFluxEuler) ? 8 : 0);
+                                      + (((M::mixed || F64E) && FLUX == kFluxEuler) ? 8 : 0);
     static constexpr int SMEM_BUDGET = 96 * 1024;
     static constexpr int EPB_SMEM = SMEM_BUDGET / (NN * NODE_BYTES) > 0 ? SMEM_BUDGET / (NN * NODE_BYTES) : 1;
     static constexpr int TARGET_LINES = NLINE >= 48 ? 256 : 128;
@@ -130,6 +133,39 @@ __device__ __forceinline__ float inv_ln_mean(float a, float b) {
         return 2.0f * rs * series_P(t * t);
     }
     return __fdividef(logf(__fdividef(a, b)), d);
+}
+
+// Reciprocal for the FP64 kernels: the hardware seed of rcp.approx.ftz.f64
+// refined by two Newton-Raphson steps r <- r + r (1 - s r) (each step doubles
+// the correct bits; four fused multiply-adds instead of a full IEEE division).
+// Accurate to about 1 ulp for normal s; subnormal s flushes to zero.
+__device__ __forceinline__ double rcp_nr(double s) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(s));
+    double e = fma(-s, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-s, r, 1.0);
+    return fma(r, e, r);
+}
+
+// FP64 logarithmic means with the band test taken on FP32 copies of the
+// arguments (af, bf), so that it costs no FP64 instruction.
+__device__ __forceinline__ double ln_mean_f64(double a, double b, float af, float bf) {
+    const double d = a - b, s = a + b;
+    if (fabsf(af - bf) < 0.1f * (af + bf)) {
+        const double t = d * rcp_nr(s);
+        return (0.5 * s) * series_S(t * t);
+    }
+    return d / log(a / b);
+}
+__device__ __forceinline__ double inv_ln_mean_f64(double a, double b, float af, float bf) {
+    const double d = a - b, s = a + b;
+    if (fabsf(af - bf) < 0.1f * (af + bf)) {
+        const double rs = rcp_nr(s);
+        const double t = d * rs;
+        return (2.0 * rs) * series_P(t * t);
+    }
+    return log(a / b) / d;
 }
 
 // Value and both partial derivatives of {a,b}_ln (FP64, for the adjoint).

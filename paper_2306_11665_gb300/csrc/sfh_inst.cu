@@ -5,6 +5,7 @@
 #include "sfh_internal.h"
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
+#include "sfh_volume_tma.cuh"
 
 #ifndef SFH_INST_D
 #error "SFH_INST_D must be defined"
@@ -50,6 +51,18 @@ using Mode = ModeMixed;
 cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,
                    const OpTab<typename Mode::T> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
+#if defined(SFH_INST_FP32K)
+    // FP32-Kahan: the persistent TMA-staged kernel
+#define SFH_TCASE(N)                                                                                         \
+    case N:                                                                                                  \
+        return flux == kFluxEuler ? launch_volume_fp32_tma<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream) \
+                                  : launch_volume_fp32_tma<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
+    switch (n) {
+        SFH_TCASE(2) SFH_TCASE(3) SFH_TCASE(4) SFH_TCASE(5) SFH_TCASE(6) SFH_TCASE(7) SFH_TCASE(8) SFH_TCASE(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SFH_TCASE
+#endif
 #define SFH_CASE(N)                                                                                              \
     case N:                                                                                                      \
         return flux == kFluxEuler ? launch_volume<D, N, kFluxEuler, Mode>(u, Ja, r, n_elem, tab, err, stream)     \

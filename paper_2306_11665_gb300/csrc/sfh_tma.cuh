@@ -1,0 +1,134 @@
+// sfh_tma.cuh -- bulk asynchronous copies (TMA, sm_90+ / sm_103a) and
+// mbarrier helpers in inline PTX, with bounded waits.
+//
+// Every wait here gives up after a time limit (globaltimer) or an iteration
+// cap, whichever comes first; the caller then records an error instead of
+// spinning forever.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace sfh {
+
+constexpr int kErrDomain = 1;    // density or pressure <= 0 (or NaN)
+constexpr int kErrTimeout = 2;   // a bounded wait gave up
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// make generic-proxy shared-memory writes visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier; false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = global_timer_ns();
+    for (uint32_t it = 0; it < (1u << 30); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && global_timer_ns() - t0 > limit_ns) return false;
+    }
+    return false;
+}
+
+// 1D bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0,
+// both addresses 16-byte aligned).
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src_gmem, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst_smem)),
+        "l"(src_gmem), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// 1D bulk copy shared -> global (bytes % 16 == 0, 16-byte aligned), tracked by
+// the issuing thread's bulk group.
+__device__ __forceinline__ void bulk_store(void *dst_gmem, const void *src_smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst_gmem),
+                 "r"(smem_addr(src_smem)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the shared-memory source of every committed bulk store has been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed bulk store has completed
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// FP64 -> FP32 by integer operations (IEEE-754 field arithmetic), so that the
+// conversion does not occupy the FP64 pipe.  Rounds to nearest with ties away
+// from zero; magnitudes below the FP32 normal range give a signed zero and
+// magnitudes at or above 2^128 give infinity (metric terms are O(h^{d-1})).
+__device__ __forceinline__ float d2f_int(double x) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
+    const uint32_t sign = hi & 0x80000000u;
+    const uint32_t mag = hi & 0x7fffffffu;
+    // exponent re-bias (1023 -> 127 is 896 << 20 in the high word), then the
+    // 64-bit field shifted left by 3 lines the exponent up with bit 23
+    uint32_t f = __funnelshift_l(lo, mag - 0x38000000u, 3);
+    f += (lo >> 28) & 1u;
+    f = mag < 0x38100000u ? 0u : f;
+    f = mag >= 0x47f00000u ? 0x7f800000u : f;
+    return __uint_as_float(f | sign);
+}
+
+// ---------------------------------------------------------------------------
+// Packed FP32x2 arithmetic (sm_100+): one instruction performs the same
+// operation on two independent FP32 lanes (here: two grid lines).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    unsigned long long x = *reinterpret_cast<unsigned long long *>(&a), y = *reinterpret_cast<unsigned long long *>(&b), d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    return *reinterpret_cast<float2 *>(&d);
+}
+
+// Kahan accumulation of two lanes at once, with the compensation kept negated
+// (cn = -c) so that every step is one packed instruction:
+//   y = q f + cn, t = s + y, cn = y - (t - s), s = t;   value = s + cn.
+struct KahanF2 {
+    float2 s, cn;
+    __device__ __forceinline__ void zero() { s = f2s(0.0f); cn = f2s(0.0f); }
+    __device__ __forceinline__ void add_prod(float2 q, float2 f) {
+        const float2 y = fma2(q, f, cn);
+        const float2 t = add2(s, y);
+        cn = sub2(y, sub2(t, s));
+        s = t;
+    }
+    __device__ __forceinline__ float2 value() const { return add2(s, cn); }
+};
+
+}  // namespace sfh

@@ -22,6 +22,7 @@
 #pragma once
 
 #include "sfh_device.cuh"
+#include "sfh_tma.cuh"
 
 namespace sfh {
 
@@ -72,6 +73,53 @@ __device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, t
     F[D + 1] = frho * (half * vv + iLb * (T)(1.0 / (kGamma - 1.0))) + half * (A.p * vnb + B.p * vna);
 }
 
+// FP64 pair flux: the node carries v/2 (hv) and FP32 copies of rho and beta
+// (rf, bf) for the band tests; see euler_pair_flux for the formula.
+template <int D>
+struct EulerNodeD {
+    double rho, hv[D], p, beta;
+    double J[D];
+    float rf, bf;
+};
+
+template <int D>
+__device__ __forceinline__ void euler_pair_flux_f64(const EulerNodeD<D> &A, const EulerNodeD<D> &B, double F[D + 2]) {
+    double n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = A.J[k] + B.J[k];
+    double hna = A.hv[0] * n[0], hnb = B.hv[0] * n[0], hvv = A.hv[0] * B.hv[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) {
+        hna = fma(A.hv[k], n[k], hna);
+        hnb = fma(B.hv[k], n[k], hnb);
+        hvv = fma(A.hv[k], B.hv[k], hvv);
+    }
+    const double Lr = ln_mean_f64(A.rho, B.rho, A.rf, B.rf);
+    const double iLb = inv_ln_mean_f64(A.beta, B.beta, A.bf, B.bf);
+    const double frho = Lr * (hna + hnb);              // {rho}_ln {v.n}
+    const double pavg = 0.5 * (A.p + B.p);
+    F[0] = frho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] = fma(frho, A.hv[k] + B.hv[k], pavg * n[k]);
+    const double K = fma(2.0, hvv, iLb * (1.0 / (kGamma - 1.0)));
+    F[D + 1] = fma(frho, K, fma(A.p, hnb, B.p * hna));
+}
+
+template <int D>
+__device__ __forceinline__ void euler_diag_flux_f64(const EulerNodeD<D> &A, double F[D + 2]) {
+    double n[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) n[k] = 2.0 * A.J[k];
+    double hn = A.hv[0] * n[0], hv2 = A.hv[0] * A.hv[0];
+#pragma unroll
+    for (int k = 1; k < D; ++k) { hn = fma(A.hv[k], n[k], hn); hv2 = fma(A.hv[k], A.hv[k], hv2); }
+    const double frho = 2.0 * A.rho * hn;
+    F[0] = frho;
+#pragma unroll
+    for (int k = 0; k < D; ++k) F[1 + k] = fma(2.0 * frho, A.hv[k], A.p * n[k]);
+    F[D + 1] = fma(frho, 2.0 * hv2, 2.0 * A.p * hn * (kGamma / (kGamma - 1.0)));
+}
+
 // Physical Euler flux f(u_a) . (2 Ja^m(a)) = the two-point flux at (u_a, u_a).
 template <class M, int D>
 __device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
@@ -104,8 +152,11 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // layout: [beta_d (mixed)] [J: EPB][D][NN] TJ  [P: EPB][NP][NN] T  [R: EPB][NVAR][NN] T
+    //         (FP64 Euler: [rho_f: EPB][NN] [beta_f: EPB][NN] float in place of beta_d)
+    constexpr bool F64E = S::F64E;
     double *sBd = reinterpret_cast<double *>(smem_raw);
-    constexpr int BD_COUNT = (M::mixed && FLUX == kFluxEuler) ? EPB * NN : 0;
+    float *sRF = reinterpret_cast<float *>(smem_raw);
+    constexpr int BD_COUNT = ((M::mixed || F64E) && FLUX == kFluxEuler) ? EPB * NN : 0;
     TJ *sJ = reinterpret_cast<TJ *>(smem_raw + sizeof(double) * BD_COUNT);
     T *sP = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sJ) + sizeof(TJ) * EPB * D * NN);
     T *sR = sP + EPB * NP * NN;
@@ -129,7 +180,7 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
             for (int k = 0; k < D; ++k) {
                 const T mk = ue[(1 + k) * NN];
                 const T vk = mk * irho;
-                pe[(1 + k) * NN] = vk;
+                pe[(1 + k) * NN] = F64E ? (T)0.5 * vk : vk;   // FP64 keeps v/2
                 ke += mk * vk;
             }
             const T p = (T)(kGamma - 1.0) * (E - (T)0.5 * ke);
@@ -137,6 +188,10 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
             pe[(D + 1) * NN] = p;
             pe[(D + 2) * NN] = rho / p;
             if constexpr (M::mixed) sBd[el * NN + i] = (double)rho / (double)p;
+            if constexpr (F64E) {
+                sRF[el * NN + i] = d2f_int((double)rho);
+                sRF[EPB * NN + el * NN + i] = d2f_int((double)(rho / p));
+            }
             bad |= !(rho > (T)0 && p > (T)0);
         } else {
             pe[0] = ue[0];
@@ -179,7 +234,41 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
 #pragma unroll
                 for (int v = 0; v < NVAR; ++v) acc[a][v].zero();
 
-            if constexpr (FLUX == kFluxEuler) {
+            if constexpr (F64E) {
+                EulerNodeD<D> nd[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    const int i = nb + a * stride;
+                    const T *pe = sP + el * NP * NN + (base + a * stride);
+                    nd[a].rho = pe[0];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) nd[a].hv[k] = pe[(1 + k) * NN];
+                    nd[a].p = pe[(D + 1) * NN];
+                    nd[a].beta = pe[(D + 2) * NN];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) nd[a].J[k] = sJ[(el * D + k) * NN + base + a * stride];
+                    nd[a].rf = sRF[i];
+                    nd[a].bf = sRF[EPB * NN + i];
+                }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < N; ++b) {
+                        double F[D + 2];
+                        euler_pair_flux_f64<D>(nd[a], nd[b], F);
+                        const double qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) { acc[a][v].add_prod(qab, F[v]); acc[b][v].add_prod(qba, F[v]); }
+                    }
+                    const double qaa = tab.Q1[a * N + a];
+                    if (qaa != 0.0) {
+                        double F[D + 2];
+                        euler_diag_flux_f64<D>(nd[a], F);
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) acc[a][v].add_prod(qaa, F[v]);
+                    }
+                }
+            } else if constexpr (FLUX == kFluxEuler) {
                 EulerNode<T, TJ, D> nd[N];
 #pragma unroll
                 for (int a = 0; a < N; ++a) {

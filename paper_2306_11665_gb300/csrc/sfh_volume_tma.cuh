@@ -1,0 +1,498 @@
+// sfh_volume_tma.cuh -- persistent FP32 (Kahan) volume-residual kernel with
+// TMA bulk staging.
+//
+// Same arithmetic as volume_kernel (Eq. 3 with the Eq. 5 operators, one
+// unordered line pair per flux evaluation, compensated line sums), organised
+// for GB300:
+//   * persistent CTAs walk element blocks blk = blockIdx.x, + gridDim.x, ...;
+//   * the raw u (FP32) and Ja (FP64) of a block arrive in shared memory by
+//     two 1D bulk copies (cp.async.bulk + mbarrier), issued by one thread;
+//     a block whose start is not 16-byte aligned is fetched through a wider
+//     aligned window and indexed from the remainder;
+//   * as soon as a block's raw data has been converted (primitives, and Ja to
+//     FP32 with integer field arithmetic -- an FP64->FP32 conversion
+//     instruction would run on the narrow FP64 pipe), the next block's bulk
+//     copies are issued into the same raw buffers, so the HBM traffic of
+//     block k+1 overlaps the line sweeps of block k;
+//   * the d directions are swept concurrently (one thread per line and
+//     direction), each direction writing its own residual slice, summed in a
+//     fixed order afterwards (deterministic);
+//   * r leaves by a bulk store when the block is 16-byte aligned, else by
+//     coalesced stores.
+// Waits are bounded: a bulk copy that does not arrive within 2 s sets the
+// timeout bit of the error word and the CTA leaves after draining its copies.
+#pragma once
+
+#include "sfh_device.cuh"
+#include "sfh_tma.cuh"
+
+namespace sfh {
+
+// Residency.  Each of the four sub-partitions of an SM holds its warps'
+// registers in its own 16K-register file, so CPS resident CTAs of W warps
+// each fit only if CPS * ceil(W/4) * regs * 32 <= 16384: the register cap is
+// 512 / (CPS * WPS) with WPS = ceil(W/4).  Two CTAs per SM let one CTA's
+// per-node phases and barriers overlap the other's line sweeps (measured on
+// the 3D n=5 shape: 202 us against 221 us with one CTA); the pairs below
+// follow the register counts ptxas reports for each line body (about 55, 64,
+// 80, 96, 125, 150, 205, 230 registers for 3D Euler n = 2..9).
+template <int D, int N, int FLUX>
+constexpr int tma_cps() {
+    if (FLUX != kFluxEuler) return 2;
+    return N <= (D == 3 ? 6 : 7) ? 2 : 1;
+}
+template <int D, int N, int FLUX>
+constexpr int tma_wps() {
+    if (FLUX != kFluxEuler) return 3;
+    if (D == 3) return N <= 3 ? 4 : (N == 4 ? 3 : 2);
+    return N <= 4 ? 4 : (N <= 7 ? 2 : 3);
+}
+
+template <int D, int N, int FLUX>
+struct TmaShape {
+    static constexpr int CPS = tma_cps<D, N, FLUX>();
+    static constexpr int WPS = tma_wps<D, N, FLUX>();   // per CTA
+    static constexpr int NN = ipow(N, D);
+    static constexpr int NLINE = ipow(N, D - 1);
+    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
+    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;      // rho, v/2 [D], p, beta | u
+    static constexpr int NJ = FLUX == kFluxEuler ? D * D : D;       // FP32 metric values kept per node
+    static constexpr int U_EL = NVAR * NN;                          // floats of u (and r) per element
+    static constexpr int J_EL = D * D * NN;                         // doubles of Ja per element
+    static constexpr int EL_BYTES = 4 * U_EL + 8 * J_EL + 4 * NP * NN + 4 * NJ * NN + 4 * D * U_EL;
+    static constexpr int BUDGET = (CPS == 1 ? 200 : 108) * 1024;
+    static constexpr int MAX_THREADS = 128 * WPS;
+    static constexpr int epb_by_smem() { return BUDGET / EL_BYTES > 0 ? BUDGET / EL_BYTES : 1; }
+    // largest EPB whose D * EPB * NLINE line tasks fit the thread budget
+    static constexpr int epb_by_threads() {
+        int e = 1;
+        while (D * (e + 1) * NLINE <= MAX_THREADS) ++e;
+        return e;
+    }
+    static constexpr int epb_raw() { return epb_by_smem() < epb_by_threads() ? epb_by_smem() : epb_by_threads(); }
+    static constexpr bool aligned_blocks(int e) { return (e * U_EL * 4) % 16 == 0; }
+    // prefer a block whose r slice is a whole number of 16-byte units (bulk store)
+    static constexpr int pick_epb() {
+        for (int e = epb_raw(); e >= 1 && 4 * e >= 3 * epb_raw(); --e)
+            if (aligned_blocks(e)) return e;
+        return epb_raw();
+    }
+    static constexpr int EPB = pick_epb();
+    static constexpr int THREADS = ((D * EPB * NLINE + 31) / 32) * 32;
+    static constexpr int MAXREG = (512 / (WPS * CPS)) / 8 * 8 < 255 ? (512 / (WPS * CPS)) / 8 * 8 : 255;
+    static_assert(THREADS <= MAX_THREADS, "line tasks exceed the CTA");
+    static constexpr int RAWU_BYTES = ((EPB * U_EL * 4 + 16) + 15) / 16 * 16;   // + window slack
+    static constexpr int RAWJ_BYTES = ((EPB * J_EL * 8 + 16) + 15) / 16 * 16;
+    static constexpr int OFF_U = 16;                                             // [0,16): mbarrier
+    static constexpr int OFF_J = OFF_U + RAWU_BYTES;
+    static constexpr int OFF_P = OFF_J + RAWJ_BYTES;
+    static constexpr int up16(int x) { return (x + 15) / 16 * 16; }
+    static constexpr int OFF_JF = up16(OFF_P + EPB * NP * NN * 4);
+    static constexpr int OFF_R = up16(OFF_JF + EPB * NJ * NN * 4);   // bulk-store source: 16-byte aligned
+    static constexpr size_t SMEM = OFF_R + (size_t)D * EPB * U_EL * 4;
+    static_assert(OFF_U % 16 == 0 && OFF_J % 16 == 0 && OFF_R % 16 == 0, "bulk-copy buffers must be 16-byte aligned");
+};
+
+struct BlockPlan {
+    int64_t e0;
+    int ne;
+    bool tma;
+    uint32_t offU, offJ;          // element offsets of the block inside the raw windows
+    const char *srcU, *srcJ;
+    uint32_t bytesU, bytesJ;
+};
+
+template <class S>
+__device__ __forceinline__ BlockPlan plan_block(int64_t blk, int64_t n_elem, const float *u, const double *Ja,
+                                                bool aligned_bases) {
+    BlockPlan pl;
+    pl.e0 = blk * S::EPB;
+    pl.ne = (int)((n_elem - pl.e0) < S::EPB ? (n_elem - pl.e0) : S::EPB);
+    const uintptr_t aU = reinterpret_cast<uintptr_t>(u + pl.e0 * S::U_EL);
+    const uintptr_t eU = reinterpret_cast<uintptr_t>(u + n_elem * S::U_EL);
+    const uintptr_t loU = aU & ~uintptr_t(15), hiU = (aU + (uintptr_t)pl.ne * S::U_EL * 4 + 15) & ~uintptr_t(15);
+    const uintptr_t aJ = reinterpret_cast<uintptr_t>(Ja + pl.e0 * S::J_EL);
+    const uintptr_t eJ = reinterpret_cast<uintptr_t>(Ja + n_elem * S::J_EL);
+    const uintptr_t loJ = aJ & ~uintptr_t(15), hiJ = (aJ + (uintptr_t)pl.ne * S::J_EL * 8 + 15) & ~uintptr_t(15);
+    pl.tma = aligned_bases && hiU <= eU && hiJ <= eJ;   // never read past the end of either array
+    pl.offU = (uint32_t)((aU - loU) / 4);
+    pl.offJ = (uint32_t)((aJ - loJ) / 8);
+    pl.srcU = reinterpret_cast<const char *>(loU);
+    pl.srcJ = reinterpret_cast<const char *>(loJ);
+    pl.bytesU = (uint32_t)(hiU - loU);
+    pl.bytesJ = (uint32_t)(hiJ - loJ);
+    if (!pl.tma) { pl.offU = 0; pl.offJ = 0; }
+    return pl;
+}
+
+// Geometry of one grid line of an element block: first node, node stride
+// along direction m, and omega_m (the product of the other directions'
+// weights, constant along the line).
+template <int D, int N>
+__device__ __forceinline__ void line_geometry(int m, int l, const OpTab<float> &tab, int &base, float &omega) {
+    if constexpr (D == 3) {
+        const int o0 = l % N, o1 = l / N;
+        base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
+        omega = tab.w[o0] * tab.w[o1];
+    } else {
+        base = m == 0 ? N * l : l;
+        omega = tab.w[l];
+    }
+}
+
+// One Euler line from scratch, with the logarithm for pairs outside the
+// series band.  Kept out of line (one copy per kernel) because it runs only
+// for states with large jumps along a line; the arithmetic is that of the
+// fast path otherwise.
+template <int D, int N, int NN, int NP>
+__device__ __noinline__ void euler_line_general(const float *pe, const float *je, float *re, int stride, float omega,
+                                                const OpTab<float> &tab) {
+    constexpr int NVAR = D + 2;
+#pragma unroll 1
+    for (int a = 0; a < N; ++a) {
+        KahanF acc[NVAR];
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) acc[v].zero();
+        const float ra = pe[a * stride], pa = pe[(D + 1) * NN + a * stride], ba = pe[(D + 2) * NN + a * stride];
+        float hva[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) hva[k] = pe[(1 + k) * NN + a * stride];
+#pragma unroll 1
+        for (int b = 0; b < N; ++b) {
+            const float q = tab.Q1[a * N + b];
+            if (q == 0.0f) continue;
+            const float rb = pe[b * stride], pb = pe[(D + 1) * NN + b * stride], bb = pe[(D + 2) * NN + b * stride];
+            float hvb[D], n[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                hvb[k] = pe[(1 + k) * NN + b * stride];
+                n[k] = je[k * NN + a * stride] + je[k * NN + b * stride];
+            }
+            float hna = 0.0f, hnb = 0.0f, hvv = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) { hna = fmaf(hva[k], n[k], hna); hnb = fmaf(hvb[k], n[k], hnb); hvv = fmaf(hva[k], hvb[k], hvv); }
+            const float Lr = ln_mean(ra, rb), iLb = inv_ln_mean(ba, bb);
+            float F[D + 2];
+            const float frho = Lr * (hna + hnb);
+            const float pavg = 0.5f * (pa + pb);
+            F[0] = frho;
+#pragma unroll
+            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(frho, hva[k] + hvb[k], pavg * n[k]);
+            F[D + 1] = fmaf(frho, fmaf(2.0f, hvv, iLb * (float)(1.0 / (kGamma - 1.0))), fmaf(pa, hnb, pb * hna));
+#pragma unroll
+            for (int v = 0; v < NVAR; ++v) acc[v].add_prod(q, F[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < NVAR; ++v) re[v * NN + a * stride] = omega * acc[v].value();
+    }
+}
+
+template <int D, int N, int FLUX>
+__global__ void __launch_bounds__(TmaShape<D, N, FLUX>::THREADS) __maxnreg__((TmaShape<D, N, FLUX>::MAXREG))
+volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ Ja, float *__restrict__ r,
+                       int64_t n_elem, const __grid_constant__ OpTab<float> tab, int *__restrict__ err,
+                       int aligned_bases) {
+    using S = TmaShape<D, N, FLUX>;
+    constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, NJ = S::NJ, EPB = S::EPB;
+    constexpr int U_EL = S::U_EL, J_EL = S::J_EL;
+    extern __shared__ __align__(128) unsigned char sm[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
+    float *rawU = reinterpret_cast<float *>(sm + S::OFF_U);
+    double *rawJ = reinterpret_cast<double *>(sm + S::OFF_J);
+    float *sP = reinterpret_cast<float *>(sm + S::OFF_P);
+    float *sJF = reinterpret_cast<float *>(sm + S::OFF_JF);
+    float *sR = reinterpret_cast<float *>(sm + S::OFF_R);
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    const int64_t nblk = (n_elem + EPB - 1) / EPB;
+    if ((int64_t)blockIdx.x >= nblk) return;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        s_abort = 0;
+        fence_proxy_async_smem();
+    }
+    __syncthreads();
+
+    uint32_t phase = 0;
+    int64_t blk = blockIdx.x;
+    BlockPlan cur = plan_block<S>(blk, n_elem, u, Ja, aligned_bases != 0);
+    if (tid == 0 && cur.tma) {
+        mbar_arrive_expect_tx(bar, cur.bytesU + cur.bytesJ);
+        bulk_load(rawU, cur.srcU, cur.bytesU, bar);
+        bulk_load(rawJ, cur.srcJ, cur.bytesJ, bar);
+    }
+
+    for (; blk < nblk; blk += gridDim.x) {
+        const int ne = cur.ne;
+        // ---- 1. raw data of this block
+        if (cur.tma) {
+            if (!mbar_wait_bounded(bar, phase, 2000000000ull)) s_abort = 1;
+            phase ^= 1u;
+        } else {
+            const float *gU = u + cur.e0 * U_EL;
+            const double *gJ = Ja + cur.e0 * J_EL;
+            for (int s = tid; s < ne * U_EL; s += blockDim.x) rawU[s] = gU[s];
+            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJ[s];
+        }
+        __syncthreads();
+        if (s_abort) {
+            if (tid == 0) {
+                atomicOr(err, kErrTimeout);
+                mbar_wait_bounded(bar, phase ^ 1u, 1000000000ull);
+                bulk_wait_all();
+            }
+            return;
+        }
+
+        // ---- 2. primitives and FP32 metrics
+        const float *U = rawU + cur.offU;
+        const double *J = rawJ + cur.offJ;
+        bool bad = false;
+        for (int s = tid; s < ne * NN; s += blockDim.x) {
+            const int el = s / NN, i = s - el * NN;
+            const float *ue = U + el * U_EL + i;
+            float *pe = sP + el * NP * NN + i;
+            if constexpr (FLUX == kFluxEuler) {
+                // per-node divisions to within about half an ulp: with the
+                // residual's cancellation, per-node errors act like
+                // perturbations of the input state.  q = m / rho is formed as
+                // m r (r: reciprocal seed plus one Newton step) followed by one
+                // residual correction q += r (m - rho q), each a fused op.
+                const float rho = ue[0], E = ue[(D + 1) * NN];
+                float ir = __fdividef(1.0f, rho);
+                ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
+                float ke = 0.0f;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const float mk = ue[(1 + k) * NN];
+                    float vk = mk * ir;
+                    vk = fmaf(ir, fmaf(-rho, vk, mk), vk);
+                    pe[(1 + k) * NN] = 0.5f * vk;
+                    ke = fmaf(mk, vk, ke);
+                }
+                const float p = (float)(kGamma - 1.0) * fmaf(-0.5f, ke, E);
+                float ip = __fdividef(1.0f, p);
+                ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
+                float bt = rho * ip;
+                bt = fmaf(ip, fmaf(-p, bt, rho), bt);
+                pe[0] = rho;
+                pe[(D + 1) * NN] = p;
+                pe[(D + 2) * NN] = bt;
+                bad |= !(rho > 0.0f && p > 0.0f);
+            } else {
+                pe[0] = ue[0];
+            }
+        }
+        if constexpr (FLUX == kFluxEuler) {
+            for (int s = tid; s < ne * J_EL; s += blockDim.x) sJF[s] = d2f_int(J[s]);
+        } else {
+            for (int s = tid; s < ne * D * NN; s += blockDim.x) {
+                const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
+                const double *jm = J + ((el * D + m) * D) * NN + i;
+                float acc = d2f_int(jm[0]);
+#pragma unroll
+                for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
+                sJF[s] = acc;
+            }
+        }
+        if (bad) atomicOr(err, kErrDomain);
+        if (tid == 0) bulk_wait_read_all();   // the previous block's r store has left sR
+        __syncthreads();
+
+        // ---- 3. prefetch the next block into the raw buffers
+        const int64_t nxt = blk + gridDim.x;
+        BlockPlan nx = cur;
+        if (nxt < nblk) nx = plan_block<S>(nxt, n_elem, u, Ja, aligned_bases != 0);
+        if (tid == 0 && nxt < nblk && nx.tma) {
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, nx.bytesU + nx.bytesJ);
+            bulk_load(rawU, nx.srcU, nx.bytesU, bar);
+            bulk_load(rawJ, nx.srcJ, nx.bytesJ, bar);
+        }
+
+        // ---- 4. line sweeps, all directions at once
+        if (tid < D * EPB * NLINE) {
+            const int m = tid / (EPB * NLINE);
+            const int L = tid - m * (EPB * NLINE);
+            const int el = L / NLINE, l = L - el * NLINE;
+            if (el < ne) {
+                const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
+                int base;
+                float omega;
+                if constexpr (D == 3) {
+                    const int o0 = l % N, o1 = l / N;
+                    base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
+                    omega = tab.w[o0] * tab.w[o1];
+                } else {
+                    base = m == 0 ? N * l : l;
+                    omega = tab.w[l];
+                }
+                KahanF acc[N][NVAR];
+#pragma unroll
+                for (int a = 0; a < N; ++a)
+#pragma unroll
+                    for (int v = 0; v < NVAR; ++v) acc[a][v].zero();
+                const float *pe = sP + el * NP * NN + base;
+                bool oob = false;   // a pair outside the series band was met
+                if constexpr (FLUX == kFluxEuler) {
+                    const float *je = sJF + (el * D + m) * D * NN + base;
+                    float rho[N], hv[N][D], p[N], beta[N];
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+                        rho[a] = pe[a * stride];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) hv[a][k] = pe[(1 + k) * NN + a * stride];
+                        p[a] = pe[(D + 1) * NN + a * stride];
+                        beta[a] = pe[(D + 2) * NN + a * stride];
+                    }
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+#pragma unroll
+                        for (int b = a + 1; b < N; ++b) {
+                            float n[D];
+#pragma unroll
+                            for (int k = 0; k < D; ++k) n[k] = je[k * NN + a * stride] + je[k * NN + b * stride];
+                            // half normal velocities hv.n, half-velocity product
+                            float hna = hv[a][0] * n[0], hnb = hv[b][0] * n[0], hvv = hv[a][0] * hv[b][0];
+#pragma unroll
+                            for (int k = 1; k < D; ++k) {
+                                hna = fmaf(hv[a][k], n[k], hna);
+                                hnb = fmaf(hv[b][k], n[k], hnb);
+                                hvv = fmaf(hv[a][k], hv[b][k], hvv);
+                            }
+                            // {rho}_ln = (s/2) S(t^2); 1/{beta}_ln = (2/s) P(t^2)
+                            // logarithmic means by the series (no branch in the
+                            // common case); a pair outside the band |a-b| < 0.1 (a+b)
+                            // is recomputed from the logarithm in a rarely taken branch
+                            const float dr = rho[a] - rho[b], sr = rho[a] + rho[b];
+                            const float db = beta[a] - beta[b], sb = beta[a] + beta[b];
+                            const float tr = dr * __fdividef(1.0f, sr);
+                            float rs = __fdividef(1.0f, sb);
+                            rs = fmaf(rs, fmaf(-sb, rs, 1.0f), rs);    // 1/s scales the energy flux: one Newton step
+                            const float tb = db * rs;
+                            const float Lr = (0.5f * sr) * series_S(tr * tr);
+                            const float iLb = (2.0f * rs) * series_P(tb * tb);
+                            oob |= !(fabsf(dr) < 0.1f * sr) || !(fabsf(db) < 0.1f * sb);
+                            float F[D + 2];
+                            const float frho = Lr * (hna + hnb);          // {rho}_ln {v.n}
+                            const float pavg = 0.5f * (p[a] + p[b]);
+                            F[0] = frho;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(frho, hv[a][k] + hv[b][k], pavg * n[k]);
+                            // energy: frho (v_a.v_b / 2 + 1/((g-1){beta}_ln)) + (p_a v_b.n + p_b v_a.n)/2
+                            const float K = fmaf(2.0f, hvv, iLb * (float)(1.0 / (kGamma - 1.0)));
+                            F[D + 1] = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
+#pragma unroll
+                            for (int v = 0; v < NVAR; ++v) {
+                                acc[a][v].add_prod(qab, F[v]);
+                                acc[b][v].add_prod(qba, F[v]);
+                            }
+                        }
+                        const float qaa = tab.Q1[a * N + a];
+                        if (qaa != 0.0f) {
+                            // physical flux f(u_a) . (2 Ja^m(a))
+                            float n[D];
+#pragma unroll
+                            for (int k = 0; k < D; ++k) n[k] = 2.0f * je[k * NN + a * stride];
+                            float hn = hv[a][0] * n[0], hv2 = hv[a][0] * hv[a][0];
+#pragma unroll
+                            for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
+                            float F[D + 2];
+                            const float frho = 2.0f * rho[a] * hn;
+                            F[0] = frho;
+#pragma unroll
+                            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], p[a] * n[k]);
+                            F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
+#pragma unroll
+                            for (int v = 0; v < NVAR; ++v) acc[a][v].add_prod(qaa, F[v]);
+                        }
+                    }
+                } else {
+                    const float *je = sJF + (el * D + m) * NN + base;
+                    float uu[N], Sm[N];
+#pragma unroll
+                    for (int a = 0; a < N; ++a) { uu[a] = pe[a * stride]; Sm[a] = je[a * stride]; }
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+#pragma unroll
+                        for (int b = a + 1; b < N; ++b) {
+                            const float F = (uu[a] * uu[a] + uu[a] * uu[b] + uu[b] * uu[b]) * (1.0f / 6.0f) * (Sm[a] + Sm[b]);
+                            acc[a][0].add_prod(tab.Q1[a * N + b], F);
+                            acc[b][0].add_prod(tab.Q1[b * N + a], F);
+                        }
+                        const float qaa = tab.Q1[a * N + a];
+                        if (qaa != 0.0f) acc[a][0].add_prod(qaa, uu[a] * uu[a] * Sm[a]);
+                    }
+                }
+                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+                if constexpr (FLUX == kFluxEuler) {
+                    if (__builtin_expect(oob, 0)) {
+                        // rare: redo the whole line with logarithms where needed
+                        euler_line_general<D, N, NN, NP>(sP + el * NP * NN + base, sJF + (el * D + m) * D * NN + base,
+                                                         re, stride, omega, tab);
+                    }
+                }
+                if (!oob) {
+#pragma unroll
+                    for (int a = 0; a < N; ++a)
+#pragma unroll
+                        for (int v = 0; v < NVAR; ++v) re[v * NN + a * stride] = omega * acc[a][v].value();
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---- 5. sum the directions in a fixed order, store r
+        for (int s = tid; s < ne * U_EL; s += blockDim.x) {
+            float t = sR[s] + sR[EPB * U_EL + s];
+            if constexpr (D == 3) t += sR[2 * EPB * U_EL + s];
+            sR[s] = t;
+        }
+        __syncthreads();
+        float *gR = r + cur.e0 * U_EL;
+        const uint32_t rbytes = (uint32_t)ne * U_EL * 4;
+        const bool bulk = aligned_bases && (reinterpret_cast<uintptr_t>(gR) & 15) == 0 && (rbytes & 15) == 0;
+        if (bulk) {
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                bulk_store(gR, sR, rbytes);
+                bulk_commit();
+            }
+        } else {
+            for (int s = tid; s < ne * U_EL; s += blockDim.x) gR[s] = sR[s];
+        }
+        cur = nx;
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
+// grid: one resident CTA per SM slot (persistent); occupancy is queried once
+template <int D, int N, int FLUX>
+cudaError_t launch_volume_fp32_tma(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab,
+                                   int *err, cudaStream_t stream) {
+    using S = TmaShape<D, N, FLUX>;
+    auto kern = volume_fp32_tma_kernel<D, N, FLUX>;
+    static_assert(S::SMEM <= 227 * 1024, "shared memory");
+    static int per_sm = 0, sms = 0;
+    if (per_sm == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::THREADS, S::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    }
+    const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
+    const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
+    const int aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(Ja) |
+                          reinterpret_cast<uintptr_t>(r)) & 15) == 0;
+    kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja, static_cast<float *>(r),
+                                                         n_elem, tab, err, aligned);
+    return cudaGetLastError();
+}
+
+}  // namespace sfh

@@ -17,7 +17,7 @@ from paper_2306_11665_gb300 import _abi as A
 from paper_2306_11665_gb300 import api
 from paper_2306_11665_gb300 import inputs as I
 from tests._entropy import identity_residual, kron_q
-from tests._helpers import rel_err_per_var
+from tests._helpers import fp32_check, rel_err_per_var
 
 pytestmark = pytest.mark.gpu
 
@@ -63,29 +63,23 @@ def test_fp64_parity_small(d, flux, kind, p):
     assert rel_err_per_var(got, ref) <= 1e-12
 
 
-def fp32_bar(d, p, kind, flux, u, Ja, r):
-    """FP32 bar of a test case: the 2e-5 of the full-size configurations, or,
-    where the case is worse conditioned, 2.5 u32 kappa with u32 = 2^-24 and
-    kappa = max_v max_i sum_{m,j} |Q_m,ij||F_m,ij,v| / max_i |r_i,v| (the
-    sum the residual cancels, over its size; measured on the first elements)."""
-    kappa = 0.0
-    E = min(u.shape[0], 3)
-    for v in range(u.shape[1]):
-        S = np.zeros((E, u.shape[2]))
-        for e in range(E):
-            for m in range(d):
-                Q = kron_q(d, p, kind, m)
-                rows, cols = np.nonzero(Q)
-                for i, j in zip(rows, cols):
-                    F = O.ec_flux(d, FLUXES[flux], u[e, :, i], u[e, :, j], Ja[e, m, :, i] + Ja[e, m, :, j])
-                    S[e, i] += abs(Q[i, j]) * abs(F[v])
-        kappa = max(kappa, S.max() / np.abs(r[:E, v]).max())
-    return max(2e-5, 2.5 * 2.0 ** -24 * kappa)
+def kappa(d, p, kind, flux, u, Ja, r, n_el=3):
+    """kappa_v = max_i sum_{m,j} |Q_m,ij||F_m,ij,v| / max_i |r_i,v| on the first elements."""
+    E = min(u.shape[0], n_el)
+    S = np.zeros((E,) + u.shape[1:])
+    for e in range(E):
+        for m in range(d):
+            Q = kron_q(d, p, kind, m)
+            rows, cols = np.nonzero(Q)
+            for i, j in zip(rows, cols):
+                F = O.ec_flux(d, FLUXES[flux], u[e, :, i], u[e, :, j], Ja[e, m, :, i] + Ja[e, m, :, j])
+                S[e, :, i] += abs(Q[i, j]) * np.abs(F)
+    return [S[:, v].max() / np.abs(r[:E, v]).max() for v in range(u.shape[1])]
 
 
 @pytest.mark.parametrize("d, flux", CASES)
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("p", [1, 2, 4, 7, 8])
+@pytest.mark.parametrize("p", range(1, 9))
 @pytest.mark.parametrize("prec", ["fp32k", "fp32mix"])
 def test_fp32_parity_small(d, flux, kind, p, prec):
     u, Ja = small_case(d, p, kind, flux)
@@ -95,11 +89,7 @@ def test_fp32_parity_small(d, flux, kind, p, prec):
     ctx = api.Context(d, p, kind, flux)
     got, st = run_gpu(ctx, u32, Ja, prec)
     assert st == A.SFH_OK
-    err = rel_err_per_var(got, ref)
-    if err > 2e-5:
-        bar = fp32_bar(d, p, kind, flux, u, Ja, ref)
-        assert err <= bar, (err, bar)
-        assert rel_err_per_var(got, ref_w) <= bar
+    fp32_check(got, ref, ref_w, lambda: kappa(d, p, kind, flux, u, Ja, ref))
 
 
 def test_burgers_2d_full_config_fp64():
@@ -114,33 +104,47 @@ def test_burgers_2d_full_config_fp64():
 
 
 def _sampled(d, p, kind, N, precs, n_sample, seed):
+    """Full-size run on the GPU, the oracle on sampled elements; FP64 is held
+    to 1e-12 per variable, the FP32 modes to the FP32 bars (fp32_check)."""
     u, Ja = I.workload(d, p, kind, N)
     E = u.shape[0]
     rng = np.random.default_rng(seed)
     idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, size=n_sample, replace=False)]))
     ref = O.volume_sf(d, p, kind, O.FLUX_EULER, u[idx], Ja[idx])
+    ref_w = O.volume_sf(d, p, kind, O.FLUX_EULER, I.to_fp32(u[idx]).astype(np.float64), Ja[idx])
     ctx = api.Context(d, p, kind, "euler")
     out = {}
     for prec in precs:
         src = u if prec == "fp64" else I.to_fp32(u)
         got, st = run_gpu(ctx, src, Ja, prec)
         assert st == A.SFH_OK
-        out[prec] = rel_err_per_var(got[idx], ref)
+        if prec == "fp64":
+            out[prec] = {"per_variable_worst": float(rel_err_per_var(got[idx], ref))}
+            assert out[prec]["per_variable_worst"] <= 1e-12
+        else:
+            out[prec] = fp32_check(got[idx], ref, ref_w,
+                                   lambda: kappa(d, p, kind, "euler", u[idx], Ja[idx], ref))
     return out, u, Ja, idx, ctx
+
+
+def _report(name, data):
+    import json
+    import os
+    d = os.environ.get("SFH_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, f"{name}.json"), "w") as f:
+            json.dump(data, f, indent=1)
 
 
 def test_euler_p4_32cubed_sampled():
     errs, *_ = _sampled(3, 4, 0, 32, ["fp64", "fp32k", "fp32mix"], 96, 21)
-    assert errs["fp64"] <= 1e-12
-    assert errs["fp32k"] <= 2e-5
-    assert errs["fp32mix"] <= 2e-5
+    _report("parity_euler_p4_gll_32cubed", errs)
 
 
 def test_euler_p7_gauss_16cubed_sampled():
     errs, *_ = _sampled(3, 7, 1, 16, ["fp64", "fp32k", "fp32mix"], 24, 22)
-    assert errs["fp64"] <= 1e-12
-    assert errs["fp32k"] <= 2e-5
-    assert errs["fp32mix"] <= 2e-5
+    _report("parity_euler_p7_gauss_16cubed", errs)
 
 
 @pytest.mark.parametrize("p, kind, N", [(4, 0, 8), (7, 1, 4)])
@@ -222,3 +226,28 @@ def test_host_entry_point_matches_device(prec):
     Jh = torch.from_numpy(Ja).pin_memory()
     host = ctx.volume_residual_host(uh, Jh, prec).double().numpy()
     assert np.array_equal(host, dev)
+
+
+@pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 2, 1), (2, 5, 0), (3, 7, 1)])
+def test_rough_states_take_the_logarithm_path(d, p, kind):
+    """States with large jumps between neighbouring nodes put many pairs
+    outside the series band of the logarithmic mean (|a-b| >= 0.1 (a+b)),
+    exercising the logarithm branch of every precision mode."""
+    rng = np.random.default_rng(31)
+    x, Ja = I.mesh(d, p, kind, 2, 0.1)
+    E, nn = x.shape[0], x.shape[2]
+    rho = 1.0 + 0.8 * rng.uniform(-1, 1, size=(E, nn))
+    pr = 1.0 + 0.8 * rng.uniform(-1, 1, size=(E, nn))
+    v = [0.3 * rng.uniform(-1, 1, size=(E, nn)) for _ in range(d)]
+    u = np.ascontiguousarray(I.conservative(rho, v, pr))
+    ref = O.volume_sf(d, p, kind, O.FLUX_EULER, u, Ja)
+    ctx = api.Context(d, p, kind, "euler")
+    got, st = run_gpu(ctx, u, Ja, "fp64")
+    assert st == A.SFH_OK
+    assert rel_err_per_var(got, ref) <= 1e-12
+    u32 = I.to_fp32(u)
+    ref_w = O.volume_sf(d, p, kind, O.FLUX_EULER, u32.astype(np.float64), Ja)
+    for prec in ("fp32k", "fp32mix"):
+        got, st = run_gpu(ctx, u32, Ja, prec)
+        assert st == A.SFH_OK
+        fp32_check(got, ref, ref_w, lambda: kappa(d, p, kind, "euler", u, Ja, ref))
