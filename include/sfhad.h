@@ -128,6 +128,30 @@ sfh_status sfh_check(sfh_ctx *ctx, sfh_stream_t stream);
 sfh_status sfh_volume_residual_host(sfh_ctx *ctx, int64_t n_elem, const void *u_host,
                                     const double *Ja_host, void *r_host, sfh_prec prec);
 
+/* Volume residual for callers that cannot allocate device memory (no
+ * counterpart in the paper: this is a deployment convenience).  Some callers
+ * cannot call cudaMalloc -- for instance a host application whose device
+ * memory belongs to another allocator with a fixed budget, or one that must
+ * not allocate after start-up.  They pass host buffers (layouts as in
+ * sfh_volume_residual; pageable or page-locked) and a stream; the library
+ * needs no context: it builds the operator tables on the host stack and
+ * stages u, Ja and r, plus its device error word, through one fixed device
+ * array that is part of the library image (64 MiB; every GPU that loads the
+ * library holds it until the process exits).  It calls no cudaMalloc,
+ * cudaFree or allocating routine.
+ * Limit: 256 + 2 * round256(bytes(u)) + round256(bytes(Ja)) <= 64 MiB (for 3D
+ * Euler p = 4: about 4,790 elements in FP32, 3,530 in FP64); larger
+ * requests return SFH_EINVAL with the limit in sfh_last_error().
+ * The array keeps the last call's contents (the error word is cleared at the
+ * start of each call); calls that overlap on the GPU -- from two host threads
+ * or on two streams -- race on it and must be serialized by the caller.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current).  Synchronous: returns when r_host is
+ * filled.  Errors: SFH_EINVAL, SFH_ECUDA, SFH_EDOMAIN, SFH_ETIMEOUT. */
+sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes nodes, sfh_flux flux, int64_t n_elem,
+                                            const void *u_host, const double *Ja_host, void *r_host,
+                                            sfh_prec prec, sfh_stream_t stream);
+
 /* Describe a context: any output pointer may be NULL.  n_nodes = (p+1)^d. */
 sfh_status sfh_ctx_info(const sfh_ctx *ctx, int *d, int *p, int *nodes, int *nvar, int *flux,
                         int *n_nodes);

@@ -58,6 +58,8 @@ _SIGS = {
     "sfh_check": [vp, vp],
     "sfh_volume_residual_host": [vp, i64, vp, vp, vp, ctypes.c_int],
     "sfh_ctx_info": [vp, ip, ip, ip, ip, ip, ip],
+    "sfh_volume_residual_host_noalloc": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, vp, vp, vp,
+                                         ctypes.c_int, vp],
     "sfh_operator_tables": [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp],
     "sfh_peak_fma": [ctypes.c_int, dp, dp],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
@@ -128,6 +130,14 @@ def sfh_check(ctx: int, stream: int = 0) -> int:
 
 def sfh_volume_residual_host(ctx: int, n_elem: int, u_host: int, Ja_host: int, r_host: int, prec: int) -> int:
     return _call("sfh_volume_residual_host", ctx, n_elem, u_host, Ja_host, r_host, prec, ok=(SFH_OK, SFH_EDOMAIN))
+
+
+def sfh_volume_residual_host_noalloc(d: int, p: int, nodes: int, flux: int, n_elem: int, u_host: int,
+                                     Ja_host: int, r_host: int, prec: int, stream: int = 0) -> int:
+    """Context-free, allocation-free host-buffer residual (returns the status;
+    SFH_OK or SFH_EDOMAIN; raises on other errors)."""
+    return _call("sfh_volume_residual_host_noalloc", d, p, nodes, flux, n_elem, u_host, Ja_host, r_host, prec, stream,
+                 ok=(SFH_OK, SFH_EDOMAIN))
 
 
 def sfh_ctx_info(ctx: int) -> dict:

@@ -32,6 +32,8 @@ static sfh_status cuda_fail(cudaError_t e, const char *what) {
 static void clear_err() { g_err[0] = '\0'; }
 
 extern "C" const char *sfh_last_error(void) { return g_err; }
+
+void sfh::set_error_message(const char *msg) { snprintf(g_err, sizeof g_err, "%s", msg); }
 extern "C" int sfh_version(void) { return 10000; }
 
 // ---------------------------------------------------------------------------

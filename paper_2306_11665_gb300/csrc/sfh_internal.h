@@ -29,6 +29,9 @@ SFH_DECL_VJP(vjp_d2)
 SFH_DECL_VJP(vjp_d3)
 #undef SFH_DECL_VJP
 
+// Set the calling thread's message returned by sfh_last_error().
+void set_error_message(const char *msg);
+
 // Elements per CTA of the forward kernel for a (d, n, flux, mode): the unit
 // in which the serving runtime cuts requests into tiles.
 int volume_epb(int mode, int d, int n, int flux);

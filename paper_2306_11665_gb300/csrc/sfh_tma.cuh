@@ -84,21 +84,21 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // FP64 -> FP32 by integer operations (IEEE-754 field arithmetic), so that the
-// conversion does not occupy the FP64 pipe.  Rounds to nearest with ties away
-// from zero; magnitudes below the FP32 normal range give a signed zero and
-// magnitudes at or above 2^128 give infinity (metric terms are O(h^{d-1})).
+// conversion does not occupy the FP64 pipe.  On the magnitude m (sign removed):
+// adding 2^28 rounds the 29 discarded mantissa bits half away from zero (the
+// carry may ripple into the exponent, which is the correct rounding), the
+// funnel shift by 3 lines the exponent up with bit 23 of the high word, and
+// subtracting 896 << 23 re-biases it (1023 -> 127; the modular arithmetic is
+// exact because the FP32 exponent fits 8 bits).  Magnitudes below the FP32
+// normal range give a signed zero; inputs must stay below 2^128 (metric
+// terms are O(h^{d-1})).
 __device__ __forceinline__ float d2f_int(double x) {
     const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
-    const uint32_t hi = static_cast<uint32_t>(b >> 32), lo = static_cast<uint32_t>(b);
-    const uint32_t sign = hi & 0x80000000u;
-    const uint32_t mag = hi & 0x7fffffffu;
-    // exponent re-bias (1023 -> 127 is 896 << 20 in the high word), then the
-    // 64-bit field shifted left by 3 lines the exponent up with bit 23
-    uint32_t f = __funnelshift_l(lo, mag - 0x38000000u, 3);
-    f += (lo >> 28) & 1u;
-    f = mag < 0x38100000u ? 0u : f;
-    f = mag >= 0x47f00000u ? 0x7f800000u : f;
-    return __uint_as_float(f | sign);
+    const unsigned long long mag = (b & 0x7fffffffffffffffull) + (1ull << 28);
+    const uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
+    uint32_t f = __funnelshift_l(lo, hi, 3) - 0xc0000000u;   // (896 << 23) mod 2^32
+    f = hi < 0x38100000u ? 0u : f;
+    return __uint_as_float(f | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
 }
 
 // ---------------------------------------------------------------------------

@@ -280,13 +280,16 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                 pe[(D + 1) * NN] = p;
                 pe[(D + 2) * NN] = bt;
                 bad |= !(rho > 0.0f && p > 0.0f);
+                // the node's d*d metric values, FP64 -> FP32 (same [el][m][k][i] layout)
+                const double *je = J + el * J_EL + i;
+                float *jf = sJF + el * J_EL + i;
+#pragma unroll
+                for (int q = 0; q < D * D; ++q) jf[q * NN] = d2f_int(je[q * NN]);
             } else {
                 pe[0] = ue[0];
             }
         }
-        if constexpr (FLUX == kFluxEuler) {
-            for (int s = tid; s < ne * J_EL; s += blockDim.x) sJF[s] = d2f_int(J[s]);
-        } else {
+        if constexpr (FLUX != kFluxEuler) {
             for (int s = tid; s < ne * D * NN; s += blockDim.x) {
                 const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
                 const double *jm = J + ((el * D + m) * D) * NN + i;
@@ -297,7 +300,6 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
             }
         }
         if (bad) atomicOr(err, kErrDomain);
-        if (tid == 0) bulk_wait_read_all();   // the previous block's r store has left sR
         __syncthreads();
 
         // ---- 3. prefetch the next block into the raw buffers
@@ -328,24 +330,34 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                     base = m == 0 ? N * l : l;
                     omega = tab.w[l];
                 }
-                KahanF acc[N][NVAR];
-#pragma unroll
-                for (int a = 0; a < N; ++a)
-#pragma unroll
-                    for (int v = 0; v < NVAR; ++v) acc[a][v].zero();
                 const float *pe = sP + el * NP * NN + base;
                 bool oob = false;   // a pair outside the series band was met
                 if constexpr (FLUX == kFluxEuler) {
-                    const float *je = sJF + (el * D + m) * D * NN + base;
-                    float rho[N], hv[N][D], p[N], beta[N];
+                    // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
+                    constexpr int NPAIR = NVAR / 2;
+                    KahanF2 accp[N][NPAIR];
+                    KahanF acc4[N];
 #pragma unroll
                     for (int a = 0; a < N; ++a) {
-                        rho[a] = pe[a * stride];
+#pragma unroll
+                        for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
+                        acc4[a].zero();
+                    }
+                    const float *je = sJF + (el * D + m) * D * NN + base;
+                    float2 rb[N];          // (rho, beta)
+                    float hv[N][D], p[N];
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+                        rb[a] = f2(pe[a * stride], pe[(D + 2) * NN + a * stride]);
 #pragma unroll
                         for (int k = 0; k < D; ++k) hv[a][k] = pe[(1 + k) * NN + a * stride];
                         p[a] = pe[(D + 1) * NN + a * stride];
-                        beta[a] = pe[(D + 2) * NN + a * stride];
                     }
+                    // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean) as one packed Horner chain
+                    const float cg = (float)(2.0 / (kGamma - 1.0));
+                    const float2 c0 = f2(0.5f, cg), c1 = f2(0.5f * (-1.0f / 3.0f), cg * (1.0f / 3.0f));
+                    const float2 c2 = f2(0.5f * (-4.0f / 45.0f), cg * (1.0f / 5.0f));
+                    const float2 c3 = f2(0.5f * (-44.0f / 945.0f), cg * (1.0f / 7.0f));
 #pragma unroll
                     for (int a = 0; a < N; ++a) {
 #pragma unroll
@@ -353,7 +365,6 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                             float n[D];
 #pragma unroll
                             for (int k = 0; k < D; ++k) n[k] = je[k * NN + a * stride] + je[k * NN + b * stride];
-                            // half normal velocities hv.n, half-velocity product
                             float hna = hv[a][0] * n[0], hnb = hv[b][0] * n[0], hvv = hv[a][0] * hv[b][0];
 #pragma unroll
                             for (int k = 1; k < D; ++k) {
@@ -361,33 +372,43 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                                 hnb = fmaf(hv[b][k], n[k], hnb);
                                 hvv = fmaf(hv[a][k], hv[b][k], hvv);
                             }
-                            // {rho}_ln = (s/2) S(t^2); 1/{beta}_ln = (2/s) P(t^2)
-                            // logarithmic means by the series (no branch in the
-                            // common case); a pair outside the band |a-b| < 0.1 (a+b)
-                            // is recomputed from the logarithm in a rarely taken branch
-                            const float dr = rho[a] - rho[b], sr = rho[a] + rho[b];
-                            const float db = beta[a] - beta[b], sb = beta[a] + beta[b];
-                            const float tr = dr * __fdividef(1.0f, sr);
-                            float rs = __fdividef(1.0f, sb);
-                            rs = fmaf(rs, fmaf(-sb, rs, 1.0f), rs);    // 1/s scales the energy flux: one Newton step
-                            const float tb = db * rs;
-                            const float Lr = (0.5f * sr) * series_S(tr * tr);
-                            const float iLb = (2.0f * rs) * series_P(tb * tb);
-                            oob |= !(fabsf(dr) < 0.1f * sr) || !(fabsf(db) < 0.1f * sb);
-                            float F[D + 2];
-                            const float frho = Lr * (hna + hnb);          // {rho}_ln {v.n}
+                            // both logarithmic means at once (.x: rho, .y: beta), by the series;
+                            // a pair outside the band |a-b| < 0.1 (a+b) sends the line to the general routine
+                            const float2 d2 = sub2(rb[a], rb[b]), s2 = add2(rb[a], rb[b]);
+                            float2 r2 = f2(__fdividef(1.0f, s2.x), __fdividef(1.0f, s2.y));
+                            r2 = fma2(r2, fma2(sub2(f2s(0.0f), s2), r2, f2s(1.0f)), r2);   // one Newton step
+                            const float2 t2 = mul2(d2, r2);
+                            const float2 u2 = mul2(t2, t2);
+                            float2 h = fma2(u2, c3, c2);
+                            h = fma2(u2, h, c1);
+                            h = fma2(u2, h, c0);
+                            oob |= !(fabsf(d2.x) < 0.1f * s2.x) || !(fabsf(d2.y) < 0.1f * s2.y);
+                            const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
+                            const float frho = m2.x * (hna + hnb);      // {rho}_ln {v.n}
                             const float pavg = 0.5f * (p[a] + p[b]);
-                            F[0] = frho;
-#pragma unroll
-                            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(frho, hv[a][k] + hv[b][k], pavg * n[k]);
-                            // energy: frho (v_a.v_b / 2 + 1/((g-1){beta}_ln)) + (p_a v_b.n + p_b v_a.n)/2
-                            const float K = fmaf(2.0f, hvv, iLb * (float)(1.0 / (kGamma - 1.0)));
-                            F[D + 1] = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            float2 F01, F23;
+                            F01.x = frho;
+                            F01.y = fmaf(frho, hv[a][0] + hv[b][0], pavg * n[0]);
+                            float FE;
+                            const float K = fmaf(2.0f, hvv, m2.y);
+                            if constexpr (D == 3) {
+                                F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
+                                F23.y = fmaf(frho, hv[a][2] + hv[b][2], pavg * n[2]);
+                                FE = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            } else {
+                                F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
+                                F23.y = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                                FE = 0.0f;
+                            }
                             const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
-#pragma unroll
-                            for (int v = 0; v < NVAR; ++v) {
-                                acc[a][v].add_prod(qab, F[v]);
-                                acc[b][v].add_prod(qba, F[v]);
+                            const float2 qa2 = f2s(qab), qb2 = f2s(qba);
+                            accp[a][0].add_prod(qa2, F01);
+                            accp[b][0].add_prod(qb2, F01);
+                            accp[a][1].add_prod(qa2, F23);
+                            accp[b][1].add_prod(qb2, F23);
+                            if constexpr (D == 3) {
+                                acc4[a].add_prod(qab, FE);
+                                acc4[b].add_prod(qba, FE);
                             }
                         }
                         const float qaa = tab.Q1[a * N + a];
@@ -400,16 +421,36 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
 #pragma unroll
                             for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
                             float F[D + 2];
-                            const float frho = 2.0f * rho[a] * hn;
+                            const float frho = 2.0f * rb[a].x * hn;
                             F[0] = frho;
 #pragma unroll
                             for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], p[a] * n[k]);
                             F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
+                            const float2 qq = f2s(qaa);
+                            accp[a][0].add_prod(qq, f2(F[0], F[1]));
+                            accp[a][1].add_prod(qq, f2(F[2], F[3]));
+                            if constexpr (D == 3) acc4[a].add_prod(qaa, F[4]);
+                        }
+                    }
+                    float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+                    if (__builtin_expect(oob, 0)) {
+                        // rare: redo the whole line with logarithms where needed
+                        euler_line_general<D, N, NN, NP>(pe, je, re, stride, omega, tab);
+                    } else {
 #pragma unroll
-                            for (int v = 0; v < NVAR; ++v) acc[a][v].add_prod(qaa, F[v]);
+                        for (int a = 0; a < N; ++a) {
+                            const float2 v01 = accp[a][0].value(), v23 = accp[a][1].value();
+                            re[0 * NN + a * stride] = omega * v01.x;
+                            re[1 * NN + a * stride] = omega * v01.y;
+                            re[2 * NN + a * stride] = omega * v23.x;
+                            re[3 * NN + a * stride] = omega * v23.y;
+                            if constexpr (D == 3) re[4 * NN + a * stride] = omega * acc4[a].value();
                         }
                     }
                 } else {
+                    KahanF acc[N][NVAR];
+#pragma unroll
+                    for (int a = 0; a < N; ++a) acc[a][0].zero();
                     const float *je = sJF + (el * D + m) * NN + base;
                     float uu[N], Sm[N];
 #pragma unroll
@@ -425,47 +466,23 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                         const float qaa = tab.Q1[a * N + a];
                         if (qaa != 0.0f) acc[a][0].add_prod(qaa, uu[a] * uu[a] * Sm[a]);
                     }
-                }
-                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
-                if constexpr (FLUX == kFluxEuler) {
-                    if (__builtin_expect(oob, 0)) {
-                        // rare: redo the whole line with logarithms where needed
-                        euler_line_general<D, N, NN, NP>(sP + el * NP * NN + base, sJF + (el * D + m) * D * NN + base,
-                                                         re, stride, omega, tab);
-                    }
-                }
-                if (!oob) {
+                    float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
 #pragma unroll
-                    for (int a = 0; a < N; ++a)
-#pragma unroll
-                        for (int v = 0; v < NVAR; ++v) re[v * NN + a * stride] = omega * acc[a][v].value();
+                    for (int a = 0; a < N; ++a) re[a * stride] = omega * acc[a][0].value();
                 }
             }
         }
         __syncthreads();
 
-        // ---- 5. sum the directions in a fixed order, store r
-        for (int s = tid; s < ne * U_EL; s += blockDim.x) {
-            float t = sR[s] + sR[EPB * U_EL + s];
-            if constexpr (D == 3) t += sR[2 * EPB * U_EL + s];
-            sR[s] = t;
-        }
-        __syncthreads();
+        // ---- 5. sum the directions in a fixed order and store r
         float *gR = r + cur.e0 * U_EL;
-        const uint32_t rbytes = (uint32_t)ne * U_EL * 4;
-        const bool bulk = aligned_bases && (reinterpret_cast<uintptr_t>(gR) & 15) == 0 && (rbytes & 15) == 0;
-        if (bulk) {
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                bulk_store(gR, sR, rbytes);
-                bulk_commit();
-            }
-        } else {
-            for (int s = tid; s < ne * U_EL; s += blockDim.x) gR[s] = sR[s];
+        for (int s2 = tid; s2 < ne * U_EL; s2 += blockDim.x) {
+            float t = sR[s2] + sR[EPB * U_EL + s2];
+            if constexpr (D == 3) t += sR[2 * EPB * U_EL + s2];
+            gR[s2] = t;
         }
         cur = nx;
     }
-    if (tid == 0) bulk_wait_all();
 }
 
 // grid: one resident CTA per SM slot (persistent); occupancy is queried once
