@@ -177,6 +177,83 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0):
+    """Serving stream: n_req requests, n_elem log-uniform in [64, 4096], p uniform
+    in {2..8} (Gauss-Lobatto), 70% FP32 / 30% FP64 residuals (a vjp_share of
+    them VJPs instead), states and metrics resident, 40 GB admission budget.
+    Capacity = all requests released at once; then Poisson arrivals at the given
+    fractions of capacity; p50/p99 latency = submit -> done.  Baseline: the same
+    requests as serial single-request FP64 launches."""
+    from paper_2306_11665_gb300.serve import Server
+    rng = np.random.default_rng(seed)
+    dev = torch.device("cuda")
+    pools = {}
+    for p in range(2, 9):
+        u64, Ja = I.workload(3, p, 0, 16, seed0=2 + p)                  # 4096 elements per degree
+        pools[p] = dict(u64=torch.from_numpy(u64).to(dev), u32=torch.from_numpy(I.to_fp32(u64)).to(dev),
+                        Ja=torch.from_numpy(Ja).to(dev),
+                        lam=torch.from_numpy(I.cotangent(u64.shape, seed=100 + p)).to(dev))
+    specs = []
+    for _ in range(n_req):
+        ne = int(round(math.exp(rng.uniform(math.log(64), math.log(4096)))))
+        p = int(rng.integers(2, 9))
+        vjp = rng.uniform() < vjp_share
+        prec = A.SFH_FP64 if (vjp or rng.uniform() >= 0.7) else A.SFH_FP32_KAHAN
+        specs.append((ne, p, prec, vjp))
+    outs = []
+    reqs = []
+    dof = 0
+    for ne, p, prec, vjp in specs:
+        P = pools[p]
+        u = P["u64"] if prec == A.SFH_FP64 else P["u32"]
+        out = torch.empty((ne,) + tuple(u.shape[1:]), dtype=u.dtype, device=dev)
+        outs.append(out)
+        reqs.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, 0, prec, ne, u.data_ptr(),
+                              P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None, out.data_ptr()))
+        dof += ne * (p + 1) ** 3
+    res = {"requests": n_req, "dof_total": dof, "vjp_share": vjp_share}
+    with Server(hbm_budget_bytes=40 << 30, max_inflight=64, timeout_ms=120000) as srv:
+        A.sfh_serve_replay(srv.handle, reqs[:50], [0.0] * 50, 60000)           # warm-up
+        r = A.sfh_serve_replay(srv.handle, reqs, [0.0] * n_req, 120000)
+        assert all(x.status == A.SFH_OK for x in r)
+        span = (max(x.t_done_ns for x in r) - min(x.t_submit_ns for x in r)) * 1e-9
+        cap = dof / span
+        res["capacity_dof_per_s"] = cap
+        res["capacity_req_per_s"] = n_req / span
+        for load in loads:
+            rate = load * n_req / span
+            arr = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
+            arr -= arr[0]
+            r = A.sfh_serve_replay(srv.handle, reqs, arr.tolist(), 120000)
+            assert all(x.status == A.SFH_OK for x in r)
+            lat = np.array([(x.t_done_ns - x.t_submit_ns) * 1e-6 for x in r])
+            span_l = (max(x.t_done_ns for x in r) - min(x.t_submit_ns for x in r)) * 1e-9
+            res[f"load_{int(load * 100)}"] = {"p50_ms": float(np.percentile(lat, 50)),
+                                              "p99_ms": float(np.percentile(lat, 99)),
+                                              "dof_per_s": dof / span_l, "offered_req_per_s": rate}
+    # serial single-request FP64 launches of the same stream
+    ctxs = {p: api.Context(3, p, "gll", "euler") for p in range(2, 9)}
+    stream = torch.cuda.current_stream()
+    lat = []
+    t_all = time.perf_counter()
+    for (ne, p, prec, vjp), out in zip(specs, outs):
+        P = pools[p]
+        o64 = torch.empty((ne, 5, (p + 1) ** 3), dtype=torch.float64, device=dev)
+        t0 = time.perf_counter()
+        if vjp:
+            A.sfh_vjp(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), o64.data_ptr(),
+                      stream.cuda_stream)
+        else:
+            A.sfh_volume_residual(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), o64.data_ptr(),
+                                  A.SFH_FP64, stream.cuda_stream)
+        stream.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e3)
+    t_all = time.perf_counter() - t_all
+    res["serial_fp64"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "dof_per_s": dof / t_all}
+    return res
+
+
 def timed_launches(fn, steps, warmup, stream, torch):
     """Run `fn` warmup + steps times on `stream`; returns (total_ms, mean_launch_ms)."""
     for _ in range(warmup):
@@ -204,6 +281,7 @@ def main():
     ap.add_argument("--p", type=int, default=None, help="override the degree (exploration only)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -325,6 +403,9 @@ def main():
         _, tv = timed_launches(stepvjp, k64, 2, stream, torch)
         variants["vjp_fp64"] = {"element_dof_per_s": dof / (tv * 1e-3), "ms": tv, "forward_fp64_ms": t64}
         assert ctx.check() == A.SFH_OK
+        if not args.no_serve:
+            variants["serve"] = serve_bench(torch, A, I, api)
+            variants["serve_vjp20"] = serve_bench(torch, A, I, api, n_req=1000, loads=(0.8,), vjp_share=0.2)
 
     clocks = sampler.stop()
 

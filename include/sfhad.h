@@ -231,6 +231,16 @@ sfh_status sfh_serve_submit(sfh_server *srv, const sfh_request *req, uint64_t *t
  * unknown ticket.  A ticket can be polled done once. */
 sfh_status sfh_serve_poll(sfh_server *srv, uint64_t ticket, sfh_result *out);
 
+/* Replay a request stream: request i is submitted at arrival_s[i] seconds
+ * after the call starts (arrival_s ascending), completions are polled while
+ * the stream is fed, and results[i] receives request i's result (timestamps
+ * included; a request refused at submission carries that status).  Blocks
+ * until every request is done (SFH_OK) or timeout_ms passes (SFH_ETIMEOUT).
+ * The load generator of the serving benchmark: a native loop keeps up with
+ * arrival rates a scripting-language client cannot. */
+sfh_status sfh_serve_replay(sfh_server *srv, int n, const sfh_request *reqs, const double *arrival_s,
+                            sfh_result *results, int timeout_ms);
+
 /* Block until every submitted request is done or timeout_ms passes
  * (SFH_ETIMEOUT). */
 sfh_status sfh_serve_drain(sfh_server *srv, int timeout_ms);

@@ -66,6 +66,8 @@ _SIGS = {
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
     "sfh_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(Result)],
     "sfh_serve_drain": [vp, ctypes.c_int],
+    "sfh_serve_replay": [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
+                         ctypes.POINTER(Result), ctypes.c_int],
     "sfh_server_destroy": [vp],
 }
 
@@ -179,6 +181,16 @@ def sfh_serve_poll(srv: int, ticket: int):
     res = Result()
     st = _call("sfh_serve_poll", srv, ticket, ctypes.byref(res), ok=(SFH_OK, SFH_ENOTREADY))
     return res if st == SFH_OK else None
+
+
+def sfh_serve_replay(srv: int, reqs, arrival_s, timeout_ms: int):
+    """Replay requests (a list of Request) at the given arrival times; returns the Results."""
+    n = len(reqs)
+    R = (Request * n)(*reqs)
+    T = (ctypes.c_double * n)(*arrival_s)
+    out = (Result * n)()
+    _call("sfh_serve_replay", srv, n, R, T, out, timeout_ms)
+    return list(out)
 
 
 def sfh_serve_drain(srv: int, timeout_ms: int) -> None:

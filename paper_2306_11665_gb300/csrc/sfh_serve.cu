@@ -1,11 +1,662 @@
-// sfh_serve.cu -- serving runtime (placeholder until the runtime lands).
-#include "../../include/sfhad.h"
+// sfh_serve.cu -- serving runtime: continuous batching of residual and VJP
+// requests (3D Euler, Ranocha flux, p = 2..8, mixed precision) through one
+// persistent kernel.
+//
+// Data path
+//   * The host admission thread takes requests FIFO as long as the HBM budget
+//     and the in-flight limit allow, writes the request's descriptor into a
+//     slot table and one descriptor per element tile into a ring, both in
+//     page-locked host memory mapped into the device address space, and
+//     publishes them by advancing the ring's tail (release store).
+//   * Persistent CTAs (one per SM by default) claim ring entries with a
+//     compare-and-swap on a device-side head counter -- only entries below the
+//     published tail -- and run the tile with the body of the request's class
+//     (kind x precision x degree).  Tiles of requests that arrive while
+//     others run are claimed as soon as they are published, so their work
+//     interleaves on the GPU.
+//   * A per-request tile counter on the device finds the last tile; its CTA
+//     publishes the request's completion record (status, sequence number) to
+//     host-mapped memory after a system-scope fence.
+//   * CTAs that find no work for idle_ns (bounded also by an iteration cap)
+//     exit; the host relaunches the kernel whenever work is in flight and the
+//     kernel is not running, so a claim can never be stranded.
+// All device waits are bounded; no wait can hang the GPU.
+#include <cuda_runtime.h>
 
-extern "C" sfh_status sfh_server_create(const sfh_server_opts *, sfh_server **out) {
-    if (out) *out = nullptr;
-    return SFH_EUNSUPPORTED;
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sfhad.h"
+#include "sfh_internal.h"
+#include "sfh_tma.cuh"
+#include "sfh_volume.cuh"
+#include "sfh_vjp.cuh"
+
+namespace sfh {
+namespace serve {
+
+constexpr int kThreads = 256;
+constexpr int kMaxSlots = 256;
+constexpr uint64_t kRing = 1ull << 18;
+constexpr int kPMin = 2, kPMax = 8;
+
+struct Tile {
+    int32_t slot;
+    int32_t tile;
+};
+
+struct __align__(16) Req {   // written by the host before the request's tiles are published
+    int32_t kind, prec, n, nodes;
+    const void *u;
+    const double *Ja;
+    const double *lam;
+    void *out;
+    int32_t n_elem, epb, ntiles;
+    uint32_t seq;
+};
+static_assert(sizeof(Req) == 64, "descriptor read as four 16-byte words");
+
+struct Done {  // written by the device
+    uint32_t seq;
+    int32_t status;
+};
+
+struct DevCtrl {   // device memory
+    unsigned long long head;
+    int idle_ctas;     // CTAs that found nothing to claim for the quiet window
+    int quit;          // set once every CTA is idle: the whole kernel leaves
+    int done_tiles[kMaxSlots];
+    int err[kMaxSlots];
+};
+
+struct Args {
+    const Tile *ring;                        // mapped
+    const Req *reqs;                         // mapped
+    Done *done;                              // mapped
+    const volatile unsigned long long *tail; // mapped
+    const volatile int *stop;                // mapped
+    DevCtrl *ctrl;                           // device
+    const OpTab<double> *tabd;               // device [2][10] (nodes, n)
+    const OpTab<float> *tabf;
+    unsigned long long idle_ns;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const volatile unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
-extern "C" sfh_status sfh_serve_submit(sfh_server *, const sfh_request *, uint64_t *) { return SFH_EUNSUPPORTED; }
-extern "C" sfh_status sfh_serve_poll(sfh_server *, uint64_t, sfh_result *) { return SFH_EUNSUPPORTED; }
-extern "C" sfh_status sfh_serve_drain(sfh_server *, int) { return SFH_EUNSUPPORTED; }
-extern "C" sfh_status sfh_server_destroy(sfh_server *) { return SFH_OK; }
+
+// ---- per-class tile bodies (all 3D Euler) --------------------------------
+template <int N> struct Cls {
+    using F64 = Shape<3, N, kFluxEuler, ModeFP64>;
+    using F32 = Shape<3, N, kFluxEuler, ModeFP32K>;
+    using MIX = Shape<3, N, kFluxEuler, ModeMixed>;
+    using VJP = VjpShape<3, N, kFluxEuler>;
+};
+
+template <int N> constexpr size_t cls_smem() {
+    size_t a = Cls<N>::F64::SMEM, b = Cls<N>::F32::SMEM, c = Cls<N>::MIX::SMEM, d = Cls<N>::VJP::SMEM;
+    size_t m = a > b ? a : b;
+    m = m > c ? m : c;
+    return m > d ? m : d;
+}
+constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
+constexpr size_t kSmem = cmax(cmax(cmax(cls_smem<3>(), cls_smem<4>()), cmax(cls_smem<5>(), cls_smem<6>())),
+                              cmax(cmax(cls_smem<7>(), cls_smem<8>()), cls_smem<9>()));
+static_assert(kSmem <= 200 * 1024, "serving shared memory");
+
+// elements per tile of a class (host and device agree through this function)
+__host__ __device__ inline int tile_epb(int kind, int prec, int n) {
+#define SFH_EPB_CASE(N)                                                    \
+    case N:                                                                \
+        if (kind == SFH_REQ_VJP) return Cls<N>::VJP::EPB;                  \
+        if (prec == SFH_FP64) return Cls<N>::F64::EPB;                     \
+        if (prec == SFH_FP32_KAHAN) return Cls<N>::F32::EPB;               \
+        return Cls<N>::MIX::EPB;
+    switch (n) {
+        SFH_EPB_CASE(3) SFH_EPB_CASE(4) SFH_EPB_CASE(5) SFH_EPB_CASE(6) SFH_EPB_CASE(7) SFH_EPB_CASE(8)
+        SFH_EPB_CASE(9)
+    }
+#undef SFH_EPB_CASE
+    return 1;
+}
+
+template <int N>
+__device__ __noinline__ void run_tile(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
+                                         const OpTab<float> &tf, int *err, unsigned char *smem) {
+    if (q.kind == SFH_REQ_VJP) {
+        vjp_tile<3, N, kFluxEuler>(static_cast<const double *>(q.u), q.Ja, q.lam, static_cast<double *>(q.out), e0,
+                                   ne, td, err, smem);
+    } else if (q.prec == SFH_FP64) {
+        volume_tile<3, N, kFluxEuler, ModeFP64>(static_cast<const double *>(q.u), q.Ja, static_cast<double *>(q.out),
+                                                e0, ne, td, err, smem);
+    } else if (q.prec == SFH_FP32_KAHAN) {
+        volume_tile<3, N, kFluxEuler, ModeFP32K>(static_cast<const float *>(q.u), q.Ja, static_cast<float *>(q.out),
+                                                 e0, ne, tf, err, smem);
+    } else {
+        volume_tile<3, N, kFluxEuler, ModeMixed>(static_cast<const float *>(q.u), q.Ja, static_cast<float *>(q.out),
+                                                 e0, ne, tf, err, smem);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constant__ Args a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ Req s_req;
+    __shared__ int s_tile, s_slot, s_exit;
+    __shared__ OpTab<double> s_td;
+    __shared__ OpTab<float> s_tf;
+
+    // Idle exit is all-or-nothing: a CTA that found nothing to claim for idle_ns
+    // counts itself idle (and uncounts itself when work appears); the kernel
+    // leaves only when every CTA is idle, so a lull never thins out the CTAs
+    // of a kernel that keeps running.  The host relaunches it for new work.
+    unsigned long long last_tail = 0;
+    uint64_t quiet_since = global_timer_ns();
+    bool counted_idle = false;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            s_exit = 1;
+            for (uint32_t it = 0; it < (1u << 28); ++it) {
+                const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(&a.ctrl->head);
+                const unsigned long long t = ld_acquire_sys_u64(a.tail);
+                if (t != last_tail) {
+                    last_tail = t;
+                    quiet_since = global_timer_ns();
+                }
+                if (h < t) {
+                    if (counted_idle) {
+                        atomicSub(&a.ctrl->idle_ctas, 1);
+                        counted_idle = false;
+                    }
+                    if (atomicCAS(&a.ctrl->head, h, h + 1) == h) {
+                        const volatile Tile *te = a.ring + (h % kRing);
+                        const int slot = te->slot;
+                        s_tile = te->tile;
+                        // the 64-byte descriptor in four 16-byte volatile loads
+                        const volatile uint4 *src = reinterpret_cast<const volatile uint4 *>(a.reqs + slot);
+                        uint4 *dst = reinterpret_cast<uint4 *>(&s_req);
+#pragma unroll
+                        for (int w = 0; w < 4; ++w) {
+                            uint4 v;
+                            v.x = src[w].x; v.y = src[w].y; v.z = src[w].z; v.w = src[w].w;
+                            dst[w] = v;
+                        }
+                        s_slot = slot;
+                        s_exit = 0;
+                        break;
+                    }
+                    continue;
+                }
+                if (*a.stop || *reinterpret_cast<volatile int *>(&a.ctrl->quit)) break;
+                if ((it & 15u) == 15u) {
+                    if (!counted_idle && global_timer_ns() - quiet_since > a.idle_ns) {
+                        atomicAdd(&a.ctrl->idle_ctas, 1);
+                        counted_idle = true;
+                    }
+                    if (counted_idle && *reinterpret_cast<volatile int *>(&a.ctrl->idle_ctas) >= (int)gridDim.x) {
+                        atomicExch(&a.ctrl->quit, 1);
+                        break;
+                    }
+                }
+                __nanosleep(256);
+            }
+        }
+        __syncthreads();
+        if (s_exit) return;
+        const Req &q = s_req;
+        const int slot = s_slot;
+        const int tabi = q.nodes * 10 + q.n;
+        for (int i = threadIdx.x; i < (int)(sizeof(OpTab<double>) / 8); i += blockDim.x)
+            reinterpret_cast<double *>(&s_td)[i] = reinterpret_cast<const double *>(a.tabd + tabi)[i];
+        for (int i = threadIdx.x; i < (int)(sizeof(OpTab<float>) / 4); i += blockDim.x)
+            reinterpret_cast<float *>(&s_tf)[i] = reinterpret_cast<const float *>(a.tabf + tabi)[i];
+        __syncthreads();
+        const int64_t e0 = (int64_t)s_tile * q.epb;
+        const int ne = (int)((q.n_elem - e0) < q.epb ? (q.n_elem - e0) : q.epb);
+        int *err = &a.ctrl->err[slot];
+        switch (q.n) {
+            case 3: run_tile<3>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 4: run_tile<4>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 5: run_tile<5>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 6: run_tile<6>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 7: run_tile<7>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 8: run_tile<8>(q, e0, ne, s_td, s_tf, err, smem); break;
+            case 9: run_tile<9>(q, e0, ne, s_td, s_tf, err, smem); break;
+            default: break;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();   // this tile's output before the count
+            const int done = atomicAdd(&a.ctrl->done_tiles[slot], 1) + 1;
+            if (done == q.ntiles) {
+                __threadfence();
+                const int st = atomicExch(&a.ctrl->err[slot], 0);
+                a.ctrl->done_tiles[slot] = 0;
+                __threadfence_system();
+                volatile Done *dn = a.done + slot;
+                dn->status = st ? (st & kErrTimeout ? SFH_ETIMEOUT : SFH_EDOMAIN) : SFH_OK;
+                __threadfence_system();
+                dn->seq = q.seq;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace serve
+}  // namespace sfh
+
+// ---------------------------------------------------------------------------
+// host runtime
+// ---------------------------------------------------------------------------
+using namespace sfh::serve;
+
+namespace {
+
+uint64_t now_ns() {
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+struct Pending {
+    uint64_t ticket;
+    sfh_request req;
+    size_t bytes;
+    int epb, ntiles;
+    uint64_t t_submit;
+};
+
+struct Inflight {
+    uint64_t ticket;
+    size_t bytes;
+    int ntiles;
+    uint32_t seq;
+    uint64_t t_submit, t_admit;
+};
+
+size_t req_bytes(const sfh_request &r) {
+    const size_t nn = (size_t)(r.p + 1) * (r.p + 1) * (r.p + 1);
+    const size_t esz = (r.kind == SFH_REQ_VJP || r.prec == SFH_FP64) ? 8 : 4;
+    size_t b = (size_t)r.n_elem * nn * (2 * 5 * esz + 9 * sizeof(double));
+    if (r.kind == SFH_REQ_VJP) b += (size_t)r.n_elem * nn * 5 * sizeof(double);
+    return b;
+}
+
+}  // namespace
+
+struct sfh_server {
+    sfh_server_opts opts;
+    int device;
+    int n_workers;
+    // mapped host memory
+    Tile *ring_h;
+    Req *reqs_h;
+    Done *done_h;
+    volatile unsigned long long *tail_h;
+    volatile int *stop_h;
+    Args args;
+    DevCtrl *ctrl_d;
+    sfh::OpTab<double> *tabd_d;
+    sfh::OpTab<float> *tabf_d;
+    cudaStream_t stream;
+    // host state
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Pending> pending;
+    Inflight slots[kMaxSlots];
+    bool slot_busy[kMaxSlots];
+    uint32_t slot_seq[kMaxSlots];
+    int inflight = 0;
+    size_t used_bytes = 0;
+    uint64_t tiles_live = 0;
+    uint64_t tail = 0;
+    uint64_t next_ticket = 1;
+    std::unordered_map<uint64_t, sfh_result> results;
+    std::unordered_map<uint64_t, int> where;   // 0 pending, 1 inflight, 2 done
+    bool quit = false;
+    bool kernel_error = false;
+    std::thread worker;
+};
+
+namespace {
+
+sfh_status launch(sfh_server *s) {
+    // a fresh kernel starts with no idle CTAs and no exit decision
+    if (cudaMemsetAsync(&s->ctrl_d->idle_ctas, 0, 2 * sizeof(int), s->stream) != cudaSuccess) return SFH_ECUDA;
+    serve_kernel<<<s->n_workers, kThreads, kSmem, s->stream>>>(s->args);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SFH_OK : SFH_ECUDA;
+}
+
+void admission_loop(sfh_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        // completions
+        for (int k = 0; k < s->opts.max_inflight; ++k) {
+            if (!s->slot_busy[k]) continue;
+            const volatile Done *dn = s->done_h + k;
+            if (dn->seq != s->slots[k].seq) continue;
+            std::atomic_thread_fence(std::memory_order_acquire);
+            sfh_result r;
+            r.status = dn->status;
+            r.t_submit_ns = s->slots[k].t_submit;
+            r.t_admit_ns = s->slots[k].t_admit;
+            r.t_done_ns = now_ns();
+            s->results[s->slots[k].ticket] = r;
+            s->where[s->slots[k].ticket] = 2;
+            s->slot_busy[k] = false;
+            s->used_bytes -= s->slots[k].bytes;
+            s->tiles_live -= (uint64_t)s->slots[k].ntiles;
+            --s->inflight;
+            s->cv.notify_all();
+        }
+        // admissions, FIFO
+        while (!s->pending.empty() && s->inflight < s->opts.max_inflight) {
+            Pending &pq = s->pending.front();
+            if (s->used_bytes + pq.bytes > s->opts.hbm_budget_bytes) break;
+            if (s->tiles_live + (uint64_t)pq.ntiles > kRing) break;
+            int k = 0;
+            while (s->slot_busy[k]) ++k;
+            const uint32_t seq = ++s->slot_seq[k];
+            Req &q = s->reqs_h[k];
+            q.kind = pq.req.kind;
+            q.prec = pq.req.kind == SFH_REQ_VJP ? SFH_FP64 : pq.req.prec;
+            q.n = pq.req.p + 1;
+            q.nodes = pq.req.nodes;
+            q.n_elem = (int32_t)pq.req.n_elem;
+            q.u = pq.req.u;
+            q.Ja = pq.req.Ja;
+            q.lam = pq.req.lambda;
+            q.out = pq.req.out;
+            q.epb = pq.epb;
+            q.ntiles = pq.ntiles;
+            q.seq = seq;
+            for (int t = 0; t < pq.ntiles; ++t) {
+                Tile &te = s->ring_h[(s->tail + t) % kRing];
+                te.slot = k;
+                te.tile = t;
+            }
+            std::atomic_thread_fence(std::memory_order_release);
+            s->tail += (uint64_t)pq.ntiles;
+            *s->tail_h = s->tail;
+            Inflight &f = s->slots[k];
+            f.ticket = pq.ticket;
+            f.bytes = pq.bytes;
+            f.ntiles = pq.ntiles;
+            f.seq = seq;
+            f.t_submit = pq.t_submit;
+            f.t_admit = now_ns();
+            s->slot_busy[k] = true;
+            s->where[pq.ticket] = 1;
+            s->used_bytes += pq.bytes;
+            s->tiles_live += (uint64_t)pq.ntiles;
+            ++s->inflight;
+            s->pending.pop_front();
+        }
+        // keep the persistent kernel alive while work is in flight
+        if (s->inflight > 0 && !s->kernel_error) {
+            const cudaError_t q = cudaStreamQuery(s->stream);
+            if (q == cudaSuccess) {
+                if (launch(s) != SFH_OK) s->kernel_error = true;
+            } else if (q != cudaErrorNotReady) {
+                s->kernel_error = true;
+            }
+        }
+        if (s->kernel_error) {
+            // fail everything in flight: the device cannot be trusted to finish it
+            for (int k = 0; k < s->opts.max_inflight; ++k) {
+                if (!s->slot_busy[k]) continue;
+                sfh_result r = {SFH_ECUDA, s->slots[k].t_submit, s->slots[k].t_admit, now_ns()};
+                s->results[s->slots[k].ticket] = r;
+                s->where[s->slots[k].ticket] = 2;
+                s->slot_busy[k] = false;
+                s->used_bytes -= s->slots[k].bytes;
+                s->tiles_live -= (uint64_t)s->slots[k].ntiles;
+                --s->inflight;
+            }
+            s->cv.notify_all();
+        }
+        if (s->quit && s->pending.empty() && s->inflight == 0) break;
+        if (s->inflight == 0 && s->pending.empty()) {
+            s->cv.wait_for(lk, std::chrono::milliseconds(2));
+        } else {
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::microseconds(20));
+            lk.lock();
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" sfh_status sfh_server_create(const sfh_server_opts *opts, sfh_server **out) {
+    if (!out) return SFH_EINVAL;
+    *out = nullptr;
+    if (!opts || opts->max_inflight < 1 || opts->max_inflight > kMaxSlots || opts->timeout_ms < 1 ||
+        opts->hbm_budget_bytes == 0 || opts->n_workers < 0)
+        return SFH_EINVAL;
+    sfh_server *s = new (std::nothrow) sfh_server();
+    if (!s) return SFH_ENOMEM;
+    s->opts = *opts;
+    cudaError_t e = cudaGetDevice(&s->device);
+    int sms = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, s->device);
+    if (e != cudaSuccess) { delete s; return SFH_ECUDA; }
+    s->n_workers = opts->n_workers > 0 ? opts->n_workers : sms;
+    memset(s->slot_busy, 0, sizeof s->slot_busy);
+    memset(s->slot_seq, 0, sizeof s->slot_seq);
+    // mapped host memory for the ring, descriptors, completions and control words
+    const size_t hbytes = sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots + sizeof(Done) * kMaxSlots + 64;
+    void *h = nullptr;
+    if ((e = cudaHostAlloc(&h, hbytes, cudaHostAllocMapped)) != cudaSuccess) { delete s; return SFH_ENOMEM; }
+    memset(h, 0, hbytes);
+    char *hc = static_cast<char *>(h);
+    s->ring_h = reinterpret_cast<Tile *>(hc);
+    s->reqs_h = reinterpret_cast<Req *>(hc + sizeof(Tile) * kRing);
+    s->done_h = reinterpret_cast<Done *>(hc + sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots);
+    s->tail_h = reinterpret_cast<volatile unsigned long long *>(hc + hbytes - 64);
+    s->stop_h = reinterpret_cast<volatile int *>(hc + hbytes - 32);
+    void *dh = nullptr;
+    if ((e = cudaHostGetDevicePointer(&dh, h, 0)) != cudaSuccess) { cudaFreeHost(h); delete s; return SFH_ECUDA; }
+    char *dc = static_cast<char *>(dh);
+    s->args.ring = reinterpret_cast<const Tile *>(dc);
+    s->args.reqs = reinterpret_cast<const Req *>(dc + sizeof(Tile) * kRing);
+    s->args.done = reinterpret_cast<Done *>(dc + sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots);
+    s->args.tail = reinterpret_cast<const volatile unsigned long long *>(dc + hbytes - 64);
+    s->args.stop = reinterpret_cast<const volatile int *>(dc + hbytes - 32);
+    s->args.idle_ns = 2000000ull;   // 2 ms without work: CTAs leave, the host relaunches on demand
+    // device: control block and operator tables for every (node set, n)
+    if ((e = cudaMalloc(&s->ctrl_d, sizeof(DevCtrl))) != cudaSuccess ||
+        (e = cudaMalloc(&s->tabd_d, sizeof(sfh::OpTab<double>) * 20)) != cudaSuccess ||
+        (e = cudaMalloc(&s->tabf_d, sizeof(sfh::OpTab<float>) * 20)) != cudaSuccess) {
+        cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFreeHost(h); delete s; return SFH_ENOMEM;
+    }
+    cudaMemset(s->ctrl_d, 0, sizeof(DevCtrl));
+    std::vector<sfh::OpTab<double>> td(20);
+    std::vector<sfh::OpTab<float>> tf(20);
+    memset(td.data(), 0, sizeof(sfh::OpTab<double>) * 20);
+    memset(tf.data(), 0, sizeof(sfh::OpTab<float>) * 20);
+    for (int nodes = 0; nodes < 2; ++nodes)
+        for (int p = kPMin; p <= kPMax; ++p) {
+            double xi[sfh::NMAX], w[sfh::NMAX], D[sfh::NMAX * sfh::NMAX], Q1[sfh::NMAX * sfh::NMAX];
+            sfh_operator_tables(p, (sfh_nodes)nodes, xi, w, D, Q1);
+            const int n = p + 1, k = nodes * 10 + n;
+            for (int a = 0; a < n; ++a) {
+                td[k].w[a] = w[a];
+                tf[k].w[a] = (float)w[a];
+                for (int b = 0; b < n; ++b) {
+                    td[k].Q1[a * n + b] = Q1[a * n + b];
+                    tf[k].Q1[a * n + b] = (float)Q1[a * n + b];
+                }
+            }
+        }
+    cudaMemcpy(s->tabd_d, td.data(), sizeof(sfh::OpTab<double>) * 20, cudaMemcpyHostToDevice);
+    cudaMemcpy(s->tabf_d, tf.data(), sizeof(sfh::OpTab<float>) * 20, cudaMemcpyHostToDevice);
+    s->args.ctrl = s->ctrl_d;
+    s->args.tabd = s->tabd_d;
+    s->args.tabf = s->tabf_d;
+    if ((e = cudaFuncSetAttribute(serve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFree(s->tabf_d); cudaFreeHost(h); delete s; return SFH_ECUDA;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        cudaStreamDestroy(s->stream); cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFree(s->tabf_d);
+        cudaFreeHost(h); delete s; return SFH_ECUDA;
+    }
+    s->worker = std::thread(admission_loop, s);
+    *out = s;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_serve_submit(sfh_server *s, const sfh_request *r, uint64_t *ticket) {
+    if (!s || !r || !ticket) return SFH_EINVAL;
+    if (r->kind != SFH_REQ_RESIDUAL && r->kind != SFH_REQ_VJP) return SFH_EINVAL;
+    if (r->p < kPMin || r->p > kPMax || (r->nodes != SFH_NODES_GLL && r->nodes != SFH_NODES_GAUSS)) return SFH_EINVAL;
+    if (r->kind == SFH_REQ_RESIDUAL && r->prec != SFH_FP64 && r->prec != SFH_FP32_KAHAN && r->prec != SFH_FP32_MIXED)
+        return SFH_EINVAL;
+    if (r->n_elem < 1 || r->n_elem > (int64_t)1 << 30 || !r->u || !r->Ja || !r->out || (r->kind == SFH_REQ_VJP && !r->lambda)) return SFH_EINVAL;
+    const bool f64 = r->kind == SFH_REQ_VJP || r->prec == SFH_FP64;
+    const uintptr_t al = f64 ? 8 : 4;
+    if (((uintptr_t)r->u | (uintptr_t)r->out) % al || (uintptr_t)r->Ja % 8 ||
+        (r->kind == SFH_REQ_VJP && (uintptr_t)r->lambda % 8))
+        return SFH_EINVAL;
+    Pending pq;
+    pq.req = *r;
+    pq.bytes = req_bytes(*r);
+    if (pq.bytes > s->opts.hbm_budget_bytes) return SFH_ENOMEM;
+    pq.epb = tile_epb(r->kind, r->kind == SFH_REQ_VJP ? SFH_FP64 : r->prec, r->p + 1);
+    const int64_t nt = (r->n_elem + pq.epb - 1) / pq.epb;
+    if (nt > (int64_t)kRing) return SFH_ENOMEM;
+    pq.ntiles = (int)nt;
+    pq.t_submit = now_ns();
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->quit) return SFH_EBUSY;
+    pq.ticket = s->next_ticket++;
+    s->where[pq.ticket] = 0;
+    s->pending.push_back(pq);
+    *ticket = pq.ticket;
+    s->cv.notify_all();
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_serve_poll(sfh_server *s, uint64_t ticket, sfh_result *out) {
+    if (!s || !out) return SFH_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto w = s->where.find(ticket);
+    if (w == s->where.end()) return SFH_EINVAL;
+    if (w->second != 2) return SFH_ENOTREADY;
+    *out = s->results[ticket];
+    s->results.erase(ticket);
+    s->where.erase(w);
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_serve_drain(sfh_server *s, int timeout_ms) {
+    if (!s) return SFH_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const bool ok = s->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                   [s] { return s->pending.empty() && s->inflight == 0; });
+    return ok ? SFH_OK : SFH_ETIMEOUT;
+}
+
+extern "C" sfh_status sfh_server_destroy(sfh_server *s) {
+    if (!s) return SFH_OK;
+    sfh_status st = sfh_serve_drain(s, s->opts.timeout_ms);
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->quit = true;
+        if (st != SFH_OK) {   // give up on what is left: nothing more is admitted
+            s->pending.clear();
+        }
+        s->cv.notify_all();
+    }
+    *s->stop_h = 1;
+    // the admission thread ends once nothing is in flight (bounded by the drain above)
+    const uint64_t t0 = now_ns();
+    while (true) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (s->inflight == 0) break;
+        }
+        if (now_ns() - t0 > (uint64_t)s->opts.timeout_ms * 1000000ull) { st = SFH_ETIMEOUT; break; }
+        std::this_thread::sleep_for(std::chrono::milliseconds(1));
+    }
+    if (st == SFH_OK) {
+        s->worker.join();
+    } else {
+        s->worker.detach();   // the runtime cannot be reclaimed safely; report it
+        return SFH_ETIMEOUT;
+    }
+    // the persistent kernel leaves on the stop word; wait for it, bounded
+    const uint64_t t1 = now_ns();
+    while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
+        if (now_ns() - t1 > (uint64_t)s->opts.timeout_ms * 1000000ull) return SFH_ETIMEOUT;
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    cudaStreamDestroy(s->stream);
+    cudaFree(s->ctrl_d);
+    cudaFree(s->tabd_d);
+    cudaFree(s->tabf_d);
+    cudaFreeHost(s->ring_h);   // base of the mapped allocation
+    delete s;
+    return st;
+}
+
+extern "C" sfh_status sfh_serve_replay(sfh_server *s, int n, const sfh_request *reqs, const double *arrival_s,
+                                       sfh_result *results, int timeout_ms) {
+    if (!s || n < 0 || (n > 0 && (!reqs || !arrival_s || !results)) || timeout_ms < 1) return SFH_EINVAL;
+    std::vector<uint64_t> tickets((size_t)n, 0);
+    std::vector<int> open;            // submitted, not yet done
+    open.reserve((size_t)n);
+    int n_done = 0, next = 0;
+    const uint64_t t0 = now_ns();
+    for (int i = 0; i < n; ++i) results[i].status = SFH_ENOTREADY;
+    while (n_done < n) {
+        const uint64_t now = now_ns();
+        // submit everything whose arrival time has come
+        while (next < n && now >= t0 + (uint64_t)(arrival_s[next] * 1e9)) {
+            const sfh_status st = sfh_serve_submit(s, &reqs[next], &tickets[next]);
+            if (st != SFH_OK) {
+                results[next] = sfh_result{st, now, now, now};
+                ++n_done;
+            } else {
+                open.push_back(next);
+            }
+            ++next;
+        }
+        // collect completions under one lock acquisition per sweep
+        if (!open.empty()) {
+            std::lock_guard<std::mutex> lk(s->mu);
+            size_t w = 0;
+            for (size_t k = 0; k < open.size(); ++k) {
+                const int i = open[k];
+                auto it = s->where.find(tickets[i]);
+                if (it != s->where.end() && it->second == 2) {
+                    results[i] = s->results[tickets[i]];
+                    s->results.erase(tickets[i]);
+                    s->where.erase(it);
+                    ++n_done;
+                } else {
+                    open[w++] = i;
+                }
+            }
+            open.resize(w);
+        }
+        if (now_ns() - t0 > (uint64_t)timeout_ms * 1000000ull) return SFH_ETIMEOUT;
+        const uint64_t due = next < n ? t0 + (uint64_t)(arrival_s[next] * 1e9) : UINT64_MAX;
+        const uint64_t t = now_ns();
+        if (due > t + 30000) std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+    return SFH_OK;
+}

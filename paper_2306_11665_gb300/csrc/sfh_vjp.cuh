@@ -76,21 +76,18 @@ __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *P
     gb[D + 2] += Lb_bar * Lbb;
 }
 
+// One tile of ne (<= EPB) elements from e0, processed by the whole CTA.
 template <int D, int N, int FLUX>
-__global__ void __launch_bounds__(VjpShape<D, N, FLUX>::THREADS)
-vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const double *__restrict__ lam,
-           double *__restrict__ g, int64_t n_elem, const __grid_constant__ OpTab<double> tab,
-           int *__restrict__ err) {
+__device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const double *__restrict__ Ja,
+                                         const double *__restrict__ lam, double *__restrict__ g, int64_t e0, int ne,
+                                         const OpTab<double> &tab, int *__restrict__ err, unsigned char *smem_raw) {
     using S = VjpShape<D, N, FLUX>;
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     double *sP = reinterpret_cast<double *>(smem_raw);   // [EPB][NP][NN]
     double *sA = sP + EPB * NP * NN;                       // [EPB][NP][NN] adjoints of primitives
     double *sL = sA + EPB * NP * NN;                       // [EPB][NVAR][NN] lambda
     double *sJ = sL + EPB * NVAR * NN;                     // [EPB][D][NN]
 
-    const int64_t e0 = (int64_t)blockIdx.x * EPB;
-    const int ne = (int)((n_elem - e0) < EPB ? (n_elem - e0) : EPB);
     const double *ub = u + e0 * NVAR * NN;
     const double *lb = lam + e0 * NVAR * NN;
 
@@ -218,6 +215,18 @@ vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const do
             ge[0] = ae[0];
         }
     }
+}
+
+template <int D, int N, int FLUX>
+__global__ void __launch_bounds__(VjpShape<D, N, FLUX>::THREADS)
+vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const double *__restrict__ lam,
+           double *__restrict__ g, int64_t n_elem, const __grid_constant__ OpTab<double> tab,
+           int *__restrict__ err) {
+    using S = VjpShape<D, N, FLUX>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
+    const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
+    vjp_tile<D, N, FLUX>(u, Ja, lam, g, e0, ne, tab, err, smem_raw);
 }
 
 template <int D, int N, int FLUX>

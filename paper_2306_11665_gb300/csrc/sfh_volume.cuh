@@ -139,18 +139,21 @@ __device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, t
     F[D + 1] = frho * ((T)0.5 * v2) + A.p * vn * (T)(kGamma / (kGamma - 1.0));
 }
 
+// One tile: the ne (<= EPB) consecutive elements starting at e0, processed by
+// the whole CTA (any blockDim; every thread must call it).  smem_raw holds
+// Shape::SMEM bytes.  Used by volume_kernel (one tile per CTA) and by the
+// persistent serving kernel (tiles of many requests).
 template <int D, int N, int FLUX, class M>
-__global__ void __launch_bounds__(Shape<D, N, FLUX, M>::THREADS)
-volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
-              typename M::T *__restrict__ r, int64_t n_elem,
-              const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err) {
+__device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
+                                            typename M::T *__restrict__ r, int64_t e0, int ne,
+                                            const OpTab<typename M::T> &tab, int *__restrict__ err,
+                                            unsigned char *smem_raw) {
     using S = Shape<D, N, FLUX, M>;
     using T = typename M::T;
     using TJ = typename M::TJ;
     using Acc = typename AccOf<M>::type;
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
 
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     // layout: [beta_d (mixed)] [J: EPB][D][NN] TJ  [P: EPB][NP][NN] T  [R: EPB][NVAR][NN] T
     //         (FP64 Euler: [rho_f: EPB][NN] [beta_f: EPB][NN] float in place of beta_d)
     constexpr bool F64E = S::F64E;
@@ -161,8 +164,6 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
     T *sP = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sJ) + sizeof(TJ) * EPB * D * NN);
     T *sR = sP + EPB * NP * NN;
 
-    const int64_t e0 = (int64_t)blockIdx.x * EPB;
-    const int ne = (int)((n_elem - e0) < EPB ? (n_elem - e0) : EPB);
     const T *ub = u + e0 * NVAR * NN;
 
     // ---- 1. stage primitives, zero the residual
@@ -339,6 +340,18 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
     // ---- 3. write r (layout [el][v][i] matches the global layout)
     T *rb = r + e0 * NVAR * NN;
     for (int s = threadIdx.x; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
+}
+
+template <int D, int N, int FLUX, class M>
+__global__ void __launch_bounds__(Shape<D, N, FLUX, M>::THREADS)
+volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
+              typename M::T *__restrict__ r, int64_t n_elem,
+              const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err) {
+    using S = Shape<D, N, FLUX, M>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
+    const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
+    volume_tile<D, N, FLUX, M>(u, Ja, r, e0, ne, tab, err, smem_raw);
 }
 
 // Host-side launcher for one (D, N, FLUX, mode) instance.
