@@ -62,6 +62,29 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
     return 2 * nvar * esz + d * d * 8
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
+# ncu capture of the timed kernel, valid only while the kernel sources are the
+# ones that were profiled (their SHA-1 is recorded with the figure).
+TRAFFIC = {}
+
+
+def _kernel_sources_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2306_11665_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cuh", ".cu", ".h")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(prec, p, kind, N):
+    rec = TRAFFIC.get((prec, p, kind, N))
+    if rec and rec["sha1"] == _kernel_sources_sha1():
+        return rec["bytes"]
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -278,7 +301,12 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--p", type=int, default=None, help="override the degree (exploration only)")
+    ap.add_argument("--p", type=int, default=None, help="degree of the timed workload (default 4)")
+    ap.add_argument("--N", type=int, default=None, help="elements per direction of the timed workload (default 32)")
+    ap.add_argument("--nodes", default="gll", choices=["gll", "gauss"])
+    ap.add_argument("--prec", default="fp32k", choices=["fp32k", "fp64", "fp32mix", "vjp"],
+                    help="what the timed step runs (default: the FP32-Kahan residual)")
+    ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
@@ -288,9 +316,9 @@ def main():
         return run_reference(args)
 
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_2306_11665_gb300 import dist as D
+    rank, world, local = D.rank_world()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -307,12 +335,14 @@ def main():
         dist.barrier()
 
     W = dict(WORKLOAD)
-    if args.p is not None:
-        W["p"] = args.p
-        W["name"] = f"euler3d_p{args.p}_gll_32cubed_warped"
+    if args.p is not None or args.N is not None or args.nodes != "gll":
+        W["p"] = args.p if args.p is not None else W["p"]
+        W["N"] = args.N if args.N is not None else W["N"]
+        W["kind"] = 0 if args.nodes == "gll" else 1
+        W["name"] = f"euler3d_p{W['p']}_{args.nodes}_{W['N']}cubed_warped"
     d, p, kind, N = W["d"], W["p"], W["kind"], W["N"]
     nn = (p + 1) ** d
-    u64, Ja = I.workload(d, p, kind, N, seed0=2 + 10 * rank)   # each rank its own block
+    u64, Ja = I.workload(d, p, kind, N, seed0=D.weak_block_seed(rank))   # each rank its own block
     E = u64.shape[0]
     dof = E * nn
     dev = torch.device("cuda", local)
@@ -329,8 +359,17 @@ def main():
         os.environ.get("CUDA_VISIBLE_DEVICES") else str(local)
     sampler = ClockSampler(gpu_idx)
 
+    lam_main = torch.from_numpy(I.cotangent(u64.shape, seed=8)).to(dev) if args.prec == "vjp" else None
+
     def step32():
-        A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_KAHAN, sh)
+        if args.prec == "fp32k":
+            A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_KAHAN, sh)
+        elif args.prec == "fp32mix":
+            A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_MIXED, sh)
+        elif args.prec == "fp64":
+            A.sfh_volume_residual(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), r64.data_ptr(), A.SFH_FP64, sh)
+        else:
+            A.sfh_vjp(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), lam_main.data_ptr(), r64.data_ptr(), sh)
 
     # ---- headline: FP32-Kahan residual, K steps
     for _ in range(args.warmup):
@@ -344,22 +383,29 @@ def main():
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-        tt = torch.tensor([t_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_total = float(tt.item())
+        t_total = D.max_over_ranks(t_total, dist, dev)
     assert ctx.check() == A.SFH_OK
     ms_step = t_total / args.steps
-    value = world * dof / (ms_step * 1e-3)
+    value = D.aggregate_throughput(dof, world, ms_step * 1e-3)
 
     peaks = load_peaks() or {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    b32 = bytes_per_node("fp32k", d) * dof
-    roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": None,
-                "peak_source": hbm_src, "kernel": "volume_kernel<3,%d,euler,FP32K>" % (p + 1),
-                "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     fl = flops_per_element(d, p, kind) * E
+    if args.prec in ("fp32k", "fp32mix"):
+        b32 = bytes_per_node("fp32k", d) * dof
+        roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": measured_traffic(args.prec, p, kind, N),
+                    "peak_source": hbm_src, "kernel": "volume_fp32_tma_kernel<3,%d,euler>" % (p + 1),
+                    "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
+    else:
+        # FP64 arithmetic binds: the ALU roofline against the nominal FP64 rate
+        # (1.25 TFLOP/s; our FMA-chain microbenchmark measures the same)
+        flv = fl * (3.0 if args.prec == "vjp" else 1.0)
+        roofline = {"bound": "alu", "achieved": flv / (t_launch * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": flv / (t_launch * 1e-3) / 1e12 / 1.25, "traffic": measured_traffic(args.prec, p, kind, N),
+                    "peak_source": "nominal FP64 rate of the recipe table", "kernel": args.prec,
+                    "algorithmic_flops_per_launch": flv, "launch_ms": t_launch}
 
     variants = {}
     if not args.no_variants:
@@ -373,14 +419,20 @@ def main():
         nominal32 = 152 * 128 * 2 * 2.07e9 / 1e12
         variants["alu_peaks_tflops"] = {"fp64_measured": fp64_tf, "fp32_measured": fp32_tf,
                                         "fp64_nominal": nominal64, "fp32_nominal": round(nominal32, 1)}
-        variants["fp32k"] = {"element_dof_per_s": value / world, "ms": t_launch,
-                             "flops_per_launch": fl,
-                             "alu_frac_of_nominal": fl / (t_launch * 1e-3) / (nominal32 * 1e12),
-                             "hbm_frac_of_measured": roofline["frac"]}
+        k64 = max(5, min(50, args.steps // 20))
+        t32 = t_launch
+        if args.prec != "fp32k":
+            def s32():
+                A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(),
+                                      A.SFH_FP32_KAHAN, sh)
+            _, t32 = timed_launches(s32, k64, 2, stream, torch)
+        b32v = bytes_per_node("fp32k", d) * dof
+        variants["fp32k"] = {"element_dof_per_s": dof / (t32 * 1e-3), "ms": t32, "flops_per_launch": fl,
+                             "alu_frac_of_nominal": fl / (t32 * 1e-3) / (nominal32 * 1e12),
+                             "hbm_frac_of_measured": b32v / (t32 * 1e-3) / 1e9 / hbm_peak}
 
         def step64():
             A.sfh_volume_residual(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), r64.data_ptr(), A.SFH_FP64, sh)
-        k64 = max(5, min(50, args.steps // 20))
         _, t64 = timed_launches(step64, k64, 2, stream, torch)
         b64 = bytes_per_node("fp64", d) * dof
         variants["fp64"] = {"element_dof_per_s": dof / (t64 * 1e-3), "ms": t64, "flops_per_launch": fl,
@@ -410,24 +462,35 @@ def main():
     clocks = sampler.stop()
 
     # ---- end to end through the host-buffer C-ABI entry point (pinned memory)
-    uh = torch.from_numpy(I.to_fp32(u64)).pin_memory()
+    # (the residual in the timed precision; the adjoint has no host-buffer form)
+    e2e = None
+    if args.no_e2e or args.prec == "vjp":
+        return finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, None, clocks, variants, u64, Ja, d, p,
+                      kind, torch)
+    eprec = {"fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED, "fp64": A.SFH_FP64}[args.prec]
+    uh = torch.from_numpy(u64 if args.prec == "fp64" else I.to_fp32(u64)).pin_memory()
     Jh = torch.from_numpy(Ja).pin_memory()
     rh = torch.empty_like(uh).pin_memory()
     ke = max(3, min(20, args.steps // 100))
     for _ in range(2):
-        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), A.SFH_FP32_KAHAN)
+        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), eprec)
     t0 = time.perf_counter()
     for _ in range(ke):
-        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), A.SFH_FP32_KAHAN)
+        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), eprec)
     te = (time.perf_counter() - t0) / ke
     if dist:
-        tt = torch.tensor([te], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        te = float(tt.item())
-    e2e = {"value": world * dof / te, "unit": "element-DOF/s",
-           "h2d_bytes_per_step": int(uh.numel() * 4 + Jh.numel() * 8), "d2h_bytes_per_step": int(rh.numel() * 4),
+        te = D.max_over_ranks(te, dist, dev)
+    e2e = {"value": D.aggregate_throughput(dof, world, te), "unit": "element-DOF/s",
+           "h2d_bytes_per_step": int(uh.numel() * uh.element_size() + Jh.numel() * 8),
+           "d2h_bytes_per_step": int(rh.numel() * rh.element_size()),
            "ms_per_step": te * 1e3, "api": "sfh_volume_residual_host (pinned host buffers)"}
 
+    return finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clocks, variants, u64, Ja, d, p,
+                  kind, torch)
+
+
+def finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clocks, variants, u64, Ja, d, p, kind,
+           torch):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cores = os.cpu_count() or 1
@@ -438,9 +501,12 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f64" if args.prec in ("fp64", "vjp") else "f32", "data": "synthetic",
                 "config": {"workload": W["name"], "elements_per_gpu": E, "nodes_per_element": nn,
-                           "precision": "fp32 kahan (FP64 metric input)", "l2": "inputs larger than L2 (459 MB per step)",
+                           "precision": {"fp32k": "fp32 kahan (FP64 metric input)", "fp64": "fp64",
+                                         "fp32mix": "fp32 with fp64 log mean/metric sums",
+                                         "vjp": "fp64 adjoint (VJP)"}[args.prec],
+                           "l2": "inputs larger than L2" if E * nn * 112 > 129e6 else "inputs smaller than L2",
                            "parallelism": f"replicas x{world} (independent element blocks)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": args.steps, "variants": variants}
