@@ -38,6 +38,11 @@ METRIC = "element-DOF/s of 3D Euler volume residual"
 GAMMA_DIAG = 30          # algorithmic flops of one diagonal (physical-flux) term incl. accumulation
 PAIR_FLOPS = 92          # algorithmic flops of one off-diagonal pair (see flops_per_element)
 NODE_FLOPS = 13          # conservative -> primitive per node
+# FP64 flops of one pair in the mixed mode (both log means inside the near-equal
+# band, where the mixed mode evaluates them in FP64): metric sum 3; ln mean:
+# band test 5, quotient 2, series 14, scaling 2 -> 23; inverse ln mean: band
+# test 5, reciprocal and quotient 3, series 16, scaling 2 -> 26.
+MIX_PAIR_FP64_FLOPS = 52
 
 
 def flops_per_element(d: int, p: int, kind: int) -> float:
@@ -55,6 +60,11 @@ def flops_per_element(d: int, p: int, kind: int) -> float:
     return pairs * PAIR_FLOPS + lines * ndiag * GAMMA_DIAG + n ** d * (NODE_FLOPS + 10 * d)
 
 
+def pairs_per_element(d: int, p: int) -> int:
+    n = p + 1
+    return d * n ** (d - 1) * n * (n - 1) // 2
+
+
 def bytes_per_node(prec: str, d: int = 3) -> int:
     """Algorithmic HBM bytes per node: read u and Ja, write r."""
     nvar = d + 2
@@ -65,7 +75,14 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the timed kernel, valid only while the kernel sources are the
 # ones that were profiled (their SHA-1 is recorded with the figure).
-TRAFFIC = {}
+TRAFFIC = {
+    # (prec, p, nodes, N): ncu capture of the timed kernel, launch 2 of
+    # `bench.py --steps 3 --warmup 1 --no-variants --no-cpu --no-e2e` (+ workload flags)
+    ("fp32k", 4, 0, 32): {"bytes": 377_800_192 + 67_253_760, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
+    ("fp64", 4, 0, 32): {"bytes": 458_950_400 + 139_741_184, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
+    ("fp32k", 7, 1, 16): {"bytes": 193_145_344 + 26_364_672, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
+    ("vjp", 5, 0, 8): {"bytes": 16_863_488 + 0, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
+}
 
 
 def _kernel_sources_sha1():
@@ -151,7 +168,10 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # the oracle as CPU baseline (threads: ctypes releases the GIL)
 # ---------------------------------------------------------------------------
-def oracle_throughput(u, Ja, d, p, kind, elems, threads):
+def oracle_throughput(u, Ja, d, p, kind, elems, threads, lam=None):
+    """The oracle as it stands (volume residual, or its VJP when a cotangent is
+    given) over the first `elems` elements, split over `threads` host threads
+    (the oracle releases the GIL inside its C routines)."""
     import concurrent.futures as cf
 
     import oracle as O
@@ -161,12 +181,29 @@ def oracle_throughput(u, Ja, d, p, kind, elems, threads):
 
     def work(ix):
         if ix.size:
-            O.volume_sf(d, p, kind, O.FLUX_EULER, u[ix[0]:ix[-1] + 1], Ja[ix[0]:ix[-1] + 1])
+            a, b = ix[0], ix[-1] + 1
+            if lam is None:
+                O.volume_sf(d, p, kind, O.FLUX_EULER, u[a:b], Ja[a:b])
+            else:
+                O.vjp_sf(d, p, kind, O.FLUX_EULER, u[a:b], Ja[a:b], lam[a:b])
     t0 = time.perf_counter()
     with cf.ThreadPoolExecutor(threads) as ex:
         list(ex.map(work, chunks))
     dt = time.perf_counter() - t0
     return E * (p + 1) ** d / dt, dt, E
+
+
+def oracle_baseline(u, Ja, d, p, kind, threads, lam=None, min_s=10.0, max_passes=400):
+    """Bounded CPU baseline: whole passes over the workload until at least
+    `min_s` seconds of oracle time (one pass minimum, `max_passes` at most)."""
+    n_el = u.shape[0]
+    dof, t, passes = 0, 0.0, 0
+    while passes < max_passes and (passes == 0 or t < min_s):
+        _, dt, E = oracle_throughput(u, Ja, d, p, kind, n_el, threads, lam)
+        dof += E * (p + 1) ** d
+        t += dt
+        passes += 1
+    return dof / t, t, passes
 
 
 def run_reference(args):
@@ -177,8 +214,12 @@ def run_reference(args):
     from paper_2306_11665_gb300 import inputs as I
     W = WORKLOAD
     cores = os.cpu_count() or 1
-    sample_el = 4096                      # a bounded sample of the workload per step
-    x_u, x_J = I.workload(W["d"], W["p"], W["kind"], W["N"], n_elem=sample_el)
+    nn = (W["p"] + 1) ** W["d"]
+    x_u, x_J = I.workload(W["d"], W["p"], W["kind"], W["N"], n_elem=4096)
+    # size each step's sample so that warm-up + timed steps take about two minutes
+    r0, _, _ = oracle_throughput(x_u, x_J, W["d"], W["p"], W["kind"], 512, cores)
+    per_step_s = 120.0 / max(1, args.steps + args.warmup)
+    sample_el = int(min(4096, max(64, r0 * per_step_s / nn)))
     vals = []
     for _ in range(args.warmup):
         oracle_throughput(x_u, x_J, W["d"], W["p"], W["kind"], sample_el, cores)
@@ -186,13 +227,14 @@ def run_reference(args):
         v, dt, E = oracle_throughput(x_u, x_J, W["d"], W["p"], W["kind"], sample_el, cores)
         vals.append(dt)
     t = sum(vals) / len(vals)
-    value = sample_el * (W["p"] + 1) ** W["d"] / t
+    value = sample_el * nn / t
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": W["name"], "sample_elements_per_step": sample_el, "threads": cores},
             "cpu_baseline": {"value": value, "unit": "element-DOF/s", "cores": cores, "kind": "oracle",
-                             "sample": f"first {sample_el} of 32768 elements per step, FP64 oracle, {cores} threads"},
+                             "sample": f"first {sample_el} of {W['N'] ** W['d']} elements per step, FP64 oracle, "
+                                       f"{cores} threads"},
             "e2e": {"value": value, "unit": "element-DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -392,12 +434,19 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     fl = flops_per_element(d, p, kind) * E
-    if args.prec in ("fp32k", "fp32mix"):
+    if args.prec == "fp32k":
         b32 = bytes_per_node("fp32k", d) * dof
         roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": measured_traffic(args.prec, p, kind, N),
-                    "peak_source": hbm_src, "kernel": "volume_fp32_tma_kernel<3,%d,euler>" % (p + 1),
+                    "peak_source": hbm_src, "kernel": "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
+    elif args.prec == "fp32mix":
+        # the FP64 log means bind the mixed mode: ALU roofline of the FP64 pipe
+        flm = pairs_per_element(d, p) * MIX_PAIR_FP64_FLOPS * E
+        roofline = {"bound": "alu", "achieved": flm / (t_launch * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s",
+                    "frac": flm / (t_launch * 1e-3) / 1e12 / 1.25, "traffic": measured_traffic(args.prec, p, kind, N),
+                    "peak_source": "nominal FP64 rate of the recipe table", "kernel": "volume_kernel<mixed> (FP64 part)",
+                    "algorithmic_flops_per_launch": flm, "launch_ms": t_launch}
     else:
         # FP64 arithmetic binds: the ALU roofline against the nominal FP64 rate
         # (1.25 TFLOP/s; our FMA-chain microbenchmark measures the same)
@@ -493,10 +542,13 @@ def finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clo
            torch):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        from paper_2306_11665_gb300 import inputs as I
         cores = os.cpu_count() or 1
-        v, dt, Es = oracle_throughput(u64, Ja, d, p, kind, 8192, cores)
+        lam = I.cotangent(u64.shape, seed=8) if args.prec == "vjp" else None
+        v, dt, passes = oracle_baseline(u64, Ja, d, p, kind, cores, lam)
         cpu = {"value": v, "unit": "element-DOF/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {Es} of {E} elements, FP64 oracle, {cores} threads, {dt:.2f} s"}
+               "sample": f"{passes} pass(es) over all {E} elements ({'VJP' if lam is not None else 'residual'}), "
+                         f"FP64 oracle, {cores} threads, {dt:.1f} s"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": world, "steps": args.steps,
