@@ -438,7 +438,8 @@ def main():
         b32 = bytes_per_node("fp32k", d) * dof
         roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": measured_traffic(args.prec, p, kind, N),
-                    "peak_source": hbm_src, "kernel": "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1),
+                    "peak_source": hbm_src, "kernel": ("volume_fp32_row_kernel<%d>" % (p + 1) if d == 3 and p + 1 in (7, 8)
+                               else "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1)),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     elif args.prec == "fp32mix":
         # the FP64 log means bind the mixed mode: ALU roofline of the FP64 pipe

@@ -6,6 +6,7 @@
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
 #include "sfh_volume_tma.cuh"
+#include "sfh_volume_row.cuh"
 
 #ifndef SFH_INST_D
 #error "SFH_INST_D must be defined"
@@ -35,6 +36,17 @@ cudaError_t SFH_CAT(vjp_d, SFH_INST_D)(int n, int flux, const double *u, const d
 
 #else
 
+#if defined(SFH_INST_FP32K)
+template <int D, int N, int FLUX>
+cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab, int *err,
+                         cudaStream_t stream) {
+    if constexpr (use_row_kernel<D, N, FLUX>())
+        return launch_volume_fp32_row<N>(u, Ja, r, n_elem, tab, err, stream);
+    else
+        return launch_volume_fp32_tma<D, N, FLUX>(u, Ja, r, n_elem, tab, err, stream);
+}
+#endif
+
 #if defined(SFH_INST_FP64)
 using Mode = ModeFP64;
 #define SFH_FN SFH_CAT(volume_fp64_d, SFH_INST_D)
@@ -52,11 +64,12 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
                    const OpTab<typename Mode::T> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
 #if defined(SFH_INST_FP32K)
-    // FP32-Kahan: the persistent TMA-staged kernel
+    // FP32-Kahan: the persistent TMA-staged kernels (a thread per line, or a
+    // thread per line and node for 3D Euler at high degree)
 #define SFH_TCASE(N)                                                                                         \
     case N:                                                                                                  \
-        return flux == kFluxEuler ? launch_volume_fp32_tma<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream) \
-                                  : launch_volume_fp32_tma<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
+        return flux == kFluxEuler ? launch_fp32k<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream)       \
+                                  : launch_fp32k<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
     switch (n) {
         SFH_TCASE(2) SFH_TCASE(3) SFH_TCASE(4) SFH_TCASE(5) SFH_TCASE(6) SFH_TCASE(7) SFH_TCASE(8) SFH_TCASE(9)
         default: return cudaErrorInvalidValue;

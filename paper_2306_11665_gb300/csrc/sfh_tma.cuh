@@ -101,6 +101,14 @@ __device__ __forceinline__ float d2f_int(double x) {
     return __uint_as_float(f | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
 }
 
+// Hardware reciprocal approximation (PTX rcp.approx.ftz.f32: at most 1 ulp
+// from 1/x for normal x; subnormal inputs and results flush to zero).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ---------------------------------------------------------------------------
 // Packed FP32x2 arithmetic (sm_100+): one instruction performs the same
 // operation on two independent FP32 lanes (here: two grid lines).

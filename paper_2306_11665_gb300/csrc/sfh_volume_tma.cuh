@@ -57,9 +57,15 @@ struct TmaShape {
     static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
     static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;      // rho, v/2 [D], p, beta | u
     static constexpr int NJ = FLUX == kFluxEuler ? D * D : D;       // FP32 metric values kept per node
+    // Euler keeps the FP32 metric rows line-major per direction,
+    // [el][m][line][a][k], so that a line's values sit at constant offsets
+    // from one base; LJ = floats per line, odd so that the lines of
+    // consecutive lanes fall in different banks
+    static constexpr int LJ = (N * D) % 2 == 0 ? N * D + 1 : N * D;
+    static constexpr int JF_EL = FLUX == kFluxEuler ? D * NLINE * LJ : D * NN;   // floats per element
     static constexpr int U_EL = NVAR * NN;                          // floats of u (and r) per element
     static constexpr int J_EL = D * D * NN;                         // doubles of Ja per element
-    static constexpr int EL_BYTES = 4 * U_EL + 8 * J_EL + 4 * NP * NN + 4 * NJ * NN + 4 * D * U_EL;
+    static constexpr int EL_BYTES = 4 * U_EL + 8 * J_EL + 4 * NP * NN + 4 * JF_EL + 4 * D * U_EL;
     static constexpr int BUDGET = (CPS == 1 ? 200 : 108) * 1024;
     static constexpr int MAX_THREADS = 128 * WPS;
     static constexpr int epb_by_smem() { return BUDGET / EL_BYTES > 0 ? BUDGET / EL_BYTES : 1; }
@@ -88,7 +94,7 @@ struct TmaShape {
     static constexpr int OFF_P = OFF_J + RAWJ_BYTES;
     static constexpr int up16(int x) { return (x + 15) / 16 * 16; }
     static constexpr int OFF_JF = up16(OFF_P + EPB * NP * NN * 4);
-    static constexpr int OFF_R = up16(OFF_JF + EPB * NJ * NN * 4);   // bulk-store source: 16-byte aligned
+    static constexpr int OFF_R = up16(OFF_JF + EPB * JF_EL * 4);   // bulk-store source: 16-byte aligned
     static constexpr size_t SMEM = OFF_R + (size_t)D * EPB * U_EL * 4;
     static_assert(OFF_U % 16 == 0 && OFF_J % 16 == 0 && OFF_R % 16 == 0, "bulk-copy buffers must be 16-byte aligned");
 };
@@ -145,7 +151,7 @@ __device__ __forceinline__ void line_geometry(int m, int l, const OpTab<float> &
 // for states with large jumps along a line; the arithmetic is that of the
 // fast path otherwise.
 template <int D, int N, int NN, int NP>
-__device__ __noinline__ void euler_line_general(const float *pe, const float *je, float *re, int stride, float omega,
+__device__ __noinline__ void euler_line_general(const float *pe, const float *jl, float *re, int stride, float omega,
                                                 const OpTab<float> &tab) {
     constexpr int NVAR = D + 2;
 #pragma unroll 1
@@ -166,7 +172,7 @@ __device__ __noinline__ void euler_line_general(const float *pe, const float *je
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 hvb[k] = pe[(1 + k) * NN + b * stride];
-                n[k] = je[k * NN + a * stride] + je[k * NN + b * stride];
+                n[k] = jl[a * D + k] + jl[b * D + k];
             }
             float hna = 0.0f, hnb = 0.0f, hvv = 0.0f;
 #pragma unroll
@@ -260,7 +266,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                 // m r (r: reciprocal seed plus one Newton step) followed by one
                 // residual correction q += r (m - rho q), each a fused op.
                 const float rho = ue[0], E = ue[(D + 1) * NN];
-                float ir = __fdividef(1.0f, rho);
+                float ir = rcp_approx(rho);
                 ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
                 float ke = 0.0f;
 #pragma unroll
@@ -272,7 +278,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                     ke = fmaf(mk, vk, ke);
                 }
                 const float p = (float)(kGamma - 1.0) * fmaf(-0.5f, ke, E);
-                float ip = __fdividef(1.0f, p);
+                float ip = rcp_approx(p);
                 ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
                 float bt = rho * ip;
                 bt = fmaf(ip, fmaf(-p, bt, rho), bt);
@@ -280,11 +286,27 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                 pe[(D + 1) * NN] = p;
                 pe[(D + 2) * NN] = bt;
                 bad |= !(rho > 0.0f && p > 0.0f);
-                // the node's d*d metric values, FP64 -> FP32 (same [el][m][k][i] layout)
+                // the node's d*d metric values, FP64 -> FP32, into the line of
+                // each direction through it: (line, position) = (i / N, i0),
+                // (i0 + N i2, i1), (i0 + N i1, i2) in 3D; (i1, i0), (i0, i1) in 2D
                 const double *je = J + el * J_EL + i;
-                float *jf = sJF + el * J_EL + i;
+                float *jl = sJF + el * S::JF_EL;
+                const int i0 = i % N;
 #pragma unroll
-                for (int q = 0; q < D * D; ++q) jf[q * NN] = d2f_int(je[q * NN]);
+                for (int m = 0; m < D; ++m) {
+                    int line, pos;
+                    if constexpr (D == 3) {
+                        const int i1 = (i / N) % N, i2 = i / (N * N);
+                        line = m == 0 ? i / N : (m == 1 ? i0 + N * i2 : i0 + N * i1);
+                        pos = m == 0 ? i0 : (m == 1 ? i1 : i2);
+                    } else {
+                        line = m == 0 ? i / N : i0;
+                        pos = m == 0 ? i0 : i / N;
+                    }
+                    float *dst = jl + (m * NLINE + line) * S::LJ + pos * D;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) dst[k] = d2f_int(je[(m * D + k) * NN]);
+                }
             } else {
                 pe[0] = ue[0];
             }
@@ -293,6 +315,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
             for (int s = tid; s < ne * D * NN; s += blockDim.x) {
                 const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
                 const double *jm = J + ((el * D + m) * D) * NN + i;
+                static_assert(FLUX == kFluxEuler || S::JF_EL == D * NN, "Burgers metric sums are node-major");
                 float acc = d2f_int(jm[0]);
 #pragma unroll
                 for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
@@ -331,7 +354,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                     omega = tab.w[l];
                 }
                 const float *pe = sP + el * NP * NN + base;
-                bool oob = false;   // a pair outside the series band was met
+                float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
                 if constexpr (FLUX == kFluxEuler) {
                     // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
                     constexpr int NPAIR = NVAR / 2;
@@ -343,7 +366,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                         for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
                         acc4[a].zero();
                     }
-                    const float *je = sJF + (el * D + m) * D * NN + base;
+                    const float *jl = sJF + el * S::JF_EL + (m * NLINE + l) * S::LJ;   // this line's metric rows
                     float2 rb[N];          // (rho, beta)
                     float hv[N][D], p[N];
 #pragma unroll
@@ -364,7 +387,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                         for (int b = a + 1; b < N; ++b) {
                             float n[D];
 #pragma unroll
-                            for (int k = 0; k < D; ++k) n[k] = je[k * NN + a * stride] + je[k * NN + b * stride];
+                            for (int k = 0; k < D; ++k) n[k] = jl[a * D + k] + jl[b * D + k];
                             float hna = hv[a][0] * n[0], hnb = hv[b][0] * n[0], hvv = hv[a][0] * hv[b][0];
 #pragma unroll
                             for (int k = 1; k < D; ++k) {
@@ -372,17 +395,20 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                                 hnb = fmaf(hv[b][k], n[k], hnb);
                                 hvv = fmaf(hv[a][k], hv[b][k], hvv);
                             }
-                            // both logarithmic means at once (.x: rho, .y: beta), by the series;
-                            // a pair outside the band |a-b| < 0.1 (a+b) sends the line to the general routine
+                            // both logarithmic means at once (.x: rho, .y: beta), by the series
+                            // in u = ((a-b)/(a+b))^2.  1/(a+b) is the hardware reciprocal
+                            // (at most 1 ulp off): it scales the inverse mean directly, an
+                            // error of the order of the FP32 rounding of the other factors.
+                            // The line leaves for the general routine if any pair has
+                            // u_rho + u_beta >= 1e-2 (which covers both u < 1e-2).
                             const float2 d2 = sub2(rb[a], rb[b]), s2 = add2(rb[a], rb[b]);
-                            float2 r2 = f2(__fdividef(1.0f, s2.x), __fdividef(1.0f, s2.y));
-                            r2 = fma2(r2, fma2(sub2(f2s(0.0f), s2), r2, f2s(1.0f)), r2);   // one Newton step
+                            const float2 r2 = f2(rcp_approx(s2.x), rcp_approx(s2.y));
                             const float2 t2 = mul2(d2, r2);
                             const float2 u2 = mul2(t2, t2);
                             float2 h = fma2(u2, c3, c2);
                             h = fma2(u2, h, c1);
                             h = fma2(u2, h, c0);
-                            oob |= !(fabsf(d2.x) < 0.1f * s2.x) || !(fabsf(d2.y) < 0.1f * s2.y);
+                            umax = fmaxf(umax, u2.x + u2.y);
                             const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
                             const float frho = m2.x * (hna + hnb);      // {rho}_ln {v.n}
                             const float pavg = 0.5f * (p[a] + p[b]);
@@ -416,7 +442,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                             // physical flux f(u_a) . (2 Ja^m(a))
                             float n[D];
 #pragma unroll
-                            for (int k = 0; k < D; ++k) n[k] = 2.0f * je[k * NN + a * stride];
+                            for (int k = 0; k < D; ++k) n[k] = 2.0f * jl[a * D + k];
                             float hn = hv[a][0] * n[0], hv2 = hv[a][0] * hv[a][0];
 #pragma unroll
                             for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
@@ -433,9 +459,11 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
                         }
                     }
                     float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
-                    if (__builtin_expect(oob, 0)) {
+                    // also false for a NaN maximum (fmaxf drops NaN operands; the
+                    // domain flag of the node pass reports the state)
+                    if (__builtin_expect(!(umax < 1e-2f), 0)) {
                         // rare: redo the whole line with logarithms where needed
-                        euler_line_general<D, N, NN, NP>(pe, je, re, stride, omega, tab);
+                        euler_line_general<D, N, NN, NP>(pe, jl, re, stride, omega, tab);
                     } else {
 #pragma unroll
                         for (int a = 0; a < N; ++a) {

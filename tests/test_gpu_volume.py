@@ -228,7 +228,7 @@ def test_host_entry_point_matches_device(prec):
     assert np.array_equal(host, dev)
 
 
-@pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 2, 1), (2, 5, 0), (3, 7, 1)])
+@pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 2, 1), (2, 5, 0), (3, 7, 1), (3, 6, 0), (3, 8, 0)])
 def test_rough_states_take_the_logarithm_path(d, p, kind):
     """States with large jumps between neighbouring nodes put many pairs
     outside the series band of the logarithmic mean (|a-b| >= 0.1 (a+b)),
