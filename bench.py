@@ -77,11 +77,8 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
 # ones that were profiled (their SHA-1 is recorded with the figure).
 TRAFFIC = {
     # (prec, p, nodes, N): ncu capture of the timed kernel, launch 2 of
-    # `bench.py --steps 3 --warmup 1 --no-variants --no-cpu --no-e2e` (+ workload flags)
-    ("fp32k", 4, 0, 32): {"bytes": 377_800_192 + 67_253_760, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
-    ("fp64", 4, 0, 32): {"bytes": 458_950_400 + 139_741_184, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
-    ("fp32k", 7, 1, 16): {"bytes": 193_145_344 + 26_364_672, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
-    ("vjp", 5, 0, 8): {"bytes": 16_863_488 + 0, "sha1": "2c03f50ec1bff2b1e97544aacad4f11eee897c82"},
+    # `bench.py --steps 3 --warmup 1 --no-variants --no-cpu --no-e2e --no-serve`
+    ("fp32k", 4, 0, 32): {"bytes": 377_454_848 + 67_406_592, "sha1": "47fea2e45379329782d5752dc5e073699eaea66e"},
 }
 
 
@@ -337,6 +334,60 @@ def timed_launches(fn, steps, warmup, stream, torch):
     return total, sum(per) / len(per)
 
 
+def other_configs(torch, A, I, api, stream, hbm_peak):
+    """The precision study (3D Euler, p = 7, Gauss, 16^3 warped) in the three
+    precision modes, and the adjoint configuration (p = 5, Gauss-Lobatto,
+    8^3 warped) with its forward residual: device-resident inputs, CUDA-event
+    mean launch times."""
+    out = {}
+    sh = stream.cuda_stream
+    dev = torch.device("cuda")
+    u64, Ja = I.workload(3, 7, 1, 16)
+    E, nn = u64.shape[0], u64.shape[2]
+    dof = E * nn
+    ctx = api.Context(3, 7, "gauss", "euler")
+    tJ = torch.from_numpy(Ja).to(dev)
+    t64 = torch.from_numpy(u64).to(dev)
+    t32 = torch.from_numpy(I.to_fp32(u64)).to(dev)
+    r64, r32 = torch.empty_like(t64), torch.empty_like(t32)
+    fl = flops_per_element(3, 7, 1) * E
+    b32 = bytes_per_node("fp32k", 3) * dof
+    res = {}
+    for name, prec, tu, tr, k in (("fp32k", A.SFH_FP32_KAHAN, t32, r32, 50), ("fp32mix", A.SFH_FP32_MIXED, t32, r32, 10),
+                                  ("fp64", A.SFH_FP64, t64, r64, 10)):
+        _, ms = timed_launches(lambda: A.sfh_volume_residual(ctx.handle, E, tu.data_ptr(), tJ.data_ptr(), tr.data_ptr(),
+                                                             prec, sh), k, 3, stream, torch)
+        res[name] = {"ms": ms, "element_dof_per_s": dof / (ms * 1e-3)}
+    res["fp32k"]["hbm_frac_of_measured"] = b32 / (res["fp32k"]["ms"] * 1e-3) / 1e9 / hbm_peak
+    res["fp64"]["alu_frac_of_fp64_rate"] = fl / (res["fp64"]["ms"] * 1e-3) / 1.25e12
+    flm = pairs_per_element(3, 7) * MIX_PAIR_FP64_FLOPS * E
+    res["fp32mix"]["alu_frac_of_fp64_rate"] = flm / (res["fp32mix"]["ms"] * 1e-3) / 1.25e12
+    assert ctx.check() == A.SFH_OK
+    out["euler3d_p7_gauss_16cubed_warped"] = res
+    ctx.close()
+
+    u64, Ja = I.workload(3, 5, 0, 8)
+    E, nn = u64.shape[0], u64.shape[2]
+    dof = E * nn
+    ctx = api.Context(3, 5, "gll", "euler")
+    tJ = torch.from_numpy(Ja).to(dev)
+    t64 = torch.from_numpy(u64).to(dev)
+    lam = torch.from_numpy(I.cotangent(u64.shape, seed=8)).to(dev)
+    r64, g = torch.empty_like(t64), torch.empty_like(t64)
+    _, tf = timed_launches(lambda: A.sfh_volume_residual(ctx.handle, E, t64.data_ptr(), tJ.data_ptr(), r64.data_ptr(),
+                                                         A.SFH_FP64, sh), 20, 3, stream, torch)
+    _, tv = timed_launches(lambda: A.sfh_vjp(ctx.handle, E, t64.data_ptr(), tJ.data_ptr(), lam.data_ptr(), g.data_ptr(),
+                                             sh), 20, 3, stream, torch)
+    assert ctx.check() == A.SFH_OK
+    fl = flops_per_element(3, 5, 0) * E
+    out["euler3d_p5_gll_8cubed_warped"] = {
+        "forward_fp64": {"ms": tf, "element_dof_per_s": dof / (tf * 1e-3), "alu_frac_of_fp64_rate": fl / (tf * 1e-3) / 1.25e12},
+        "vjp_fp64": {"ms": tv, "element_dof_per_s": dof / (tv * 1e-3),
+                     "alu_frac_of_fp64_rate_3x_forward_count": 3 * fl / (tv * 1e-3) / 1.25e12}}
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -496,7 +547,7 @@ def main():
         _, tmix = timed_launches(stepmix, k64, 2, stream, torch)
         variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix}
 
-        # adjoint on the adjoint configuration (p = 5, 8^3) and on this workload
+        # adjoint on this workload (the adjoint configuration is in other_configs)
         g = torch.empty_like(tu64)
         lam = torch.from_numpy(I.cotangent(u64.shape, seed=8)).to(dev)
 
@@ -505,6 +556,7 @@ def main():
         _, tv = timed_launches(stepvjp, k64, 2, stream, torch)
         variants["vjp_fp64"] = {"element_dof_per_s": dof / (tv * 1e-3), "ms": tv, "forward_fp64_ms": t64}
         assert ctx.check() == A.SFH_OK
+        variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
         if not args.no_serve:
             variants["serve"] = serve_bench(torch, A, I, api)
             variants["serve_vjp20"] = serve_bench(torch, A, I, api, n_req=1000, loads=(0.8,), vjp_share=0.2)

@@ -7,6 +7,7 @@
 #include "sfh_vjp.cuh"
 #include "sfh_volume_tma.cuh"
 #include "sfh_volume_row.cuh"
+#include "sfh_volume_row64.cuh"
 
 #ifndef SFH_INST_D
 #error "SFH_INST_D must be defined"
@@ -48,6 +49,28 @@ cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_ele
 #endif
 
 #if defined(SFH_INST_FP64)
+template <int D, int N, int FLUX>
+cudaError_t launch_fp64(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<double> &tab, int *err,
+                        cudaStream_t stream) {
+    // The thread-per-line kernel keeps the FP64 pipe busier on large meshes;
+    // the row kernel wins where the former's element blocks would not fill
+    // two CTAs per SM (e.g. 512 elements at n = 6: 0.25 against 0.31 ms).
+    if constexpr (use_row64_kernel<D, N, FLUX>()) {
+        static int sms = 0;
+        if (sms == 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        }
+        using S = Shape<D, N, FLUX, ModeFP64>;
+        if ((n_elem + S::EPB - 1) / S::EPB < 2 * (int64_t)sms)
+            return launch_volume_fp64_row<N>(u, Ja, r, n_elem, tab, err, stream);
+    }
+    return launch_volume<D, N, FLUX, ModeFP64>(u, Ja, r, n_elem, tab, err, stream);
+}
+#endif
+
+#if defined(SFH_INST_FP64)
 using Mode = ModeFP64;
 #define SFH_FN SFH_CAT(volume_fp64_d, SFH_INST_D)
 #elif defined(SFH_INST_FP32K)
@@ -75,6 +98,17 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
         default: return cudaErrorInvalidValue;
     }
 #undef SFH_TCASE
+#endif
+#if defined(SFH_INST_FP64)
+#define SFH_DCASE(N)                                                                                    \
+    case N:                                                                                             \
+        return flux == kFluxEuler ? launch_fp64<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream)   \
+                                  : launch_fp64<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
+    switch (n) {
+        SFH_DCASE(2) SFH_DCASE(3) SFH_DCASE(4) SFH_DCASE(5) SFH_DCASE(6) SFH_DCASE(7) SFH_DCASE(8) SFH_DCASE(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SFH_DCASE
 #endif
 #define SFH_CASE(N)                                                                                              \
     case N:                                                                                                      \

@@ -108,20 +108,21 @@ struct BlockPlan {
     uint32_t bytesU, bytesJ;
 };
 
-template <class S>
-__device__ __forceinline__ BlockPlan plan_block(int64_t blk, int64_t n_elem, const float *u, const double *Ja,
+template <class S, typename TU>
+__device__ __forceinline__ BlockPlan plan_block(int64_t blk, int64_t n_elem, const TU *u, const double *Ja,
                                                 bool aligned_bases) {
+    constexpr uintptr_t ESZ = sizeof(TU);
     BlockPlan pl;
     pl.e0 = blk * S::EPB;
     pl.ne = (int)((n_elem - pl.e0) < S::EPB ? (n_elem - pl.e0) : S::EPB);
     const uintptr_t aU = reinterpret_cast<uintptr_t>(u + pl.e0 * S::U_EL);
     const uintptr_t eU = reinterpret_cast<uintptr_t>(u + n_elem * S::U_EL);
-    const uintptr_t loU = aU & ~uintptr_t(15), hiU = (aU + (uintptr_t)pl.ne * S::U_EL * 4 + 15) & ~uintptr_t(15);
+    const uintptr_t loU = aU & ~uintptr_t(15), hiU = (aU + (uintptr_t)pl.ne * S::U_EL * ESZ + 15) & ~uintptr_t(15);
     const uintptr_t aJ = reinterpret_cast<uintptr_t>(Ja + pl.e0 * S::J_EL);
     const uintptr_t eJ = reinterpret_cast<uintptr_t>(Ja + n_elem * S::J_EL);
     const uintptr_t loJ = aJ & ~uintptr_t(15), hiJ = (aJ + (uintptr_t)pl.ne * S::J_EL * 8 + 15) & ~uintptr_t(15);
     pl.tma = aligned_bases && hiU <= eU && hiJ <= eJ;   // never read past the end of either array
-    pl.offU = (uint32_t)((aU - loU) / 4);
+    pl.offU = (uint32_t)((aU - loU) / ESZ);
     pl.offJ = (uint32_t)((aJ - loJ) / 8);
     pl.srcU = reinterpret_cast<const char *>(loU);
     pl.srcJ = reinterpret_cast<const char *>(loJ);

@@ -108,7 +108,10 @@ def test_alone_equals_in_the_mix_and_parity():
             ref = O.vjp_sf(3, p, kind, O.FLUX_EULER, r["u"], r["Ja"], r["lam"])
             assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
         elif r["prec"] == "fp64":
-            assert torch.equal(a, ctx.volume_residual(dv[0], dv[1], "fp64"))
+            # the standalone FP64 path may pick another kernel (another
+            # summation order) for a small mesh: equal to round-off
+            sa = ctx.volume_residual(dv[0], dv[1], "fp64").double().cpu().numpy()
+            assert rel_err_per_var(got, sa) <= 1e-13
             ref = O.volume_sf(3, p, kind, O.FLUX_EULER, r["u"], r["Ja"])
             assert rel_err_per_var(got, ref) <= 1e-12
         else:
