@@ -43,7 +43,11 @@ struct ModeMixed { using T = float; using TJ = double; static constexpr bool kah
 // accumulator (NVAR of T), the metric row of the current direction (D of TJ)
 // and, for the mixed mode, an FP64 copy of beta = rho / p.
 // ---------------------------------------------------------------------------
-template <int D, int N, int FLUX, class M>
+// BUDGET: shared-memory budget of one tile; LINES: target line tasks per
+// tile (0: 128, or 256 for lines of 48 and more nodes).  The standalone
+// kernels use the defaults; the serving kernel asks for tiles that fill its
+// 256 threads.
+template <int D, int N, int FLUX, class M, int BUDGET = 96 * 1024, int LINES = 0>
 struct Shape {
     using T = typename M::T;
     using TJ = typename M::TJ;
@@ -56,9 +60,9 @@ struct Shape {
     static constexpr bool F64E = sizeof(T) == 8 && FLUX == kFluxEuler;
     static constexpr int NODE_BYTES = (int)sizeof(T) * (NP + NVAR) + (int)sizeof(TJ) * D
                                       + (((M::mixed || F64E) && FLUX == kFluxEuler) ? 8 : 0);
-    static constexpr int SMEM_BUDGET = 96 * 1024;
+    static constexpr int SMEM_BUDGET = BUDGET;
     static constexpr int EPB_SMEM = SMEM_BUDGET / (NN * NODE_BYTES) > 0 ? SMEM_BUDGET / (NN * NODE_BYTES) : 1;
-    static constexpr int TARGET_LINES = NLINE >= 48 ? 256 : 128;
+    static constexpr int TARGET_LINES = LINES > 0 ? LINES : (NLINE >= 48 ? 256 : 128);
     static constexpr int EPB_LINES = TARGET_LINES / NLINE > 0 ? TARGET_LINES / NLINE : 1;
     static constexpr int EPB = EPB_SMEM < EPB_LINES ? EPB_SMEM : EPB_LINES;
     static constexpr int THREADS = ((EPB * NLINE + 31) / 32) * 32;

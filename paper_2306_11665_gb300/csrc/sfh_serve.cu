@@ -97,11 +97,14 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const volatile 
 }
 
 // ---- per-class tile bodies (all 3D Euler) --------------------------------
+// tiles sized to give the 256 threads a line each (as far as a 200 KB
+// budget allows): one serving CTA per SM must keep all of its warps busy
+constexpr int kTileBudget = 200 * 1024;
 template <int N> struct Cls {
-    using F64 = Shape<3, N, kFluxEuler, ModeFP64>;
-    using F32 = Shape<3, N, kFluxEuler, ModeFP32K>;
-    using MIX = Shape<3, N, kFluxEuler, ModeMixed>;
-    using VJP = VjpShape<3, N, kFluxEuler>;
+    using F64 = Shape<3, N, kFluxEuler, ModeFP64, kTileBudget, kThreads>;
+    using F32 = Shape<3, N, kFluxEuler, ModeFP32K, kTileBudget, kThreads>;
+    using MIX = Shape<3, N, kFluxEuler, ModeMixed, kTileBudget, kThreads>;
+    using VJP = VjpShape<3, N, kFluxEuler, kTileBudget, kThreads>;
 };
 
 template <int N> constexpr size_t cls_smem() {
@@ -134,18 +137,19 @@ __host__ __device__ inline int tile_epb(int kind, int prec, int n) {
 template <int N>
 __device__ __noinline__ void run_tile(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
                                          const OpTab<float> &tf, int *err, unsigned char *smem) {
+    using C = Cls<N>;
     if (q.kind == SFH_REQ_VJP) {
-        vjp_tile<3, N, kFluxEuler>(static_cast<const double *>(q.u), q.Ja, q.lam, static_cast<double *>(q.out), e0,
-                                   ne, td, err, smem);
+        vjp_tile<3, N, kFluxEuler, typename C::VJP>(static_cast<const double *>(q.u), q.Ja, q.lam,
+                                                    static_cast<double *>(q.out), e0, ne, td, err, smem);
     } else if (q.prec == SFH_FP64) {
-        volume_tile<3, N, kFluxEuler, ModeFP64>(static_cast<const double *>(q.u), q.Ja, static_cast<double *>(q.out),
-                                                e0, ne, td, err, smem);
+        volume_tile<3, N, kFluxEuler, ModeFP64, typename C::F64>(static_cast<const double *>(q.u), q.Ja,
+                                                                 static_cast<double *>(q.out), e0, ne, td, err, smem);
     } else if (q.prec == SFH_FP32_KAHAN) {
-        volume_tile<3, N, kFluxEuler, ModeFP32K>(static_cast<const float *>(q.u), q.Ja, static_cast<float *>(q.out),
-                                                 e0, ne, tf, err, smem);
+        volume_tile<3, N, kFluxEuler, ModeFP32K, typename C::F32>(static_cast<const float *>(q.u), q.Ja,
+                                                                  static_cast<float *>(q.out), e0, ne, tf, err, smem);
     } else {
-        volume_tile<3, N, kFluxEuler, ModeMixed>(static_cast<const float *>(q.u), q.Ja, static_cast<float *>(q.out),
-                                                 e0, ne, tf, err, smem);
+        volume_tile<3, N, kFluxEuler, ModeMixed, typename C::MIX>(static_cast<const float *>(q.u), q.Ja,
+                                                                  static_cast<float *>(q.out), e0, ne, tf, err, smem);
     }
 }
 

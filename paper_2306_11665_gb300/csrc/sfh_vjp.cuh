@@ -17,15 +17,18 @@
 
 namespace sfh {
 
-template <int D, int N, int FLUX>
+// LINES: target line tasks per tile (128 for the standalone kernel; the
+// serving kernel asks for tiles that fill its 256 threads); BUDGET: shared
+// memory of one tile.
+template <int D, int N, int FLUX, int BUDGET = 96 * 1024, int LINES = 128>
 struct VjpShape {
     static constexpr int NN = ipow(N, D);
     static constexpr int NLINE = ipow(N, D - 1);
     static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
     static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;
     static constexpr int NODE_BYTES = 8 * (2 * NP + NVAR + D);
-    static constexpr int EPB_SMEM = (96 * 1024) / (NN * NODE_BYTES) > 0 ? (96 * 1024) / (NN * NODE_BYTES) : 1;
-    static constexpr int EPB_LINES = 128 / NLINE > 0 ? 128 / NLINE : 1;
+    static constexpr int EPB_SMEM = BUDGET / (NN * NODE_BYTES) > 0 ? BUDGET / (NN * NODE_BYTES) : 1;
+    static constexpr int EPB_LINES = LINES / NLINE > 0 ? LINES / NLINE : 1;
     static constexpr int EPB = EPB_SMEM < EPB_LINES ? EPB_SMEM : EPB_LINES;
     static constexpr int THREADS = ((EPB * NLINE + 31) / 32) * 32;
     static constexpr size_t SMEM = (size_t)EPB * NN * NODE_BYTES;
@@ -77,11 +80,10 @@ __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *P
 }
 
 // One tile of ne (<= EPB) elements from e0, processed by the whole CTA.
-template <int D, int N, int FLUX>
+template <int D, int N, int FLUX, class S = VjpShape<D, N, FLUX>>
 __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const double *__restrict__ Ja,
                                          const double *__restrict__ lam, double *__restrict__ g, int64_t e0, int ne,
                                          const OpTab<double> &tab, int *__restrict__ err, unsigned char *smem_raw) {
-    using S = VjpShape<D, N, FLUX>;
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
     double *sP = reinterpret_cast<double *>(smem_raw);   // [EPB][NP][NN]
     double *sA = sP + EPB * NP * NN;                       // [EPB][NP][NN] adjoints of primitives

@@ -143,12 +143,11 @@ __device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, t
 // the whole CTA (any blockDim; every thread must call it).  smem_raw holds
 // Shape::SMEM bytes.  Used by volume_kernel (one tile per CTA) and by the
 // persistent serving kernel (tiles of many requests).
-template <int D, int N, int FLUX, class M>
+template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
 __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
                                             typename M::T *__restrict__ r, int64_t e0, int ne,
                                             const OpTab<typename M::T> &tab, int *__restrict__ err,
                                             unsigned char *smem_raw) {
-    using S = Shape<D, N, FLUX, M>;
     using T = typename M::T;
     using TJ = typename M::TJ;
     using Acc = typename AccOf<M>::type;
