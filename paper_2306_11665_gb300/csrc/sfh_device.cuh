@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sfh_tma.cuh"
+
 namespace sfh {
 
 constexpr int NMAX = 9;              // p <= 8
@@ -153,12 +155,23 @@ __device__ __forceinline__ double rcp_nr(double s) {
 }
 
 // FP64 logarithmic means with the band test taken on FP32 copies of the
-// arguments (af, bf), so that it costs no FP64 instruction.
+// arguments (af, bf), so that it costs no FP64 instruction.  Inside the band
+// (u < 1e-2) the series run in FP64 up to u^4; the tail u^5 T(u) is below
+// 3e-12 relative and is summed in FP32 (its rounding then weighs < 2e-19),
+// which moves three of the eight FP64 steps to the FP32 pipe.
 __device__ __forceinline__ double ln_mean_f64(double a, double b, float af, float bf) {
     const double d = a - b, s = a + b;
     if (fabsf(af - bf) < 0.1f * (af + bf)) {
         const double t = d * rcp_nr(s);
-        return (0.5 * s) * series_S(t * t);
+        const double u = t * t;
+        const float uf = d2f_int(u);
+        const float T = fmaf(uf, fmaf(uf, (float)(-25865068.0 / 1915538625.0), (float)(-10719068.0 / 638512875.0)),
+                             (float)(-10196.0 / 467775.0));
+        double h = fma(u, f2d_int(T), -428.0 / 14175.0);
+        h = fma(u, h, -44.0 / 945.0);
+        h = fma(u, h, -4.0 / 45.0);
+        h = fma(u, h, -1.0 / 3.0);
+        return (0.5 * s) * fma(u, h, 1.0);
     }
     return d / log(a / b);
 }
@@ -167,9 +180,88 @@ __device__ __forceinline__ double inv_ln_mean_f64(double a, double b, float af, 
     if (fabsf(af - bf) < 0.1f * (af + bf)) {
         const double rs = rcp_nr(s);
         const double t = d * rs;
-        return (2.0 * rs) * series_P(t * t);
+        const double u = t * t;
+        const float uf = d2f_int(u);
+        const float T = fmaf(uf, fmaf(uf, fmaf(uf, (float)(1.0 / 17.0), (float)(1.0 / 15.0)), (float)(1.0 / 13.0)),
+                             (float)(1.0 / 11.0));
+        double h = fma(u, f2d_int(T), 1.0 / 9.0);
+        h = fma(u, h, 1.0 / 7.0);
+        h = fma(u, h, 1.0 / 5.0);
+        h = fma(u, h, 1.0 / 3.0);
+        return (2.0 * rs) * fma(u, h, 1.0);
     }
     return log(a / b) / d;
+}
+
+// Value and both partial derivatives of {a,b}_ln and of its reciprocal
+// (FP64, for the adjoint), with the band test on FP32 copies af, bf and the
+// series tails from u^5 in FP32 as in ln_mean_f64.  With s = a + b,
+// t = (a - b)/s, u = t^2, du/da = 4 t b / s^2, du/db = -4 t a / s^2:
+//   L = (s/2) S(u):       dL/da = S/2 + 2 t b S'(u) / s,   dL/db = S/2 - 2 t a S'(u) / s;
+//   M = 1/L = (2/s) P(u): dM/da = (2/s^2)(4 t b P'(u)/s - P), dM/db = -(2/s^2)(4 t a P'(u)/s + P).
+// Outside the band (logarithms): dL/da = (1 - L/a)/ln(a/b), dL/db = (L/b - 1)/ln(a/b);
+//   dM/da = (1/a - M)/(a - b), dM/db = (M - 1/b)/(a - b).
+__device__ __forceinline__ void ln_mean_grad_f64(double a, double b, float af, float bf, double &L, double &La,
+                                                 double &Lb) {
+    const double d = a - b, s = a + b;
+    if (fabsf(af - bf) < 0.1f * (af + bf)) {
+        const double rs = rcp_nr(s);
+        const double t = d * rs, u = t * t;
+        const float uf = d2f_int(u);
+        const float T = fmaf(uf, fmaf(uf, (float)(-25865068.0 / 1915538625.0), (float)(-10719068.0 / 638512875.0)),
+                             (float)(-10196.0 / 467775.0));
+        double h = fma(u, f2d_int(T), -428.0 / 14175.0);
+        h = fma(u, h, -44.0 / 945.0);
+        h = fma(u, h, -4.0 / 45.0);
+        h = fma(u, h, -1.0 / 3.0);
+        const double S = fma(u, h, 1.0);
+        const float Td = fmaf(uf, (float)(7.0 * -25865068.0 / 1915538625.0), (float)(6.0 * -10719068.0 / 638512875.0));
+        double g = fma(u, f2d_int(Td), 5.0 * -10196.0 / 467775.0);
+        g = fma(u, g, 4.0 * -428.0 / 14175.0);
+        g = fma(u, g, 3.0 * -44.0 / 945.0);
+        g = fma(u, g, 2.0 * -4.0 / 45.0);
+        const double dS = fma(u, g, -1.0 / 3.0);
+        const double hS = 0.5 * S, w = 2.0 * t * dS * rs;
+        L = s * hS;
+        La = fma(w, b, hS);
+        Lb = fma(-w, a, hS);
+    } else {
+        const double lr = log(a / b);
+        L = d / lr;
+        La = (1.0 - L / a) / lr;
+        Lb = (L / b - 1.0) / lr;
+    }
+}
+__device__ __forceinline__ void inv_ln_mean_grad_f64(double a, double b, float af, float bf, double &M, double &Ma,
+                                                     double &Mb) {
+    const double d = a - b, s = a + b;
+    if (fabsf(af - bf) < 0.1f * (af + bf)) {
+        const double rs = rcp_nr(s);
+        const double t = d * rs, u = t * t;
+        const float uf = d2f_int(u);
+        const float T = fmaf(uf, fmaf(uf, fmaf(uf, (float)(1.0 / 17.0), (float)(1.0 / 15.0)), (float)(1.0 / 13.0)),
+                             (float)(1.0 / 11.0));
+        double h = fma(u, f2d_int(T), 1.0 / 9.0);
+        h = fma(u, h, 1.0 / 7.0);
+        h = fma(u, h, 1.0 / 5.0);
+        h = fma(u, h, 1.0 / 3.0);
+        const double P = fma(u, h, 1.0);
+        const float Td = fmaf(uf, fmaf(uf, (float)(8.0 / 17.0), (float)(7.0 / 15.0)), (float)(6.0 / 13.0));
+        double g = fma(u, f2d_int(Td), 5.0 / 11.0);
+        g = fma(u, g, 4.0 / 9.0);
+        g = fma(u, g, 3.0 / 7.0);
+        g = fma(u, g, 2.0 / 5.0);
+        const double dP = fma(u, g, 1.0 / 3.0);
+        const double r2 = 2.0 * rs, c = r2 * rs, w = 4.0 * t * dP * rs;
+        M = r2 * P;
+        Ma = c * fma(w, b, -P);
+        Mb = -c * fma(w, a, P);
+    } else {
+        const double lr = log(a / b), id = 1.0 / d;
+        M = lr * id;
+        Ma = (1.0 / a - M) * id;
+        Mb = (M - 1.0 / b) * id;
+    }
 }
 
 // Value and both partial derivatives of {a,b}_ln (FP64, for the adjoint).

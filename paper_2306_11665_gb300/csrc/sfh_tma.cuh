@@ -101,6 +101,16 @@ __device__ __forceinline__ float d2f_int(double x) {
     return __uint_as_float(f | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
 }
 
+// FP32 -> FP64 by integer operations (exact for normal x; zero and
+// subnormal x are not handled), so that the widening does not occupy the
+// FP64 pipe: the exponent field moves from bit 23 to bit 52 (of the high
+// word: bit 20) and is re-biased by 1023 - 127 = 896.
+__device__ __forceinline__ double f2d_int(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
+}
+
 // Hardware reciprocal approximation (PTX rcp.approx.ftz.f32: at most 1 ulp
 // from 1/x for normal x; subnormal inputs and results flush to zero).
 __device__ __forceinline__ float rcp_approx(float x) {

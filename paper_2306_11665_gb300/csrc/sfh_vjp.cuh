@@ -40,43 +40,48 @@ template <int D>
 __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *PB, const double *n,
                                                const double *c, double *ga, double *gb) {
     const double ra = PA[0], rb = PB[0], pa = PA[D + 1], pb = PB[D + 1];
-    double vna = 0.0, vnb = 0.0, vv = 0.0;
+    double vna = PA[1] * n[0], vnb = PB[1] * n[0], vv = PA[1] * PB[1];
 #pragma unroll
-    for (int k = 0; k < D; ++k) { vna += PA[1 + k] * n[k]; vnb += PB[1 + k] * n[k]; vv += PA[1 + k] * PB[1 + k]; }
-    double Lr, Lra, Lrb, Lb, Lba, Lbb;
-    ln_mean_grad(ra, rb, Lr, Lra, Lrb);
-    ln_mean_grad(PA[D + 2], PB[D + 2], Lb, Lba, Lbb);
-    const double iLb = 1.0 / Lb;
+    for (int k = 1; k < D; ++k) {
+        vna = fma(PA[1 + k], n[k], vna);
+        vnb = fma(PB[1 + k], n[k], vnb);
+        vv = fma(PA[1 + k], PB[1 + k], vv);
+    }
+    // {rho}_ln and M = 1/{beta}_ln with their partial derivatives (band tests
+    // on FP32 copies made by integer conversion)
+    double Lr, Lra, Lrb, M, Ma, Mb;
+    ln_mean_grad_f64(ra, rb, d2f_int(ra), d2f_int(rb), Lr, Lra, Lrb);
+    inv_ln_mean_grad_f64(PA[D + 2], PB[D + 2], d2f_int(PA[D + 2]), d2f_int(PB[D + 2]), M, Ma, Mb);
     const double h = 0.5 * (vna + vnb);
     const double frho = Lr * h;
-    const double K = 0.5 * vv + iLb * (1.0 / (kGamma - 1.0));
+    const double K = fma(0.5, vv, M * (1.0 / (kGamma - 1.0)));
     const double cE = c[D + 1];
-    double frho_bar = c[0] + cE * K, pavg_bar = 0.0;
+    double frho_bar = fma(cE, K, c[0]), pavg_bar = 0.0;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         const double vavg = 0.5 * (PA[1 + l] + PB[1 + l]);
-        frho_bar += c[1 + l] * vavg;
-        pavg_bar += c[1 + l] * n[l];
-        const double vavg_bar = c[1 + l] * frho;
-        ga[1 + l] += 0.5 * vavg_bar;
-        gb[1 + l] += 0.5 * vavg_bar;
+        frho_bar = fma(c[1 + l], vavg, frho_bar);
+        pavg_bar = fma(c[1 + l], n[l], pavg_bar);
+        const double hvavg_bar = 0.5 * c[1 + l] * frho;
+        ga[1 + l] += hvavg_bar;
+        gb[1 + l] += hvavg_bar;
     }
-    const double K_bar = cE * frho;
+    const double hK_bar = 0.5 * cE * frho;
     const double Lr_bar = frho_bar * h, h_bar = frho_bar * Lr;
-    const double vna_bar = 0.5 * cE * pb + 0.5 * h_bar;
-    const double vnb_bar = 0.5 * cE * pa + 0.5 * h_bar;
+    const double vna_bar = 0.5 * fma(cE, pb, h_bar);
+    const double vnb_bar = 0.5 * fma(cE, pa, h_bar);
 #pragma unroll
     for (int k = 0; k < D; ++k) {
-        ga[1 + k] += 0.5 * K_bar * PB[1 + k] + vna_bar * n[k];
-        gb[1 + k] += 0.5 * K_bar * PA[1 + k] + vnb_bar * n[k];
+        ga[1 + k] += fma(hK_bar, PB[1 + k], vna_bar * n[k]);
+        gb[1 + k] += fma(hK_bar, PA[1 + k], vnb_bar * n[k]);
     }
-    ga[D + 1] += 0.5 * pavg_bar + 0.5 * cE * vnb;
-    gb[D + 1] += 0.5 * pavg_bar + 0.5 * cE * vna;
-    ga[0] += Lr_bar * Lra;
-    gb[0] += Lr_bar * Lrb;
-    const double Lb_bar = -(K_bar * (1.0 / (kGamma - 1.0))) * iLb * iLb;
-    ga[D + 2] += Lb_bar * Lba;
-    gb[D + 2] += Lb_bar * Lbb;
+    ga[D + 1] += 0.5 * fma(cE, vnb, pavg_bar);
+    gb[D + 1] += 0.5 * fma(cE, vna, pavg_bar);
+    ga[0] = fma(Lr_bar, Lra, ga[0]);
+    gb[0] = fma(Lr_bar, Lrb, gb[0]);
+    const double M_bar = cE * frho * (1.0 / (kGamma - 1.0));
+    ga[D + 2] = fma(M_bar, Ma, ga[D + 2]);
+    gb[D + 2] = fma(M_bar, Mb, gb[D + 2]);
 }
 
 // One tile of ne (<= EPB) elements from e0, processed by the whole CTA.
@@ -99,18 +104,21 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         const double *ue = ub + (int64_t)el * NVAR * NN + i;
         double *pe = sP + el * NP * NN + i;
         if constexpr (FLUX == kFluxEuler) {
-            const double rho = ue[0], E = ue[(D + 1) * NN], irho = 1.0 / rho;
+            const double rho = ue[0], E = ue[(D + 1) * NN], irho = rcp_nr(rho);
             double ke = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const double mk = ue[(1 + k) * NN], vk = mk * irho;
                 pe[(1 + k) * NN] = vk;
-                ke += mk * vk;
+                ke = fma(mk, vk, ke);
             }
-            const double p = (kGamma - 1.0) * (E - 0.5 * ke);
+            const double p = (kGamma - 1.0) * fma(-0.5, ke, E);
+            const double ip = rcp_nr(p);
+            double bt = rho * ip;
+            bt = fma(ip, fma(-p, bt, rho), bt);   // rho / p to within about half an ulp
             pe[0] = rho;
             pe[(D + 1) * NN] = p;
-            pe[(D + 2) * NN] = rho / p;
+            pe[(D + 2) * NN] = bt;
             bad |= !(rho > 0.0 && p > 0.0);
         } else {
             pe[0] = ue[0];
@@ -168,8 +176,9 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
 #pragma unroll
                         for (int v = 0; v < NVAR; ++v) c[v] = qab * LA[v];
                     } else {
+                        const double qbw = qba * omega;
 #pragma unroll
-                        for (int v = 0; v < NVAR; ++v) c[v] = qab * LA[v] + qba * (omega * sL[(el * NVAR + v) * NN + ib]);
+                        for (int v = 0; v < NVAR; ++v) c[v] = fma(qbw, sL[(el * NVAR + v) * NN + ib], qab * LA[v]);
                     }
                     if constexpr (FLUX == kFluxEuler) {
                         euler_pair_vjp<D>(PA, PB, n, c, GA, GB);
@@ -199,17 +208,19 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         const double *ae = sA + el * NP * NN + i;
         double *ge = gbp + (int64_t)el * NVAR * NN + i;
         if constexpr (FLUX == kFluxEuler) {
-            const double rho = pe[0], p = pe[(D + 1) * NN];
+            const double rho = pe[0], p = pe[(D + 1) * NN], beta = pe[(D + 2) * NN];
+            const double irho = rcp_nr(rho), ip = rcp_nr(p);
             const double bbar = ae[(D + 2) * NN];
-            const double rbar = ae[0] + bbar / p;
-            const double pbar = ae[(D + 1) * NN] - bbar * rho / (p * p);
+            const double rbar = fma(bbar, ip, ae[0]);            // d beta / d rho = 1/p
+            const double pbar = fma(-bbar * beta, ip, ae[(D + 1) * NN]);   // d beta / d p = -beta/p
             double g0 = rbar, v2 = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const double vk = pe[(1 + k) * NN], vbar = ae[(1 + k) * NN];
-                g0 -= vbar * vk / rho;
-                v2 += vk * vk;
-                ge[(1 + k) * NN] = vbar / rho - pbar * (kGamma - 1.0) * vk;
+                const double vbr = vbar * irho;
+                g0 = fma(-vbr, vk, g0);
+                v2 = fma(vk, vk, v2);
+                ge[(1 + k) * NN] = fma(-pbar * (kGamma - 1.0), vk, vbr);
             }
             ge[0] = g0 + pbar * (kGamma - 1.0) * 0.5 * v2;
             ge[(D + 1) * NN] = pbar * (kGamma - 1.0);
@@ -219,23 +230,21 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
     }
 }
 
-template <int D, int N, int FLUX>
-__global__ void __launch_bounds__(VjpShape<D, N, FLUX>::THREADS)
+template <int D, int N, int FLUX, class S>
+__global__ void __launch_bounds__(S::THREADS)
 vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const double *__restrict__ lam,
            double *__restrict__ g, int64_t n_elem, const __grid_constant__ OpTab<double> tab,
            int *__restrict__ err) {
-    using S = VjpShape<D, N, FLUX>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    vjp_tile<D, N, FLUX>(u, Ja, lam, g, e0, ne, tab, err, smem_raw);
+    vjp_tile<D, N, FLUX, S>(u, Ja, lam, g, e0, ne, tab, err, smem_raw);
 }
 
-template <int D, int N, int FLUX>
-cudaError_t launch_vjp(const double *u, const double *Ja, const double *lam, double *g, int64_t n_elem,
-                       const OpTab<double> &tab, int *err, cudaStream_t stream) {
-    using S = VjpShape<D, N, FLUX>;
-    auto kern = vjp_kernel<D, N, FLUX>;
+template <int D, int N, int FLUX, class S>
+cudaError_t launch_vjp_shape(const double *u, const double *Ja, const double *lam, double *g, int64_t n_elem,
+                             const OpTab<double> &tab, int *err, cudaStream_t stream) {
+    auto kern = vjp_kernel<D, N, FLUX, S>;
     static_assert(S::SMEM <= 227 * 1024, "shared memory");
     if (S::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
@@ -244,6 +253,12 @@ cudaError_t launch_vjp(const double *u, const double *Ja, const double *lam, dou
     const int64_t blocks = (n_elem + S::EPB - 1) / S::EPB;
     kern<<<(unsigned)blocks, S::THREADS, S::SMEM, stream>>>(u, Ja, lam, g, n_elem, tab, err);
     return cudaGetLastError();
+}
+
+template <int D, int N, int FLUX>
+cudaError_t launch_vjp(const double *u, const double *Ja, const double *lam, double *g, int64_t n_elem,
+                       const OpTab<double> &tab, int *err, cudaStream_t stream) {
+    return launch_vjp_shape<D, N, FLUX, VjpShape<D, N, FLUX>>(u, Ja, lam, g, n_elem, tab, err, stream);
 }
 
 }  // namespace sfh

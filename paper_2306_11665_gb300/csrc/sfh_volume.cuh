@@ -341,24 +341,22 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     for (int s = threadIdx.x; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
 }
 
-template <int D, int N, int FLUX, class M>
-__global__ void __launch_bounds__(Shape<D, N, FLUX, M>::THREADS)
+template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
+__global__ void __launch_bounds__(S::THREADS)
 volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
               typename M::T *__restrict__ r, int64_t n_elem,
               const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err) {
-    using S = Shape<D, N, FLUX, M>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    volume_tile<D, N, FLUX, M>(u, Ja, r, e0, ne, tab, err, smem_raw);
+    volume_tile<D, N, FLUX, M, S>(u, Ja, r, e0, ne, tab, err, smem_raw);
 }
 
-// Host-side launcher for one (D, N, FLUX, mode) instance.
-template <int D, int N, int FLUX, class M>
+// Host-side launcher for one (D, N, FLUX, mode) instance and tile shape.
+template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
 cudaError_t launch_volume(const void *u, const double *Ja, void *r, int64_t n_elem,
                           const OpTab<typename M::T> &tab, int *err, cudaStream_t stream) {
-    using S = Shape<D, N, FLUX, M>;
-    auto kern = volume_kernel<D, N, FLUX, M>;
+    auto kern = volume_kernel<D, N, FLUX, M, S>;
     static_assert(S::SMEM <= 227 * 1024, "shared memory");
     if (S::SMEM > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);

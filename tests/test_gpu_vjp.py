@@ -54,6 +54,18 @@ def test_vjp_adjoint_config_full():
     assert rel(got, ref) <= 1e-12
 
 
+@pytest.mark.parametrize("p, kind", [(4, 0), (3, 1)])
+def test_vjp_large_mesh_sampled(p, kind):
+    """A mesh large enough for the multi-element blocks of the default
+    launch shape (16^3 elements); sampled elements checked one by one."""
+    u, Ja = I.workload(3, p, kind, 16)
+    lam = I.cotangent(u.shape, seed=8)
+    got = gpu_vjp(api.Context(3, p, kind, "euler"), u, Ja, lam)
+    idx = np.r_[0:5, 1000:1003, np.arange(7, u.shape[0], 211), u.shape[0] - 3:u.shape[0]]
+    ref = O.vjp_sf(3, p, kind, O.FLUX_EULER, u[idx], Ja[idx], lam[idx])
+    assert rel(got[idx], ref) <= 1e-12
+
+
 def test_autograd_and_finite_differences():
     ctx = api.Context(3, 5, "gll", "euler")
     u, Ja = I.workload(3, 5, 0, 3)
