@@ -162,6 +162,12 @@ extern "C" sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, do
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
+// Host-buffer pipeline: chunks of about kHostChunkBytes (u + Ja + r) rotate
+// over kHostStages streams and device staging buffers, so that the copies of
+// one chunk overlap the kernel and the result copy of the others.
+constexpr int kHostStages = 2;
+constexpr size_t kHostChunkBytes = 48u << 20;
+
 struct sfh_ctx {
     int d, p, n, nodes, nvar, flux, device;
     int *d_err;
@@ -169,8 +175,8 @@ struct sfh_ctx {
     sfh::OpTab<float> tab_f;
     // staging of the host-buffer entry point
     std::mutex host_mu;
-    cudaStream_t hs[2];
-    void *stage[2];
+    cudaStream_t hs[kHostStages];
+    void *stage[kHostStages];
     size_t stage_bytes;
 };
 
@@ -236,8 +242,10 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
     sfh_ctx *c = new (std::nothrow) sfh_ctx();
     if (!c) return fail(SFH_ENOMEM, "host allocation failed");
     c->d = d; c->p = p; c->n = p + 1; c->nodes = nodes; c->nvar = nvar; c->flux = flux; c->device = dev;
-    c->hs[0] = c->hs[1] = nullptr;
-    c->stage[0] = c->stage[1] = nullptr;
+    for (int k = 0; k < kHostStages; ++k) {
+        c->hs[k] = nullptr;
+        c->stage[k] = nullptr;
+    }
     c->stage_bytes = 0;
     const int n = p + 1;
     memset(&c->tab_d, 0, sizeof c->tab_d);
@@ -265,7 +273,7 @@ extern "C" sfh_status sfh_destroy(sfh_ctx *c) {
     clear_err();
     if (!c) return SFH_OK;
     DeviceGuard g(c->device);
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kHostStages; ++k) {
         if (c->hs[k]) { cudaStreamSynchronize(c->hs[k]); cudaStreamDestroy(c->hs[k]); }
         if (c->stage[k]) cudaFree(c->stage[k]);
     }
@@ -368,22 +376,22 @@ extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const
     const size_t nn = (size_t)sfh::ipow(c->n, c->d);
     const size_t ub_e = c->nvar * nn * esz, jb_e = (size_t)c->d * c->d * nn * sizeof(double);
     const size_t per_elem = 2 * ub_e + jb_e;
-    int64_t chunk = std::max<int64_t>(64, (int64_t)((48u << 20) / per_elem));
+    int64_t chunk = std::max<int64_t>(64, (int64_t)(kHostChunkBytes / per_elem));
     chunk = std::min<int64_t>(chunk, n_elem);
     const size_t need = (size_t)chunk * per_elem + 3 * 256;   // three 256-byte-aligned sub-buffers
     cudaError_t e;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < kHostStages; ++k) {
         if (!c->hs[k] && (e = cudaStreamCreateWithFlags(&c->hs[k], cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamCreate");
     }
     if (c->stage_bytes < need) {
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < kHostStages; ++k) {
             if (c->stage[k]) { cudaFree(c->stage[k]); c->stage[k] = nullptr; }
         }
         c->stage_bytes = 0;
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < kHostStages; ++k)
             if ((e = cudaMalloc(&c->stage[k], need)) != cudaSuccess) {
-                if (c->stage[0]) { cudaFree(c->stage[0]); c->stage[0] = nullptr; }
+                for (int j = 0; j < k; ++j) { cudaFree(c->stage[j]); c->stage[j] = nullptr; }
                 return fail(SFH_ENOMEM, "staging allocation of %zu bytes failed", need);
             }
         c->stage_bytes = need;
@@ -394,7 +402,7 @@ extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const
     int64_t k = 0;
     for (int64_t e0 = 0; e0 < n_elem; e0 += chunk, ++k) {
         const int64_t ne = std::min<int64_t>(chunk, n_elem - e0);
-        const int b = (int)(k & 1);
+        const int b = (int)(k % kHostStages);
         cudaStream_t s = c->hs[b];
         char *base = (char *)c->stage[b];
         char *du = base;
@@ -407,7 +415,7 @@ extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const
         if ((e = cudaMemcpyAsync(rh + e0 * ub_e, dr, ne * ub_e, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
             return cuda_fail(e, "device-to-host copy");
     }
-    for (int b = 0; b < 2; ++b)
+    for (int b = 0; b < kHostStages; ++b)
         if ((e = cudaStreamSynchronize(c->hs[b])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return sfh_check(c, c->hs[0]);
 }
