@@ -582,10 +582,33 @@ def main():
     te = (time.perf_counter() - t0) / ke
     if dist:
         te = D.max_over_ranks(te, dist, dev)
+    h2d = int(uh.numel() * uh.element_size() + Jh.numel() * 8)
+    d2h = int(rh.numel() * rh.element_size())
+    # the host link's own rate: one pinned-memory copy of the same h2d bytes
+    # and one of the d2h bytes issued together (the copy engines' ceiling)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    dst = torch.empty(h2d // 4, dtype=torch.float32, device=dev)
+    srch = torch.empty(h2d // 4, dtype=torch.float32).pin_memory()
+    srcd = torch.empty(d2h // 4, dtype=torch.float32, device=dev)
+    dsth = torch.empty(d2h // 4, dtype=torch.float32).pin_memory()
+    tl = float("inf")
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(s1):
+            dst.copy_(srch, non_blocking=True)
+        with torch.cuda.stream(s2):
+            dsth.copy_(srcd, non_blocking=True)
+        torch.cuda.synchronize()
+        tl = min(tl, time.perf_counter() - t0)
+    del dst, srch, srcd, dsth
     e2e = {"value": D.aggregate_throughput(dof, world, te), "unit": "element-DOF/s",
-           "h2d_bytes_per_step": int(uh.numel() * uh.element_size() + Jh.numel() * 8),
-           "d2h_bytes_per_step": int(rh.numel() * rh.element_size()),
-           "ms_per_step": te * 1e3, "api": "sfh_volume_residual_host (pinned host buffers)"}
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+           "ms_per_step": te * 1e3, "api": "sfh_volume_residual_host (pinned host buffers)",
+           "host_link": {"copy_only_ms": tl * 1e3, "copy_only_gbs": (h2d + d2h) / tl / 1e9,
+                         "frac": tl / te,
+                         "note": "the same bytes copied alone (pinned, both directions at once) "
+                                 "against the end-to-end step"}}
 
     return finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clocks, variants, u64, Ja, d, p,
                   kind, torch)
