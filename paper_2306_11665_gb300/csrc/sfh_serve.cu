@@ -134,23 +134,41 @@ __host__ __device__ inline int tile_epb(int kind, int prec, int n) {
     return 1;
 }
 
+// One out-of-line body per class, so that each gets its own register
+// allocation (a body that shares a function with the others inherits their
+// register pressure and spills in its inner loops).
 template <int N>
-__device__ __noinline__ void run_tile(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
+__device__ __noinline__ void run_vjp(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
+                                     unsigned char *smem) {
+    vjp_tile<3, N, kFluxEuler, typename Cls<N>::VJP>(static_cast<const double *>(q.u), q.Ja, q.lam,
+                                                     static_cast<double *>(q.out), e0, ne, td, err, smem);
+}
+template <int N>
+__device__ __noinline__ void run_f64(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
+                                     unsigned char *smem) {
+    volume_tile<3, N, kFluxEuler, ModeFP64, typename Cls<N>::F64>(static_cast<const double *>(q.u), q.Ja,
+                                                                  static_cast<double *>(q.out), e0, ne, td, err, smem);
+}
+template <int N>
+__device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
+                                     unsigned char *smem) {
+    volume_tile<3, N, kFluxEuler, ModeFP32K, typename Cls<N>::F32>(static_cast<const float *>(q.u), q.Ja,
+                                                                   static_cast<float *>(q.out), e0, ne, tf, err, smem);
+}
+template <int N>
+__device__ __noinline__ void run_mix(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
+                                     unsigned char *smem) {
+    volume_tile<3, N, kFluxEuler, ModeMixed, typename Cls<N>::MIX>(static_cast<const float *>(q.u), q.Ja,
+                                                                   static_cast<float *>(q.out), e0, ne, tf, err, smem);
+}
+
+template <int N>
+__device__ __forceinline__ void run_tile(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
                                          const OpTab<float> &tf, int *err, unsigned char *smem) {
-    using C = Cls<N>;
-    if (q.kind == SFH_REQ_VJP) {
-        vjp_tile<3, N, kFluxEuler, typename C::VJP>(static_cast<const double *>(q.u), q.Ja, q.lam,
-                                                    static_cast<double *>(q.out), e0, ne, td, err, smem);
-    } else if (q.prec == SFH_FP64) {
-        volume_tile<3, N, kFluxEuler, ModeFP64, typename C::F64>(static_cast<const double *>(q.u), q.Ja,
-                                                                 static_cast<double *>(q.out), e0, ne, td, err, smem);
-    } else if (q.prec == SFH_FP32_KAHAN) {
-        volume_tile<3, N, kFluxEuler, ModeFP32K, typename C::F32>(static_cast<const float *>(q.u), q.Ja,
-                                                                  static_cast<float *>(q.out), e0, ne, tf, err, smem);
-    } else {
-        volume_tile<3, N, kFluxEuler, ModeMixed, typename C::MIX>(static_cast<const float *>(q.u), q.Ja,
-                                                                  static_cast<float *>(q.out), e0, ne, tf, err, smem);
-    }
+    if (q.kind == SFH_REQ_VJP) run_vjp<N>(q, e0, ne, td, err, smem);
+    else if (q.prec == SFH_FP64) run_f64<N>(q, e0, ne, td, err, smem);
+    else if (q.prec == SFH_FP32_KAHAN) run_f32<N>(q, e0, ne, tf, err, smem);
+    else run_mix<N>(q, e0, ne, tf, err, smem);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constant__ Args a) {
