@@ -181,6 +181,21 @@ int sfh_version(void);
 sfh_status sfh_peak_fma(sfh_prec prec, double *tflops, double *ms);
 
 /* ---------------------------------------------------------------------------
+ * Self-test of the failure path of the kernels' bounded waits (no paper
+ * counterpart: failure detection).  Launches one CTA on the current device
+ * that waits, with the same bounded wait the volume kernels use for their
+ * bulk copies, on a shared-memory barrier phase that nothing completes (a
+ * transaction count is announced, no copy is issued).  After limit_us
+ * microseconds (1 .. 10^7) the wait gives up, the kernel records the timeout
+ * in its error word and returns; no copy is in flight and the context stays
+ * usable.  Synchronous on `stream`.
+ * Returns SFH_ETIMEOUT when the wait gave up as designed, SFH_OK if it
+ * completed (a defect), SFH_EINVAL for a limit out of range, SFH_ECUDA for a
+ * CUDA error.  *elapsed_us (optional) receives the device-measured wait.
+ * ------------------------------------------------------------------------- */
+sfh_status sfh_selftest_bounded_wait(int64_t limit_us, sfh_stream_t stream, double *elapsed_us);
+
+/* ---------------------------------------------------------------------------
  * Serving: batched residual and VJP requests of mixed degree p, element
  * count and precision on one device (3D Euler, Ranocha flux).  Requests are
  * admitted in FIFO order against an HBM budget and a limit on requests in

@@ -62,6 +62,7 @@ _SIGS = {
                                          ctypes.c_int, vp],
     "sfh_operator_tables": [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp],
     "sfh_peak_fma": [ctypes.c_int, dp, dp],
+    "sfh_selftest_bounded_wait": [ctypes.c_int64, ctypes.c_void_p, dp],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
     "sfh_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(Result)],
@@ -161,6 +162,14 @@ def sfh_peak_fma(prec: int):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _call("sfh_peak_fma", prec, ctypes.byref(tf), ctypes.byref(ms))
     return tf.value, ms.value
+
+
+def sfh_selftest_bounded_wait(limit_us: int, stream: int = 0):
+    """Runs the bounded-wait self-test; returns (status, elapsed_us).  The
+    expected status is SFH_ETIMEOUT."""
+    el = ctypes.c_double()
+    st = _call("sfh_selftest_bounded_wait", limit_us, stream, ctypes.byref(el), ok=(SFH_OK, SFH_ETIMEOUT))
+    return st, el.value
 
 
 def sfh_server_create(hbm_budget_bytes: int, max_inflight: int, timeout_ms: int, n_workers: int = 0) -> int:

@@ -13,6 +13,7 @@
 
 #include "../../include/sfhad.h"
 #include "sfh_internal.h"
+#include "sfh_tma.cuh"
 
 // ---------------------------------------------------------------------------
 // thread-local error message
@@ -418,6 +419,43 @@ extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const
     for (int b = 0; b < kHostStages; ++b)
         if ((e = cudaStreamSynchronize(c->hs[b])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return sfh_check(c, c->hs[0]);
+}
+
+// ---------------------------------------------------------------------------
+// bounded-wait self-test: an mbarrier phase that nothing completes
+// ---------------------------------------------------------------------------
+__global__ void bounded_wait_selftest_kernel(uint64_t limit_ns, int *out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    sfh::mbar_init(&bar, 1);
+    sfh::fence_proxy_async_smem();
+    // announce 16 bytes that no copy will deliver: phase 0 never completes
+    sfh::mbar_arrive_expect_tx(&bar, 16);
+    const uint64_t t0 = sfh::global_timer_ns();
+    const bool done = sfh::mbar_wait_bounded(&bar, 0, limit_ns);
+    out[0] = done ? 0 : sfh::kErrTimeout;
+    out[1] = (int)((sfh::global_timer_ns() - t0) / 1000);
+}
+
+extern "C" sfh_status sfh_selftest_bounded_wait(int64_t limit_us, sfh_stream_t stream, double *elapsed_us) {
+    clear_err();
+    if (limit_us < 1 || limit_us > 10000000) return fail(SFH_EINVAL, "limit_us must be in [1, 1e7], got %lld", (long long)limit_us);
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, 2 * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h[2] = {-1, 0};
+    bounded_wait_selftest_kernel<<<1, 32, 0, s>>>((uint64_t)limit_us * 1000ull, d);
+    if ((e = cudaGetLastError()) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "self-test kernel");
+    }
+    cudaFree(d);
+    if (elapsed_us) *elapsed_us = (double)h[1];
+    if (h[0] == sfh::kErrTimeout) return fail(SFH_ETIMEOUT, "bounded wait gave up after %d us (expected)", h[1]);
+    return SFH_OK;
 }
 
 // ---------------------------------------------------------------------------
