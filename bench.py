@@ -239,7 +239,7 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0):
+def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0, fp32_share=0.7):
     """Serving stream: n_req requests, n_elem log-uniform in [64, 4096], p uniform
     in {2..8} (Gauss-Lobatto), 70% FP32 / 30% FP64 residuals (a vjp_share of
     them VJPs instead), states and metrics resident, 40 GB admission budget.
@@ -260,7 +260,7 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
         ne = int(round(math.exp(rng.uniform(math.log(64), math.log(4096)))))
         p = int(rng.integers(2, 9))
         vjp = rng.uniform() < vjp_share
-        prec = A.SFH_FP64 if (vjp or rng.uniform() >= 0.7) else A.SFH_FP32_KAHAN
+        prec = A.SFH_FP64 if (vjp or rng.uniform() >= fp32_share) else A.SFH_FP32_KAHAN
         specs.append((ne, p, prec, vjp))
     outs = []
     reqs = []
@@ -313,6 +313,25 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
     t_all = time.perf_counter() - t_all
     res["serial_fp64"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                           "dof_per_s": dof / t_all}
+    # serial single-request launches in each request's own precision (the
+    # standalone kernels, one request at a time)
+    lat = []
+    t_all = time.perf_counter()
+    for (ne, p, prec, vjp), out in zip(specs, outs):
+        P = pools[p]
+        t0 = time.perf_counter()
+        if vjp:
+            A.sfh_vjp(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), out.data_ptr(),
+                      stream.cuda_stream)
+        else:
+            u = P["u64"] if prec == A.SFH_FP64 else P["u32"]
+            A.sfh_volume_residual(ctxs[p].handle, ne, u.data_ptr(), P["Ja"].data_ptr(), out.data_ptr(), prec,
+                                  stream.cuda_stream)
+        stream.synchronize()
+        lat.append((time.perf_counter() - t0) * 1e3)
+    t_all = time.perf_counter() - t_all
+    res["serial_own_precision"] = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                   "dof_per_s": dof / t_all}
     return res
 
 

@@ -260,6 +260,20 @@ sfh_status sfh_serve_replay(sfh_server *srv, int n, const sfh_request *reqs, con
  * (SFH_ETIMEOUT). */
 sfh_status sfh_serve_drain(sfh_server *srv, int timeout_ms);
 
+/* Serving-kernel counters since the server was created (tracing; no paper
+ * counterpart), summed over the persistent CTAs from the device timer:
+ * per class (0 residual FP64, 1 residual FP32-Kahan, 2 residual mixed,
+ * 3 VJP) the tiles run and the nanoseconds spent running them, and the
+ * nanoseconds CTAs spent claiming a tile (from the end of one tile to the
+ * start of the next, idle waits included).  Call with no request in flight
+ * for exact figures (synchronizes with the device). */
+typedef struct {
+    uint64_t tiles[4];
+    uint64_t busy_ns[4];
+    uint64_t claim_ns;
+} sfh_serve_stats_t;
+sfh_status sfh_serve_stats(sfh_server *srv, sfh_serve_stats_t *out);
+
 /* Stop the server: drains (bounded by timeout_ms), stops the persistent
  * kernel, joins the admission thread and frees the server. NULL accepted. */
 sfh_status sfh_server_destroy(sfh_server *srv);

@@ -47,6 +47,10 @@ class Result(ctypes.Structure):
                 ("t_done_ns", ctypes.c_uint64)]
 
 
+class ServeStats(ctypes.Structure):
+    _fields_ = [("tiles", ctypes.c_uint64 * 4), ("busy_ns", ctypes.c_uint64 * 4), ("claim_ns", ctypes.c_uint64)]
+
+
 _lib = None
 vp, i64, dp, ip = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
 
@@ -67,6 +71,7 @@ _SIGS = {
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
     "sfh_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(Result)],
     "sfh_serve_drain": [vp, ctypes.c_int],
+    "sfh_serve_stats": [vp, ctypes.POINTER(ServeStats)],
     "sfh_serve_replay": [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(Result), ctypes.c_int],
     "sfh_server_destroy": [vp],
@@ -204,6 +209,17 @@ def sfh_serve_replay(srv: int, reqs, arrival_s, timeout_ms: int):
 
 def sfh_serve_drain(srv: int, timeout_ms: int) -> None:
     _call("sfh_serve_drain", srv, timeout_ms)
+
+
+def sfh_serve_stats(srv: int) -> dict:
+    """Serving-kernel counters: per class (fp64, fp32k, mixed, vjp) tiles and
+    busy seconds, and the seconds CTAs spent claiming tiles."""
+    st = ServeStats()
+    _call("sfh_serve_stats", srv, ctypes.byref(st))
+    names = ("fp64", "fp32k", "fp32mix", "vjp")
+    return {"tiles": {n: int(st.tiles[k]) for k, n in enumerate(names)},
+            "busy_s": {n: st.busy_ns[k] * 1e-9 for k, n in enumerate(names)},
+            "claim_s": st.claim_ns * 1e-9}
 
 
 def sfh_server_destroy(srv: int) -> None:

@@ -40,6 +40,7 @@
 #include "sfh_tma.cuh"
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
+#include "sfh_volume_tma.cuh"
 
 namespace sfh {
 namespace serve {
@@ -76,6 +77,7 @@ struct DevCtrl {   // device memory
     int quit;          // set once every CTA is idle: the whole kernel leaves
     int done_tiles[kMaxSlots];
     int err[kMaxSlots];
+    unsigned long long tiles[4], busy_ns[4], claim_ns;   // counters (sfh_serve_stats)
 };
 
 struct Args {
@@ -100,9 +102,38 @@ __device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const volatile 
 // tiles sized to give the 256 threads a line each (as far as a 200 KB
 // budget allows): one serving CTA per SM must keep all of its warps busy
 constexpr int kTileBudget = 200 * 1024;
+// FP32-Kahan tiles run the persistent kernel's block phases (packed Kahan
+// sums, series log means, line-major FP32 metric rows), all directions at
+// once: D * EPB * N^2 line tasks on the 256 threads.
+template <int N>
+struct ServeF32 {
+    static constexpr int D = 3;
+    static constexpr int NN = N * N * N, NLINE = N * N, NVAR = 5, NP = 6;
+    static constexpr int U_EL = NVAR * NN, J_EL = 9 * NN;
+    static constexpr int LJ = (N * D) % 2 == 0 ? N * D + 1 : N * D;
+    static constexpr int JF_EL = D * NLINE * LJ;
+    static constexpr int EL_BYTES = 4 * NP * NN + 4 * JF_EL + 4 * D * U_EL + 4 * U_EL + 8 * J_EL;
+    static constexpr int EPB_T = kThreads / (D * NLINE) > 0 ? kThreads / (D * NLINE) : 1;
+    static constexpr int EPB_S = kTileBudget / EL_BYTES > 0 ? kTileBudget / EL_BYTES : 1;
+    static constexpr int EPB = EPB_T < EPB_S ? EPB_T : EPB_S;   // elements per sub-block
+    // sub-blocks per tile: a tile should carry about 1024 lines per direction.
+    // Claims are serialized on the ring's head (about 0.6 us each with all
+    // SMs claiming); FP32 tiles of 256 lines kept the CTAs claiming for 3/4
+    // of their time (measured with sfh_serve_stats)
+    static constexpr int SUB = (1024 / NLINE + EPB / 2) / EPB > 0 ? (1024 / NLINE + EPB / 2) / EPB : 1;
+    static constexpr int TILE = SUB * EPB;                       // elements per tile
+    static constexpr int up16(int x) { return (x + 15) / 16 * 16; }
+    static constexpr int OFF_JF = up16(EPB * NP * NN * 4);
+    static constexpr int OFF_R = up16(OFF_JF + EPB * JF_EL * 4);
+    static constexpr int OFF_RU = up16(OFF_R + D * EPB * U_EL * 4);   // raw u of the next sub-block
+    static constexpr int OFF_RJ = up16(OFF_RU + EPB * U_EL * 4);      // raw Ja of the next sub-block
+    static constexpr size_t SMEM = OFF_RJ + (size_t)EPB * J_EL * 8;
+    static_assert(D * EPB * NLINE <= kThreads, "one thread per line task");
+};
+
 template <int N> struct Cls {
     using F64 = Shape<3, N, kFluxEuler, ModeFP64, kTileBudget, kThreads>;
-    using F32 = Shape<3, N, kFluxEuler, ModeFP32K, kTileBudget, kThreads>;
+    using F32 = ServeF32<N>;   // tiles of F32::TILE elements
     using MIX = Shape<3, N, kFluxEuler, ModeMixed, kTileBudget, kThreads>;
     using VJP = VjpShape<3, N, kFluxEuler, kTileBudget, kThreads>;
 };
@@ -124,7 +155,7 @@ __host__ __device__ inline int tile_epb(int kind, int prec, int n) {
     case N:                                                                \
         if (kind == SFH_REQ_VJP) return Cls<N>::VJP::EPB;                  \
         if (prec == SFH_FP64) return Cls<N>::F64::EPB;                     \
-        if (prec == SFH_FP32_KAHAN) return Cls<N>::F32::EPB;               \
+        if (prec == SFH_FP32_KAHAN) return Cls<N>::F32::TILE;              \
         return Cls<N>::MIX::EPB;
     switch (n) {
         SFH_EPB_CASE(3) SFH_EPB_CASE(4) SFH_EPB_CASE(5) SFH_EPB_CASE(6) SFH_EPB_CASE(7) SFH_EPB_CASE(8)
@@ -152,8 +183,37 @@ __device__ __noinline__ void run_f64(const Req &q, int64_t e0, int ne, const OpT
 template <int N>
 __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
                                      unsigned char *smem) {
-    volume_tile<3, N, kFluxEuler, ModeFP32K, typename Cls<N>::F32>(static_cast<const float *>(q.u), q.Ja,
-                                                                   static_cast<float *>(q.out), e0, ne, tf, err, smem);
+    using S = ServeF32<N>;
+    float *sP = reinterpret_cast<float *>(smem);
+    float *sJF = reinterpret_cast<float *>(smem + S::OFF_JF);
+    float *sR = reinterpret_cast<float *>(smem + S::OFF_R);
+    float *rawU = reinterpret_cast<float *>(smem + S::OFF_RU);
+    double *rawJ = reinterpret_cast<double *>(smem + S::OFF_RJ);
+    // the raw u and Ja of a sub-block arrive by per-thread asynchronous copies,
+    // issued while the previous sub-block is swept
+    auto fetch = [&](int b0) {
+        const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
+        const float *U = static_cast<const float *>(q.u) + (e0 + b0) * S::U_EL;
+        const double *J = q.Ja + (e0 + b0) * S::J_EL;
+        for (int s = threadIdx.x; s < nb * S::U_EL; s += blockDim.x) cp_async4(rawU + s, U + s);
+        for (int s = threadIdx.x; s < nb * S::J_EL; s += blockDim.x) cp_async8(rawJ + s, J + s);
+        cp_async_commit();
+    };
+    bool bad = false;
+    fetch(0);
+    for (int b0 = 0; b0 < ne; b0 += S::EPB) {
+        const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
+        cp_async_wait_all();
+        __syncthreads();
+        bad |= fp32_block_convert<S, 3, N, kFluxEuler>(rawU, rawJ, nb, sP, sJF, threadIdx.x, blockDim.x);
+        __syncthreads();
+        if (b0 + S::EPB < ne) fetch(b0 + S::EPB);
+        fp32_block_sweep<S, 3, N, kFluxEuler>(threadIdx.x, nb, sP, sJF, sR, tf);
+        __syncthreads();
+        fp32_block_store<S, 3>(sR, static_cast<float *>(q.out) + (e0 + b0) * S::U_EL, nb, threadIdx.x, blockDim.x);
+        __syncthreads();
+    }
+    if (bad) atomicOr(err, kErrDomain);
 }
 template <int N>
 __device__ __noinline__ void run_mix(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
@@ -182,15 +242,21 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
     // counts itself idle (and uncounts itself when work appears); the kernel
     // leaves only when every CTA is idle, so a lull never thins out the CTAs
     // of a kernel that keeps running.  The host relaunches it for new work.
-    unsigned long long last_tail = 0;
+    unsigned long long last_tail = 0, known_tail = 0;   // known_tail: last tail read (acquire)
     uint64_t quiet_since = global_timer_ns();
     bool counted_idle = false;
     for (;;) {
+        uint64_t t_claim = 0;
         if (threadIdx.x == 0) {
+            t_claim = global_timer_ns();
             s_exit = 1;
             for (uint32_t it = 0; it < (1u << 28); ++it) {
                 const unsigned long long h = *reinterpret_cast<volatile unsigned long long *>(&a.ctrl->head);
-                const unsigned long long t = ld_acquire_sys_u64(a.tail);
+                // the host-mapped tail is read (system-scope acquire) only when
+                // the head has caught up with the last value seen: entries
+                // below a tail that was acquired are published
+                if (h >= known_tail) known_tail = ld_acquire_sys_u64(a.tail);
+                const unsigned long long t = known_tail;
                 if (t != last_tail) {
                     last_tail = t;
                     quiet_since = global_timer_ns();
@@ -243,6 +309,11 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
         for (int i = threadIdx.x; i < (int)(sizeof(OpTab<float>) / 4); i += blockDim.x)
             reinterpret_cast<float *>(&s_tf)[i] = reinterpret_cast<const float *>(a.tabf + tabi)[i];
         __syncthreads();
+        uint64_t t_run = 0;
+        if (threadIdx.x == 0) {
+            t_run = global_timer_ns();
+            atomicAdd(&a.ctrl->claim_ns, (unsigned long long)(t_run - t_claim));
+        }
         const int64_t e0 = (int64_t)s_tile * q.epb;
         const int ne = (int)((q.n_elem - e0) < q.epb ? (q.n_elem - e0) : q.epb);
         int *err = &a.ctrl->err[slot];
@@ -258,6 +329,9 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
         }
         __syncthreads();
         if (threadIdx.x == 0) {
+            const int cls = q.kind == SFH_REQ_VJP ? 3 : (q.prec == SFH_FP64 ? 0 : (q.prec == SFH_FP32_KAHAN ? 1 : 2));
+            atomicAdd(&a.ctrl->tiles[cls], 1ull);
+            atomicAdd(&a.ctrl->busy_ns[cls], (unsigned long long)(global_timer_ns() - t_run));
             __threadfence();   // this tile's output before the count
             const int done = atomicAdd(&a.ctrl->done_tiles[slot], 1) + 1;
             if (done == q.ntiles) {
@@ -581,6 +655,20 @@ extern "C" sfh_status sfh_serve_poll(sfh_server *s, uint64_t ticket, sfh_result 
     *out = s->results[ticket];
     s->results.erase(ticket);
     s->where.erase(w);
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_serve_stats(sfh_server *s, sfh_serve_stats_t *out) {
+    if (!s || !out) return SFH_EINVAL;
+    DevCtrl c;
+    cudaError_t e = cudaSetDevice(s->device);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, s->ctrl_d, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return SFH_ECUDA;
+    for (int k = 0; k < 4; ++k) {
+        out->tiles[k] = c.tiles[k];
+        out->busy_ns[k] = c.busy_ns[k];
+    }
+    out->claim_ns = c.claim_ns;
     return SFH_OK;
 }
 

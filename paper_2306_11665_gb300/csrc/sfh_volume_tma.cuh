@@ -194,6 +194,273 @@ __device__ __noinline__ void euler_line_general(const float *pe, const float *jl
     }
 }
 
+// ---------------------------------------------------------------------------
+// The phases of one element block, shared by the persistent kernel and the
+// serving kernel's FP32 tiles.  S supplies the block geometry (NN, NLINE,
+// NVAR, NP, U_EL, J_EL, LJ, JF_EL, EPB).
+// ---------------------------------------------------------------------------
+
+// Primitives and FP32 metric rows of ne elements from U ([el][var][i] floats)
+// and J ([el][m][k][i] doubles), in shared or global memory; returns whether
+// this thread saw rho <= 0 or p <= 0 (or NaN).
+template <class S, int D, int N, int FLUX>
+__device__ __forceinline__ bool fp32_block_convert(const float *U, const double *J, int ne, float *sP, float *sJF,
+                                                   int tid, int nthreads) {
+    constexpr int NN = S::NN, NLINE = S::NLINE, NP = S::NP, U_EL = S::U_EL, J_EL = S::J_EL;
+    bool bad = false;
+    for (int s = tid; s < ne * NN; s += nthreads) {
+        const int el = s / NN, i = s - el * NN;
+        const float *ue = U + el * U_EL + i;
+        float *pe = sP + el * NP * NN + i;
+        if constexpr (FLUX == kFluxEuler) {
+            // per-node divisions to within about half an ulp: with the
+            // residual's cancellation, per-node errors act like
+            // perturbations of the input state.  q = m / rho is formed as
+            // m r (r: reciprocal seed plus one Newton step) followed by one
+            // residual correction q += r (m - rho q), each a fused op.
+            const float rho = ue[0], E = ue[(D + 1) * NN];
+            float ir = rcp_approx(rho);
+            ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
+            float ke = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float mk = ue[(1 + k) * NN];
+                float vk = mk * ir;
+                vk = fmaf(ir, fmaf(-rho, vk, mk), vk);
+                pe[(1 + k) * NN] = 0.5f * vk;
+                ke = fmaf(mk, vk, ke);
+            }
+            const float p = (float)(kGamma - 1.0) * fmaf(-0.5f, ke, E);
+            float ip = rcp_approx(p);
+            ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
+            float bt = rho * ip;
+            bt = fmaf(ip, fmaf(-p, bt, rho), bt);
+            pe[0] = rho;
+            pe[(D + 1) * NN] = p;
+            pe[(D + 2) * NN] = bt;
+            bad |= !(rho > 0.0f && p > 0.0f);
+            // the node's d*d metric values, FP64 -> FP32, into the line of
+            // each direction through it: (line, position) = (i / N, i0),
+            // (i0 + N i2, i1), (i0 + N i1, i2) in 3D; (i1, i0), (i0, i1) in 2D
+            const double *je = J + el * J_EL + i;
+            float *jl = sJF + el * S::JF_EL;
+            const int i0 = i % N;
+#pragma unroll
+            for (int m = 0; m < D; ++m) {
+                int line, pos;
+                if constexpr (D == 3) {
+                    const int i1 = (i / N) % N, i2 = i / (N * N);
+                    line = m == 0 ? i / N : (m == 1 ? i0 + N * i2 : i0 + N * i1);
+                    pos = m == 0 ? i0 : (m == 1 ? i1 : i2);
+                } else {
+                    line = m == 0 ? i / N : i0;
+                    pos = m == 0 ? i0 : i / N;
+                }
+                float *dst = jl + (m * NLINE + line) * S::LJ + pos * D;
+#pragma unroll
+                for (int k = 0; k < D; ++k) dst[k] = d2f_int(je[(m * D + k) * NN]);
+            }
+        } else {
+            pe[0] = ue[0];
+        }
+    }
+    if constexpr (FLUX != kFluxEuler) {
+        for (int s = tid; s < ne * D * NN; s += nthreads) {
+            const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
+            const double *jm = J + ((el * D + m) * D) * NN + i;
+            static_assert(FLUX == kFluxEuler || S::JF_EL == D * NN, "Burgers metric sums are node-major");
+            float acc = d2f_int(jm[0]);
+#pragma unroll
+            for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
+            sJF[s] = acc;
+        }
+    }
+    return bad;
+}
+
+// Line sweeps of all directions at once: thread tid < D * EPB * NLINE owns one
+// (direction, element, line) and writes its direction's residual slice of sR
+// ([m][el][var][i]).
+template <class S, int D, int N, int FLUX>
+__device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *sP, const float *sJF, float *sR,
+                                                 const OpTab<float> &tab) {
+    constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB, U_EL = S::U_EL;
+    if (tid < D * EPB * NLINE) {
+        const int m = tid / (EPB * NLINE);
+        const int L = tid - m * (EPB * NLINE);
+        const int el = L / NLINE, l = L - el * NLINE;
+        if (el < ne) {
+            const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
+            int base;
+            float omega;
+            if constexpr (D == 3) {
+                const int o0 = l % N, o1 = l / N;
+                base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
+                omega = tab.w[o0] * tab.w[o1];
+            } else {
+                base = m == 0 ? N * l : l;
+                omega = tab.w[l];
+            }
+            const float *pe = sP + el * NP * NN + base;
+            float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
+            if constexpr (FLUX == kFluxEuler) {
+                // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
+                constexpr int NPAIR = NVAR / 2;
+                KahanF2 accp[N][NPAIR];
+                KahanF acc4[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
+                    acc4[a].zero();
+                }
+                const float *jl = sJF + el * S::JF_EL + (m * NLINE + l) * S::LJ;   // this line's metric rows
+                float2 rb[N];          // (rho, beta)
+                float hv[N][D], p[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+                    rb[a] = f2(pe[a * stride], pe[(D + 2) * NN + a * stride]);
+#pragma unroll
+                    for (int k = 0; k < D; ++k) hv[a][k] = pe[(1 + k) * NN + a * stride];
+                    p[a] = pe[(D + 1) * NN + a * stride];
+                }
+                // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean) as one packed Horner chain
+                const float cg = (float)(2.0 / (kGamma - 1.0));
+                const float2 c0 = f2(0.5f, cg), c1 = f2(0.5f * (-1.0f / 3.0f), cg * (1.0f / 3.0f));
+                const float2 c2 = f2(0.5f * (-4.0f / 45.0f), cg * (1.0f / 5.0f));
+                const float2 c3 = f2(0.5f * (-44.0f / 945.0f), cg * (1.0f / 7.0f));
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < N; ++b) {
+                        float n[D];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) n[k] = jl[a * D + k] + jl[b * D + k];
+                        float hna = hv[a][0] * n[0], hnb = hv[b][0] * n[0], hvv = hv[a][0] * hv[b][0];
+#pragma unroll
+                        for (int k = 1; k < D; ++k) {
+                            hna = fmaf(hv[a][k], n[k], hna);
+                            hnb = fmaf(hv[b][k], n[k], hnb);
+                            hvv = fmaf(hv[a][k], hv[b][k], hvv);
+                        }
+                        // both logarithmic means at once (.x: rho, .y: beta), by the series
+                        // in u = ((a-b)/(a+b))^2.  1/(a+b) is the hardware reciprocal
+                        // (at most 1 ulp off): it scales the inverse mean directly, an
+                        // error of the order of the FP32 rounding of the other factors.
+                        // The line leaves for the general routine if any pair has
+                        // u_rho + u_beta >= 1e-2 (which covers both u < 1e-2).
+                        const float2 d2 = sub2(rb[a], rb[b]), s2 = add2(rb[a], rb[b]);
+                        const float2 r2 = f2(rcp_approx(s2.x), rcp_approx(s2.y));
+                        const float2 t2 = mul2(d2, r2);
+                        const float2 u2 = mul2(t2, t2);
+                        float2 h = fma2(u2, c3, c2);
+                        h = fma2(u2, h, c1);
+                        h = fma2(u2, h, c0);
+                        umax = fmaxf(umax, u2.x + u2.y);
+                        const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
+                        const float frho = m2.x * (hna + hnb);      // {rho}_ln {v.n}
+                        const float pavg = 0.5f * (p[a] + p[b]);
+                        float2 F01, F23;
+                        F01.x = frho;
+                        F01.y = fmaf(frho, hv[a][0] + hv[b][0], pavg * n[0]);
+                        float FE;
+                        const float K = fmaf(2.0f, hvv, m2.y);
+                        if constexpr (D == 3) {
+                            F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
+                            F23.y = fmaf(frho, hv[a][2] + hv[b][2], pavg * n[2]);
+                            FE = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                        } else {
+                            F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
+                            F23.y = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            FE = 0.0f;
+                        }
+                        const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
+                        const float2 qa2 = f2s(qab), qb2 = f2s(qba);
+                        accp[a][0].add_prod(qa2, F01);
+                        accp[b][0].add_prod(qb2, F01);
+                        accp[a][1].add_prod(qa2, F23);
+                        accp[b][1].add_prod(qb2, F23);
+                        if constexpr (D == 3) {
+                            acc4[a].add_prod(qab, FE);
+                            acc4[b].add_prod(qba, FE);
+                        }
+                    }
+                    const float qaa = tab.Q1[a * N + a];
+                    if (qaa != 0.0f) {
+                        // physical flux f(u_a) . (2 Ja^m(a))
+                        float n[D];
+#pragma unroll
+                        for (int k = 0; k < D; ++k) n[k] = 2.0f * jl[a * D + k];
+                        float hn = hv[a][0] * n[0], hv2 = hv[a][0] * hv[a][0];
+#pragma unroll
+                        for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
+                        float F[D + 2];
+                        const float frho = 2.0f * rb[a].x * hn;
+                        F[0] = frho;
+#pragma unroll
+                        for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], p[a] * n[k]);
+                        F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
+                        const float2 qq = f2s(qaa);
+                        accp[a][0].add_prod(qq, f2(F[0], F[1]));
+                        accp[a][1].add_prod(qq, f2(F[2], F[3]));
+                        if constexpr (D == 3) acc4[a].add_prod(qaa, F[4]);
+                    }
+                }
+                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+                // also false for a NaN maximum (fmaxf drops NaN operands; the
+                // domain flag of the node pass reports the state)
+                if (__builtin_expect(!(umax < 1e-2f), 0)) {
+                    // rare: redo the whole line with logarithms where needed
+                    euler_line_general<D, N, NN, NP>(pe, jl, re, stride, omega, tab);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < N; ++a) {
+                        const float2 v01 = accp[a][0].value(), v23 = accp[a][1].value();
+                        re[0 * NN + a * stride] = omega * v01.x;
+                        re[1 * NN + a * stride] = omega * v01.y;
+                        re[2 * NN + a * stride] = omega * v23.x;
+                        re[3 * NN + a * stride] = omega * v23.y;
+                        if constexpr (D == 3) re[4 * NN + a * stride] = omega * acc4[a].value();
+                    }
+                }
+            } else {
+                KahanF acc[N][NVAR];
+#pragma unroll
+                for (int a = 0; a < N; ++a) acc[a][0].zero();
+                const float *je = sJF + (el * D + m) * NN + base;
+                float uu[N], Sm[N];
+#pragma unroll
+                for (int a = 0; a < N; ++a) { uu[a] = pe[a * stride]; Sm[a] = je[a * stride]; }
+#pragma unroll
+                for (int a = 0; a < N; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < N; ++b) {
+                        const float F = (uu[a] * uu[a] + uu[a] * uu[b] + uu[b] * uu[b]) * (1.0f / 6.0f) * (Sm[a] + Sm[b]);
+                        acc[a][0].add_prod(tab.Q1[a * N + b], F);
+                        acc[b][0].add_prod(tab.Q1[b * N + a], F);
+                    }
+                    const float qaa = tab.Q1[a * N + a];
+                    if (qaa != 0.0f) acc[a][0].add_prod(qaa, uu[a] * uu[a] * Sm[a]);
+                }
+                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+#pragma unroll
+                for (int a = 0; a < N; ++a) re[a * stride] = omega * acc[a][0].value();
+            }
+        }
+    }
+}
+
+// The directions' slices summed in a fixed order into r (coalesced).
+template <class S, int D>
+__device__ __forceinline__ void fp32_block_store(const float *sR, float *gR, int ne, int tid, int nthreads) {
+    constexpr int EPB = S::EPB, U_EL = S::U_EL;
+    for (int s2 = tid; s2 < ne * U_EL; s2 += nthreads) {
+        float t = sR[s2] + sR[EPB * U_EL + s2];
+        if constexpr (D == 3) t += sR[2 * EPB * U_EL + s2];
+        gR[s2] = t;
+    }
+}
+
 template <int D, int N, int FLUX>
 __global__ void __launch_bounds__(TmaShape<D, N, FLUX>::THREADS) __maxnreg__((TmaShape<D, N, FLUX>::MAXREG))
 volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ Ja, float *__restrict__ r,
@@ -253,76 +520,8 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
         }
 
         // ---- 2. primitives and FP32 metrics
-        const float *U = rawU + cur.offU;
-        const double *J = rawJ + cur.offJ;
-        bool bad = false;
-        for (int s = tid; s < ne * NN; s += blockDim.x) {
-            const int el = s / NN, i = s - el * NN;
-            const float *ue = U + el * U_EL + i;
-            float *pe = sP + el * NP * NN + i;
-            if constexpr (FLUX == kFluxEuler) {
-                // per-node divisions to within about half an ulp: with the
-                // residual's cancellation, per-node errors act like
-                // perturbations of the input state.  q = m / rho is formed as
-                // m r (r: reciprocal seed plus one Newton step) followed by one
-                // residual correction q += r (m - rho q), each a fused op.
-                const float rho = ue[0], E = ue[(D + 1) * NN];
-                float ir = rcp_approx(rho);
-                ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
-                float ke = 0.0f;
-#pragma unroll
-                for (int k = 0; k < D; ++k) {
-                    const float mk = ue[(1 + k) * NN];
-                    float vk = mk * ir;
-                    vk = fmaf(ir, fmaf(-rho, vk, mk), vk);
-                    pe[(1 + k) * NN] = 0.5f * vk;
-                    ke = fmaf(mk, vk, ke);
-                }
-                const float p = (float)(kGamma - 1.0) * fmaf(-0.5f, ke, E);
-                float ip = rcp_approx(p);
-                ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
-                float bt = rho * ip;
-                bt = fmaf(ip, fmaf(-p, bt, rho), bt);
-                pe[0] = rho;
-                pe[(D + 1) * NN] = p;
-                pe[(D + 2) * NN] = bt;
-                bad |= !(rho > 0.0f && p > 0.0f);
-                // the node's d*d metric values, FP64 -> FP32, into the line of
-                // each direction through it: (line, position) = (i / N, i0),
-                // (i0 + N i2, i1), (i0 + N i1, i2) in 3D; (i1, i0), (i0, i1) in 2D
-                const double *je = J + el * J_EL + i;
-                float *jl = sJF + el * S::JF_EL;
-                const int i0 = i % N;
-#pragma unroll
-                for (int m = 0; m < D; ++m) {
-                    int line, pos;
-                    if constexpr (D == 3) {
-                        const int i1 = (i / N) % N, i2 = i / (N * N);
-                        line = m == 0 ? i / N : (m == 1 ? i0 + N * i2 : i0 + N * i1);
-                        pos = m == 0 ? i0 : (m == 1 ? i1 : i2);
-                    } else {
-                        line = m == 0 ? i / N : i0;
-                        pos = m == 0 ? i0 : i / N;
-                    }
-                    float *dst = jl + (m * NLINE + line) * S::LJ + pos * D;
-#pragma unroll
-                    for (int k = 0; k < D; ++k) dst[k] = d2f_int(je[(m * D + k) * NN]);
-                }
-            } else {
-                pe[0] = ue[0];
-            }
-        }
-        if constexpr (FLUX != kFluxEuler) {
-            for (int s = tid; s < ne * D * NN; s += blockDim.x) {
-                const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
-                const double *jm = J + ((el * D + m) * D) * NN + i;
-                static_assert(FLUX == kFluxEuler || S::JF_EL == D * NN, "Burgers metric sums are node-major");
-                float acc = d2f_int(jm[0]);
-#pragma unroll
-                for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
-                sJF[s] = acc;
-            }
-        }
+        const bool bad = fp32_block_convert<S, D, N, FLUX>(rawU + cur.offU, rawJ + cur.offJ, ne, sP, sJF, tid,
+                                                           blockDim.x);
         if (bad) atomicOr(err, kErrDomain);
         __syncthreads();
 
@@ -338,178 +537,11 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
         }
 
         // ---- 4. line sweeps, all directions at once
-        if (tid < D * EPB * NLINE) {
-            const int m = tid / (EPB * NLINE);
-            const int L = tid - m * (EPB * NLINE);
-            const int el = L / NLINE, l = L - el * NLINE;
-            if (el < ne) {
-                const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
-                int base;
-                float omega;
-                if constexpr (D == 3) {
-                    const int o0 = l % N, o1 = l / N;
-                    base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
-                    omega = tab.w[o0] * tab.w[o1];
-                } else {
-                    base = m == 0 ? N * l : l;
-                    omega = tab.w[l];
-                }
-                const float *pe = sP + el * NP * NN + base;
-                float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
-                if constexpr (FLUX == kFluxEuler) {
-                    // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
-                    constexpr int NPAIR = NVAR / 2;
-                    KahanF2 accp[N][NPAIR];
-                    KahanF acc4[N];
-#pragma unroll
-                    for (int a = 0; a < N; ++a) {
-#pragma unroll
-                        for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
-                        acc4[a].zero();
-                    }
-                    const float *jl = sJF + el * S::JF_EL + (m * NLINE + l) * S::LJ;   // this line's metric rows
-                    float2 rb[N];          // (rho, beta)
-                    float hv[N][D], p[N];
-#pragma unroll
-                    for (int a = 0; a < N; ++a) {
-                        rb[a] = f2(pe[a * stride], pe[(D + 2) * NN + a * stride]);
-#pragma unroll
-                        for (int k = 0; k < D; ++k) hv[a][k] = pe[(1 + k) * NN + a * stride];
-                        p[a] = pe[(D + 1) * NN + a * stride];
-                    }
-                    // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean) as one packed Horner chain
-                    const float cg = (float)(2.0 / (kGamma - 1.0));
-                    const float2 c0 = f2(0.5f, cg), c1 = f2(0.5f * (-1.0f / 3.0f), cg * (1.0f / 3.0f));
-                    const float2 c2 = f2(0.5f * (-4.0f / 45.0f), cg * (1.0f / 5.0f));
-                    const float2 c3 = f2(0.5f * (-44.0f / 945.0f), cg * (1.0f / 7.0f));
-#pragma unroll
-                    for (int a = 0; a < N; ++a) {
-#pragma unroll
-                        for (int b = a + 1; b < N; ++b) {
-                            float n[D];
-#pragma unroll
-                            for (int k = 0; k < D; ++k) n[k] = jl[a * D + k] + jl[b * D + k];
-                            float hna = hv[a][0] * n[0], hnb = hv[b][0] * n[0], hvv = hv[a][0] * hv[b][0];
-#pragma unroll
-                            for (int k = 1; k < D; ++k) {
-                                hna = fmaf(hv[a][k], n[k], hna);
-                                hnb = fmaf(hv[b][k], n[k], hnb);
-                                hvv = fmaf(hv[a][k], hv[b][k], hvv);
-                            }
-                            // both logarithmic means at once (.x: rho, .y: beta), by the series
-                            // in u = ((a-b)/(a+b))^2.  1/(a+b) is the hardware reciprocal
-                            // (at most 1 ulp off): it scales the inverse mean directly, an
-                            // error of the order of the FP32 rounding of the other factors.
-                            // The line leaves for the general routine if any pair has
-                            // u_rho + u_beta >= 1e-2 (which covers both u < 1e-2).
-                            const float2 d2 = sub2(rb[a], rb[b]), s2 = add2(rb[a], rb[b]);
-                            const float2 r2 = f2(rcp_approx(s2.x), rcp_approx(s2.y));
-                            const float2 t2 = mul2(d2, r2);
-                            const float2 u2 = mul2(t2, t2);
-                            float2 h = fma2(u2, c3, c2);
-                            h = fma2(u2, h, c1);
-                            h = fma2(u2, h, c0);
-                            umax = fmaxf(umax, u2.x + u2.y);
-                            const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
-                            const float frho = m2.x * (hna + hnb);      // {rho}_ln {v.n}
-                            const float pavg = 0.5f * (p[a] + p[b]);
-                            float2 F01, F23;
-                            F01.x = frho;
-                            F01.y = fmaf(frho, hv[a][0] + hv[b][0], pavg * n[0]);
-                            float FE;
-                            const float K = fmaf(2.0f, hvv, m2.y);
-                            if constexpr (D == 3) {
-                                F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
-                                F23.y = fmaf(frho, hv[a][2] + hv[b][2], pavg * n[2]);
-                                FE = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
-                            } else {
-                                F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
-                                F23.y = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
-                                FE = 0.0f;
-                            }
-                            const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
-                            const float2 qa2 = f2s(qab), qb2 = f2s(qba);
-                            accp[a][0].add_prod(qa2, F01);
-                            accp[b][0].add_prod(qb2, F01);
-                            accp[a][1].add_prod(qa2, F23);
-                            accp[b][1].add_prod(qb2, F23);
-                            if constexpr (D == 3) {
-                                acc4[a].add_prod(qab, FE);
-                                acc4[b].add_prod(qba, FE);
-                            }
-                        }
-                        const float qaa = tab.Q1[a * N + a];
-                        if (qaa != 0.0f) {
-                            // physical flux f(u_a) . (2 Ja^m(a))
-                            float n[D];
-#pragma unroll
-                            for (int k = 0; k < D; ++k) n[k] = 2.0f * jl[a * D + k];
-                            float hn = hv[a][0] * n[0], hv2 = hv[a][0] * hv[a][0];
-#pragma unroll
-                            for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
-                            float F[D + 2];
-                            const float frho = 2.0f * rb[a].x * hn;
-                            F[0] = frho;
-#pragma unroll
-                            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], p[a] * n[k]);
-                            F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
-                            const float2 qq = f2s(qaa);
-                            accp[a][0].add_prod(qq, f2(F[0], F[1]));
-                            accp[a][1].add_prod(qq, f2(F[2], F[3]));
-                            if constexpr (D == 3) acc4[a].add_prod(qaa, F[4]);
-                        }
-                    }
-                    float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
-                    // also false for a NaN maximum (fmaxf drops NaN operands; the
-                    // domain flag of the node pass reports the state)
-                    if (__builtin_expect(!(umax < 1e-2f), 0)) {
-                        // rare: redo the whole line with logarithms where needed
-                        euler_line_general<D, N, NN, NP>(pe, jl, re, stride, omega, tab);
-                    } else {
-#pragma unroll
-                        for (int a = 0; a < N; ++a) {
-                            const float2 v01 = accp[a][0].value(), v23 = accp[a][1].value();
-                            re[0 * NN + a * stride] = omega * v01.x;
-                            re[1 * NN + a * stride] = omega * v01.y;
-                            re[2 * NN + a * stride] = omega * v23.x;
-                            re[3 * NN + a * stride] = omega * v23.y;
-                            if constexpr (D == 3) re[4 * NN + a * stride] = omega * acc4[a].value();
-                        }
-                    }
-                } else {
-                    KahanF acc[N][NVAR];
-#pragma unroll
-                    for (int a = 0; a < N; ++a) acc[a][0].zero();
-                    const float *je = sJF + (el * D + m) * NN + base;
-                    float uu[N], Sm[N];
-#pragma unroll
-                    for (int a = 0; a < N; ++a) { uu[a] = pe[a * stride]; Sm[a] = je[a * stride]; }
-#pragma unroll
-                    for (int a = 0; a < N; ++a) {
-#pragma unroll
-                        for (int b = a + 1; b < N; ++b) {
-                            const float F = (uu[a] * uu[a] + uu[a] * uu[b] + uu[b] * uu[b]) * (1.0f / 6.0f) * (Sm[a] + Sm[b]);
-                            acc[a][0].add_prod(tab.Q1[a * N + b], F);
-                            acc[b][0].add_prod(tab.Q1[b * N + a], F);
-                        }
-                        const float qaa = tab.Q1[a * N + a];
-                        if (qaa != 0.0f) acc[a][0].add_prod(qaa, uu[a] * uu[a] * Sm[a]);
-                    }
-                    float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
-#pragma unroll
-                    for (int a = 0; a < N; ++a) re[a * stride] = omega * acc[a][0].value();
-                }
-            }
-        }
+        fp32_block_sweep<S, D, N, FLUX>(tid, ne, sP, sJF, sR, tab);
         __syncthreads();
 
         // ---- 5. sum the directions in a fixed order and store r
-        float *gR = r + cur.e0 * U_EL;
-        for (int s2 = tid; s2 < ne * U_EL; s2 += blockDim.x) {
-            float t = sR[s2] + sR[EPB * U_EL + s2];
-            if constexpr (D == 3) t += sR[2 * EPB * U_EL + s2];
-            gR[s2] = t;
-        }
+        fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, blockDim.x);
         cur = nx;
     }
 }
