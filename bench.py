@@ -239,6 +239,11 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def srv_ctas(torch):
+    """Persistent serving CTAs: one per SM."""
+    return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+
+
 def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0, fp32_share=0.7):
     """Serving stream: n_req requests, n_elem log-uniform in [64, 4096], p uniform
     in {2..8} (Gauss-Lobatto), 70% FP32 / 30% FP64 residuals (a vjp_share of
@@ -276,12 +281,20 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
     res = {"requests": n_req, "dof_total": dof, "vjp_share": vjp_share}
     with Server(hbm_budget_bytes=40 << 30, max_inflight=64, timeout_ms=120000) as srv:
         A.sfh_serve_replay(srv.handle, reqs[:50], [0.0] * 50, 60000)           # warm-up
+        s0 = A.sfh_serve_stats(srv.handle)
         r = A.sfh_serve_replay(srv.handle, reqs, [0.0] * n_req, 120000)
+        s1 = A.sfh_serve_stats(srv.handle)
         assert all(x.status == A.SFH_OK for x in r)
         span = (max(x.t_done_ns for x in r) - min(x.t_submit_ns for x in r)) * 1e-9
         cap = dof / span
         res["capacity_dof_per_s"] = cap
         res["capacity_req_per_s"] = n_req / span
+        # where the serving CTAs' time went during the capacity run (device timer)
+        cta_s = srv_ctas(torch) * span
+        busy = {k: s1["busy_s"][k] - s0["busy_s"][k] for k in s1["busy_s"]}
+        res["cta_time"] = {"busy_frac": {k: v / cta_s for k, v in busy.items() if v > 0},
+                           "claim_frac": (s1["claim_s"] - s0["claim_s"]) / cta_s,
+                           "tiles": {k: s1["tiles"][k] - s0["tiles"][k] for k in s1["tiles"]}}
         for load in loads:
             rate = load * n_req / span
             arr = np.cumsum(rng.exponential(1.0 / rate, size=n_req))

@@ -180,3 +180,23 @@ def test_idle_relaunch_drain_timeout_and_domain_error():
         res = _wait(srv, [tb, tg])
         assert res[tb].status == A.SFH_EDOMAIN
         assert res[tg].status == A.SFH_OK
+
+
+def test_serve_stats_count_tiles_per_class():
+    reqs = _make_requests()
+    devs = [_to_dev(r) for r in reqs]
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=16) as srv:
+        s0 = A.sfh_serve_stats(srv.handle)
+        tickets = [_submit(srv, r, dv) for r, dv in zip(reqs, devs)]
+        res = _wait(srv, tickets)
+        assert all(x.status == A.SFH_OK for x in res.values())
+        s1 = A.sfh_serve_stats(srv.handle)
+    used = {"fp64": 0, "fp32k": 0, "fp32mix": 0, "vjp": 0}
+    for r in reqs:
+        used[r["prec"]] += 1
+    for k, n in used.items():
+        dt = s1["tiles"][k] - s0["tiles"][k]
+        assert (dt > 0) == (n > 0), (k, dt, n)
+        if n:
+            assert s1["busy_s"][k] > s0["busy_s"][k]
+    assert s1["claim_s"] >= s0["claim_s"]
