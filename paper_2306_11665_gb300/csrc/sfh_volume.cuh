@@ -47,18 +47,26 @@ __device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, t
     using T = typename M::T;
     T n[D];
 #pragma unroll
-    for (int k = 0; k < D; ++k) n[k] = (T)(A.J[k] + B.J[k]);   // TJ sum, then rounded to T
+    for (int k = 0; k < D; ++k) {
+        // TJ sum, then rounded to T (an FP64 sum rounded by integer
+        // conversion, off the FP64 pipe)
+        if constexpr (sizeof(typename M::TJ) == 8 && sizeof(T) == 4) n[k] = d2f_int(A.J[k] + B.J[k]);
+        else n[k] = (T)(A.J[k] + B.J[k]);
+    }
     T vna = A.v[0] * n[0], vnb = B.v[0] * n[0], vv = A.v[0] * B.v[0];
 #pragma unroll
     for (int k = 1; k < D; ++k) { vna += A.v[k] * n[k]; vnb += B.v[k] * n[k]; vv += A.v[k] * B.v[k]; }
     T Lr, iLb;
     if constexpr (M::mixed) {
-        // FP64 logarithmic mean inside the near-equal band, FP32 outside
+        // FP64 logarithmic mean inside the near-equal band (the FP64 routines
+        // of the FP64 kernels: Newton reciprocal, series tail in FP32, band
+        // test on the FP32 values), FP32 outside; widening by integer
+        // conversion keeps the FP64 pipe for the arithmetic
         const float dr = A.rho - B.rho, sr = A.rho + B.rho;
-        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = (float)ln_mean((double)A.rho, (double)B.rho);
+        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = d2f_int(ln_mean_f64(f2d_int(A.rho), f2d_int(B.rho), A.rho, B.rho));
         else Lr = ln_mean(A.rho, B.rho);
         const float db = A.beta - B.beta, sb = A.beta + B.beta;
-        if (db * db < (float)kLnBand * (sb * sb)) iLb = (float)inv_ln_mean(A.beta_d, B.beta_d);
+        if (db * db < (float)kLnBand * (sb * sb)) iLb = d2f_int(inv_ln_mean_f64(A.beta_d, B.beta_d, A.beta, B.beta));
         else iLb = inv_ln_mean(A.beta, B.beta);
     } else {
         Lr = ln_mean(A.rho, B.rho);
@@ -172,25 +180,51 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
         const T *ue = ub + (int64_t)el * NVAR * NN + i;
         T *pe = sP + el * NP * NN + i;
         if constexpr (FLUX == kFluxEuler) {
+            // reciprocals refined by Newton steps instead of IEEE divisions
+            // (FP64: rcp_nr; FP32: hardware seed + one step); beta = rho / p
+            // to within about half an ulp by one residual correction, and in
+            // FP32 v = m / rho too (FP64 keeps m (1/rho), within an ulp)
             const T rho = ue[0];
             const T E = ue[(D + 1) * NN];
-            const T irho = (T)1 / rho;
+            T irho;
+            if constexpr (sizeof(T) == 8) {
+                irho = rcp_nr(rho);
+            } else {
+                irho = rcp_approx(rho);
+                irho = fmaf(irho, fmaf(-rho, irho, 1.0f), irho);
+            }
             T ke = (T)0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 const T mk = ue[(1 + k) * NN];
-                const T vk = mk * irho;
+                T vk = mk * irho;
+                if constexpr (sizeof(T) == 4) vk = fma(irho, fma(-rho, vk, mk), vk);
                 pe[(1 + k) * NN] = F64E ? (T)0.5 * vk : vk;   // FP64 keeps v/2
-                ke += mk * vk;
+                ke = fma(mk, vk, ke);
             }
-            const T p = (T)(kGamma - 1.0) * (E - (T)0.5 * ke);
+            const T p = (T)(kGamma - 1.0) * fma((T)-0.5, ke, E);
+            T ip;
+            if constexpr (sizeof(T) == 8) {
+                ip = rcp_nr(p);
+            } else {
+                ip = rcp_approx(p);
+                ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
+            }
+            T bt = rho * ip;
+            bt = fma(ip, fma(-p, bt, rho), bt);
             pe[0] = rho;
             pe[(D + 1) * NN] = p;
-            pe[(D + 2) * NN] = rho / p;
-            if constexpr (M::mixed) sBd[el * NN + i] = (double)rho / (double)p;
+            pe[(D + 2) * NN] = bt;
+            if constexpr (M::mixed) {
+                // FP64 beta = rho / p to within about half an ulp (Newton
+                // reciprocal, product, one residual correction)
+                const double rd = f2d_int((float)rho), pd = f2d_int((float)p), ip = rcp_nr(pd);
+                double bt = rd * ip;
+                sBd[el * NN + i] = fma(ip, fma(-pd, bt, rd), bt);
+            }
             if constexpr (F64E) {
                 sRF[el * NN + i] = d2f_int((double)rho);
-                sRF[EPB * NN + el * NN + i] = d2f_int((double)(rho / p));
+                sRF[EPB * NN + el * NN + i] = d2f_int((double)bt);
             }
             bad |= !(rho > (T)0 && p > (T)0);
         } else {
