@@ -65,12 +65,9 @@ cudaError_t launch_fp64(const void *u, const double *Ja, void *r, int64_t n_elem
     // the row kernel wins where the former's element blocks would not fill
     // two CTAs per SM (e.g. 512 elements at n = 6: 0.25 against 0.31 ms).
     if constexpr (use_row64_kernel<D, N, FLUX>()) {
-        static int sms = 0;
-        if (sms == 0) {
-            int dev = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        }
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return cudaErrorInvalidDevice;
         using S = Fp64Shape<D, N, FLUX>;
         if ((n_elem + S::EPB - 1) / S::EPB < 2 * (int64_t)sms)
             return launch_volume_fp64_row<N>(u, Ja, r, n_elem, tab, err, stream);

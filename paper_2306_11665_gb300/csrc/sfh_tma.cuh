@@ -11,6 +11,7 @@
 
 namespace sfh {
 
+constexpr int kMaxDevices = 64;  // launch facts are cached per device index below this
 constexpr int kErrDomain = 1;    // density or pressure <= 0 (or NaN)
 constexpr int kErrTimeout = 2;   // a bounded wait gave up
 
@@ -82,6 +83,32 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 // every committed bulk store has completed
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// SM count of the current device and resident CTAs per SM of a persistent
+// kernel, asked of the runtime once per device (the kernel's dynamic
+// shared-memory limit is raised on that device at the same time) and cached
+// in the caller's per-device arrays.
+template <typename Kern>
+inline cudaError_t persistent_slots(Kern kern, int threads, size_t smem, int *cache_per_sm, int *cache_sms,
+                                    int &per_sm, int &sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (cache_per_sm[dev] == 0) {
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+        int n = 0, k = 0;
+        if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kern, threads, smem)) != cudaSuccess) return e;
+        if (k < 1) return cudaErrorInvalidConfiguration;
+        cache_sms[dev] = n;
+        cache_per_sm[dev] = k;
+    }
+    per_sm = cache_per_sm[dev];
+    sms = cache_sms[dev];
+    return cudaSuccess;
+}
 
 // Per-thread asynchronous global -> shared copies (cp.async, sm_80+): each
 // thread waits only for its own copies, so a wait always ends.
