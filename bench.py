@@ -99,6 +99,14 @@ def measured_traffic(prec, p, kind, N):
     return None
 
 
+def measured_counters(prec, p, kind, N):
+    """The same capture's utilisation counters (which unit binds), or None."""
+    rec = TRAFFIC.get((prec, p, kind, N))
+    if rec and rec["sha1"] == _kernel_sources_sha1() and "counters" in rec:
+        return rec["counters"]
+    return None
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -523,6 +531,7 @@ def main():
                     "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": measured_traffic(args.prec, p, kind, N),
                     "peak_source": hbm_src, "kernel": ("volume_fp32_row_kernel<%d>" % (p + 1) if d == 3 and p + 1 in (7, 8)
                                else "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1)),
+                    "ncu": measured_counters(args.prec, p, kind, N),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     elif args.prec == "fp32mix":
         # the FP64 log means bind the mixed mode: ALU roofline of the FP64 pipe
@@ -654,9 +663,13 @@ def finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clo
         cores = os.cpu_count() or 1
         lam = I.cotangent(u64.shape, seed=8) if args.prec == "vjp" else None
         v, dt, passes = oracle_baseline(u64, Ja, d, p, kind, cores, lam)
+        # one host thread as well (a bounded sample: about two seconds)
+        n1 = max(16, min(E, int(2.0 * v / cores / nn)))
+        v1, dt1, _ = oracle_throughput(u64, Ja, d, p, kind, n1, 1, lam)
         cpu = {"value": v, "unit": "element-DOF/s", "cores": cores, "kind": "oracle",
                "sample": f"{passes} pass(es) over all {E} elements ({'VJP' if lam is not None else 'residual'}), "
-                         f"FP64 oracle, {cores} threads, {dt:.1f} s"}
+                         f"FP64 oracle, {cores} threads, {dt:.1f} s",
+               "single_thread": {"value": v1, "sample": f"first {n1} elements, one thread, {dt1:.1f} s"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "element-DOF/s", "n_gpus": world, "steps": args.steps,

@@ -164,6 +164,34 @@ def test_entropy_identity_on_gpu_results(p, kind, N):
     _report(f"entropy_identity_euler_p{p}_{'gll' if kind == 0 else 'gauss'}_{N}cubed", worst)
 
 
+@pytest.mark.parametrize("prec", ["fp32k", "fp64"])
+def test_large_mesh_64bit_offsets(prec):
+    """2^21 elements of 3D Euler p = 4 (the 32^3 state tiled 64 times on the
+    device): Ja alone spans 18.9 GB, so element offsets pass 2^31 floats and
+    2^32 bytes; sampled elements, the last ones included, match the oracle."""
+    u, Ja = I.workload(3, 4, 0, 32)
+    E0, rep = u.shape[0], 64
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    src = u if prec == "fp64" else I.to_fp32(u)
+    ut = torch.from_numpy(np.ascontiguousarray(src)).to(dt).cuda().repeat(rep, 1, 1)
+    Jt = torch.from_numpy(Ja).cuda().repeat(rep, 1, 1, 1)
+    ctx = api.Context(3, 4, "gll", "euler")
+    r = ctx.volume_residual(ut, Jt, prec)
+    assert ctx.check() == A.SFH_OK
+    E = E0 * rep
+    idx = np.array([0, 1, E0 - 1, E0, E // 2 + 7, E - E0, E - 2, E - 1])
+    got = r[torch.from_numpy(idx).cuda()].double().cpu().numpy()
+    del ut, Jt, r
+    torch.cuda.empty_cache()
+    base = idx % E0
+    ref = O.volume_sf(3, 4, 0, O.FLUX_EULER, u[base], Ja[base])
+    if prec == "fp64":
+        assert rel_err_per_var(got, ref) <= 1e-12
+    else:
+        ref_w = O.volume_sf(3, 4, 0, O.FLUX_EULER, I.to_fp32(u[base]).astype(np.float64), Ja[base])
+        fp32_check(got, ref, ref_w, lambda: kappa(3, 4, 0, "euler", u[base], Ja[base], ref))
+
+
 def test_edge_cases():
     ctx = api.Context(3, 4, "gll", "euler")
     # n_elem = 0 is a no-op
