@@ -195,8 +195,8 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
         const float *U = static_cast<const float *>(q.u) + (e0 + b0) * S::U_EL;
         const double *J = q.Ja + (e0 + b0) * S::J_EL;
-        for (int s = threadIdx.x; s < nb * S::U_EL; s += blockDim.x) cp_async4(rawU + s, U + s);
-        for (int s = threadIdx.x; s < nb * S::J_EL; s += blockDim.x) cp_async8(rawJ + s, J + s);
+        for (int s = threadIdx.x; s < nb * S::U_EL; s += kThreads) cp_async4(rawU + s, U + s);
+        for (int s = threadIdx.x; s < nb * S::J_EL; s += kThreads) cp_async8(rawJ + s, J + s);
         cp_async_commit();
     };
     bool bad = false;
@@ -205,12 +205,12 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
         cp_async_wait_all();
         __syncthreads();
-        bad |= fp32_block_convert<S, 3, N, kFluxEuler>(rawU, rawJ, nb, sP, sJF, threadIdx.x, blockDim.x);
+        bad |= fp32_block_convert<S, 3, N, kFluxEuler>(rawU, rawJ, nb, sP, sJF, threadIdx.x, kThreads);
         __syncthreads();
         if (b0 + S::EPB < ne) fetch(b0 + S::EPB);
         fp32_block_sweep<S, 3, N, kFluxEuler>(threadIdx.x, nb, sP, sJF, sR, tf);
         __syncthreads();
-        fp32_block_store<S, 3>(sR, static_cast<float *>(q.out) + (e0 + b0) * S::U_EL, nb, threadIdx.x, blockDim.x);
+        fp32_block_store<S, 3>(sR, static_cast<float *>(q.out) + (e0 + b0) * S::U_EL, nb, threadIdx.x, kThreads);
         __syncthreads();
     }
     if (bad) atomicOr(err, kErrDomain);

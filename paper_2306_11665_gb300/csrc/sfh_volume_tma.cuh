@@ -521,7 +521,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
 
         // ---- 2. primitives and FP32 metrics
         const bool bad = fp32_block_convert<S, D, N, FLUX>(rawU + cur.offU, rawJ + cur.offJ, ne, sP, sJF, tid,
-                                                           blockDim.x);
+                                                           S::THREADS);
         if (bad) atomicOr(err, kErrDomain);
         __syncthreads();
 
@@ -541,7 +541,7 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
         __syncthreads();
 
         // ---- 5. sum the directions in a fixed order and store r
-        fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, blockDim.x);
+        fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, S::THREADS);
         cur = nx;
     }
 }
