@@ -374,6 +374,12 @@ def timed_launches(fn, steps, warmup, stream, torch):
     return total, sum(per) / len(per)
 
 
+def entropy_defect_max(torch, ctx, tu64, tJ, r):
+    """Largest per-element defect of the entropy identity of residual r, over
+    the whole mesh (FP64, on the GPU: sfh_entropy_residual)."""
+    return float(ctx.entropy_residual(tu64, tJ, r).max().item())
+
+
 def other_configs(torch, A, I, api, stream, hbm_peak):
     """The precision study (3D Euler, p = 7, Gauss, 16^3 warped) in the three
     precision modes, and the adjoint configuration (p = 5, Gauss-Lobatto,
@@ -397,7 +403,8 @@ def other_configs(torch, A, I, api, stream, hbm_peak):
                                   ("fp64", A.SFH_FP64, t64, r64, 10)):
         _, ms = timed_launches(lambda: A.sfh_volume_residual(ctx.handle, E, tu.data_ptr(), tJ.data_ptr(), tr.data_ptr(),
                                                              prec, sh), k, 3, stream, torch)
-        res[name] = {"ms": ms, "element_dof_per_s": dof / (ms * 1e-3)}
+        res[name] = {"ms": ms, "element_dof_per_s": dof / (ms * 1e-3),
+                     "entropy_identity_defect_max": entropy_defect_max(torch, ctx, t64, tJ, tr)}
     res["fp32k"]["hbm_frac_of_measured"] = b32 / (res["fp32k"]["ms"] * 1e-3) / 1e9 / hbm_peak
     res["fp64"]["alu_frac_of_fp64_rate"] = fl / (res["fp64"]["ms"] * 1e-3) / 1.25e12
     flm = pairs_per_element(3, 7) * MIX_PAIR_FP64_FLOPS * E
@@ -571,7 +578,8 @@ def main():
         b32v = bytes_per_node("fp32k", d) * dof
         variants["fp32k"] = {"element_dof_per_s": dof / (t32 * 1e-3), "ms": t32, "flops_per_launch": fl,
                              "alu_frac_of_nominal": fl / (t32 * 1e-3) / (nominal32 * 1e12),
-                             "hbm_frac_of_measured": b32v / (t32 * 1e-3) / 1e9 / hbm_peak}
+                             "hbm_frac_of_measured": b32v / (t32 * 1e-3) / 1e9 / hbm_peak,
+                             "entropy_identity_defect_max": entropy_defect_max(torch, ctx, tu64, tJ, r32)}
 
         def step64():
             A.sfh_volume_residual(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), r64.data_ptr(), A.SFH_FP64, sh)
@@ -581,12 +589,14 @@ def main():
                             "bound": "alu(fp64)",
                             "alu_frac_of_nominal": fl / (t64 * 1e-3) / (nominal64 * 1e12),
                             "alu_frac_of_measured": (fl / (t64 * 1e-3) / (fp64_tf * 1e12)) if fp64_tf else None,
-                            "hbm_frac_of_measured": b64 / (t64 * 1e-3) / 1e9 / hbm_peak}
+                            "hbm_frac_of_measured": b64 / (t64 * 1e-3) / 1e9 / hbm_peak,
+                            "entropy_identity_defect_max": entropy_defect_max(torch, ctx, tu64, tJ, r64)}
 
         def stepmix():
             A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_MIXED, sh)
         _, tmix = timed_launches(stepmix, k64, 2, stream, torch)
-        variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix}
+        variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix,
+                               "entropy_identity_defect_max": entropy_defect_max(torch, ctx, tu64, tJ, r32)}
 
         # adjoint on this workload (the adjoint configuration is in other_configs)
         g = torch.empty_like(tu64)

@@ -111,6 +111,22 @@ sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, cons
 sfh_status sfh_vjp(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *Ja,
                    const double *lambda, double *grad_u, sfh_stream_t stream);
 
+/* Entropy identity of the volume term (summation by parts, Tadmor's
+ * condition for the symmetric entropy-conservative flux; general SBP form,
+ * which for Gauss-Lobatto nodes is the element's boundary entropy flux):
+ * per element e, in FP64 on the GPU,
+ *   out[e] = |w^T r_e - sum_m [ 1/2 sum_ij E_ij w_i.F_ij - 1/2 sum_i (E 1)_i psi_i.J_i
+ *                                - 1/2 psi^T E J + psi^T Q J ]| / sum_m sum_ij |Q_ij| |w_i . F_ij|,
+ * E = Q_m + Q_m^T, J = Ja^m, w the entropy variables and psi the entropy
+ * potential of the FP64 state u (Eq. 3 operators).  r is a residual of this
+ * context's volume term computed in any mode: r_prec SFH_FP64 (double) or
+ * SFH_FP32_KAHAN / SFH_FP32_MIXED (float).  A residual of the method sits at
+ * the round-off of its precision (FP64 ~1e-16, FP32 ~1e-9).
+ * u: device double [n_elem][nvar][n^d]; Ja as above; out: device double
+ * [n_elem].  Asynchronous; domain errors latched for sfh_check(). */
+sfh_status sfh_entropy_residual(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *Ja, const void *r,
+                                sfh_prec r_prec, double *out, sfh_stream_t stream);
+
 /* Synchronize `stream`, then read and clear the context's device error word.
  * Returns SFH_EDOMAIN if any kernel of this context saw rho <= 0 or p <= 0
  * (or a NaN) since the last check, SFH_ECUDA on a CUDA error, else SFH_OK. */

@@ -66,6 +66,7 @@ _SIGS = {
                                          ctypes.c_int, vp],
     "sfh_operator_tables": [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp],
     "sfh_peak_fma": [ctypes.c_int, dp, dp],
+    "sfh_entropy_residual": [vp, i64, vp, vp, vp, ctypes.c_int, vp, vp],
     "sfh_selftest_bounded_wait": [ctypes.c_int64, ctypes.c_void_p, dp],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
@@ -161,6 +162,10 @@ def sfh_operator_tables(p: int, nodes: int):
     c = lambda a: a.ctypes.data_as(dp)  # noqa: E731
     _call("sfh_operator_tables", p, nodes, c(xi), c(w), c(D), c(Q1))
     return xi, w, D, Q1
+
+
+def sfh_entropy_residual(ctx: int, n_elem: int, u: int, Ja: int, r: int, r_prec: int, out: int, stream: int = 0):
+    _call("sfh_entropy_residual", ctx, n_elem, u, Ja, r, r_prec, out, stream)
 
 
 def sfh_peak_fma(prec: int):

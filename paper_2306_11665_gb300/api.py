@@ -75,6 +75,18 @@ class Context:
                   torch.cuda.current_stream(u.device).cuda_stream)
         return g
 
+    def entropy_residual(self, u: torch.Tensor, Ja: torch.Tensor, r: torch.Tensor) -> torch.Tensor:
+        """Per-element defect of the entropy identity (FP64, on the GPU) of a
+        residual r of this volume term (float64 or float32) at the FP64 state u."""
+        self._shape_check(u, Ja, torch.float64)
+        if r.shape != u.shape or not r.is_contiguous() or not r.is_cuda or r.dtype not in (torch.float64, torch.float32):
+            raise ValueError("r must be a contiguous float32/float64 CUDA tensor shaped like u")
+        out = torch.empty(u.shape[0], dtype=torch.float64, device=u.device)
+        A.sfh_entropy_residual(self.handle, u.shape[0], u.data_ptr(), Ja.data_ptr(), r.data_ptr(),
+                               A.SFH_FP64 if r.dtype == torch.float64 else A.SFH_FP32_KAHAN, out.data_ptr(),
+                               torch.cuda.current_stream(u.device).cuda_stream)
+        return out
+
     def volume_residual_host(self, u, Ja, prec="fp64"):
         """Host-buffer entry point: u, Ja CPU tensors (pinned for full speed); returns r on the host."""
         pr = _enum(PREC, prec)

@@ -311,6 +311,23 @@ static sfh_status check_common(const sfh_ctx *c, int64_t n_elem, const void *u, 
     return SFH_OK;
 }
 
+extern "C" sfh_status sfh_entropy_residual(sfh_ctx *c, int64_t n_elem, const double *u, const double *Ja,
+                                           const void *r, sfh_prec r_prec, double *out, sfh_stream_t stream) {
+    clear_err();
+    if (r_prec != SFH_FP64 && r_prec != SFH_FP32_KAHAN && r_prec != SFH_FP32_MIXED)
+        return fail(SFH_EINVAL, "bad precision mode %d", (int)r_prec);
+    sfh_status st = check_common(c, n_elem, u, Ja, out, sizeof(double));
+    if (st != SFH_OK || n_elem == 0) return st;
+    if (!r || ((uintptr_t)r % elem_size(r_prec))) return fail(SFH_EINVAL, "null or misaligned residual pointer");
+    if (n_elem > ((int64_t)1 << 31) - 1) return fail(SFH_EINVAL, "n_elem must be below 2^31 (one CTA per element)");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    const cudaError_t e = sfh::entropy_identity(c->d, c->n, c->flux, u, Ja, r, r_prec != SFH_FP64, out, n_elem,
+                                                c->tab_d, c->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "entropy identity kernel launch");
+    return SFH_OK;
+}
+
 extern "C" sfh_status sfh_volume_residual(sfh_ctx *c, int64_t n_elem, const void *u, const double *Ja, void *r,
                                           sfh_prec prec, sfh_stream_t stream) {
     clear_err();

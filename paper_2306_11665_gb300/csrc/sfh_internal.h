@@ -22,6 +22,10 @@ SFH_DECL_VOLUME(volume_mixed_d2, float)
 SFH_DECL_VOLUME(volume_mixed_d3, float)
 #undef SFH_DECL_VOLUME
 
+// Entropy-identity defect per element (sfh_entropy.cu); r in FP32 or FP64.
+cudaError_t entropy_identity(int d, int n, int flux, const double *u, const double *Ja, const void *r, bool r_fp32,
+                             double *out, int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);
+
 #define SFH_DECL_VJP(name)                                                                          \
     cudaError_t name(int n, int flux, const double *u, const double *Ja, const double *lam, double *g, \
                      int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);

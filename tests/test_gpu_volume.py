@@ -192,6 +192,39 @@ def test_large_mesh_64bit_offsets(prec):
         fp32_check(got, ref, ref_w, lambda: kappa(3, 4, 0, "euler", u[base], Ja[base], ref))
 
 
+@pytest.mark.parametrize("d, p, kind, flux", [(3, 4, 0, "euler"), (3, 7, 1, "euler"), (3, 3, 1, "euler"),
+                                             (2, 5, 1, "euler"), (2, 4, 0, "burgers"), (3, 2, 1, "burgers")])
+def test_entropy_residual_kernel_matches_host(d, p, kind, flux):
+    """The GPU's FP64 entropy-identity defect against the host evaluation of
+    the same identity (tests/_entropy.py), for FP64 and FP32 residuals; and the
+    whole mesh under the bars."""
+    N = 2 if (d == 3 and p >= 7) else 3
+    u, Ja = I.workload(d, p, kind, N, flux=flux)
+    ctx = api.Context(d, p, kind, flux)
+    ut, Jt = torch.from_numpy(u).cuda(), torch.from_numpy(Ja).cuda()
+    for prec, bar in (("fp64", 1e-10), ("fp32k", 1e-4)):
+        src = u if prec == "fp64" else I.to_fp32(u)
+        r = ctx.volume_residual(torch.from_numpy(np.ascontiguousarray(src)).cuda(), Jt, prec)
+        dev = ctx.entropy_residual(ut, Jt, r).cpu().numpy()
+        assert ctx.check() == A.SFH_OK
+        assert dev.shape == (u.shape[0],) and np.all(dev <= bar), (prec, dev.max())
+        rh = r.double().cpu().numpy()
+        fl = FLUXES[flux]
+        for e in (0, u.shape[0] - 1):
+            host = identity_residual(d, p, kind, fl, u[e], Ja[e], rh[e])
+            assert abs(dev[e] - host) <= 1e-15 + 1e-6 * host, (prec, e, dev[e], host)
+
+
+def test_entropy_residual_detects_a_wrong_residual():
+    u, Ja = I.workload(3, 4, 0, 2)
+    ctx = api.Context(3, 4, "gll", "euler")
+    ut, Jt = torch.from_numpy(u).cuda(), torch.from_numpy(Ja).cuda()
+    r = ctx.volume_residual(ut, Jt, "fp64")
+    r[3, 4, 17] += 1e-3 * r[3].abs().max()   # one energy component off by 0.1 % of the element's scale
+    dev = ctx.entropy_residual(ut, Jt, r).cpu().numpy()
+    assert dev[3] > 1e-8 and np.delete(dev, 3).max() <= 1e-10
+
+
 def test_edge_cases():
     ctx = api.Context(3, 4, "gll", "euler")
     # n_elem = 0 is a no-op
