@@ -316,10 +316,19 @@ extern "C" sfh_status sfh_entropy_residual(sfh_ctx *c, int64_t n_elem, const dou
     clear_err();
     if (r_prec != SFH_FP64 && r_prec != SFH_FP32_KAHAN && r_prec != SFH_FP32_MIXED)
         return fail(SFH_EINVAL, "bad precision mode %d", (int)r_prec);
-    sfh_status st = check_common(c, n_elem, u, Ja, out, sizeof(double));
-    if (st != SFH_OK || n_elem == 0) return st;
-    if (!r || ((uintptr_t)r % elem_size(r_prec))) return fail(SFH_EINVAL, "null or misaligned residual pointer");
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (n_elem < 0) return fail(SFH_EINVAL, "n_elem must be >= 0, got %lld", (long long)n_elem);
+    if (n_elem == 0) return SFH_OK;
     if (n_elem > ((int64_t)1 << 31) - 1) return fail(SFH_EINVAL, "n_elem must be below 2^31 (one CTA per element)");
+    if (!u || !Ja || !r || !out) return fail(SFH_EINVAL, "null array pointer");
+    const size_t resz = elem_size(r_prec);
+    if (((uintptr_t)u | (uintptr_t)Ja | (uintptr_t)out) % sizeof(double) || (uintptr_t)r % resz)
+        return fail(SFH_EINVAL, "misaligned array pointer");
+    const size_t nn = (size_t)sfh::ipow(c->n, c->d);
+    const size_t ub = (size_t)n_elem * c->nvar * nn * sizeof(double), rb = (size_t)n_elem * c->nvar * nn * resz;
+    const size_t jb = (size_t)n_elem * c->d * c->d * nn * sizeof(double), ob = (size_t)n_elem * sizeof(double);
+    if (overlap(out, ob, u, ub) || overlap(out, ob, Ja, jb) || overlap(out, ob, r, rb))
+        return fail(SFH_EINVAL, "output overlaps an input");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
     const cudaError_t e = sfh::entropy_identity(c->d, c->n, c->flux, u, Ja, r, r_prec != SFH_FP64, out, n_elem,

@@ -223,6 +223,11 @@ def test_entropy_residual_detects_a_wrong_residual():
     r[3, 4, 17] += 1e-3 * r[3].abs().max()   # one energy component off by 0.1 % of the element's scale
     dev = ctx.entropy_residual(ut, Jt, r).cpu().numpy()
     assert dev[3] > 1e-8 and np.delete(dev, 3).max() <= 1e-10
+    # an output that overlaps an input is refused before any launch
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_entropy_residual(ctx.handle, u.shape[0], ut.data_ptr(), Jt.data_ptr(), r.data_ptr(), A.SFH_FP64,
+                               ut.data_ptr() + 8)
+    assert e.value.status == A.SFH_EINVAL
 
 
 def test_edge_cases():
