@@ -1,0 +1,48 @@
+"""The benchmark's work accounting (pairs per element, algorithmic bytes and
+flops) checked against the operators themselves: every off-diagonal nonzero
+of Q_m = Q1 (x) W (x) W couples an unordered pair of nodes on one line, each
+pair appearing twice (Q1[a][b] and Q1[b][a] are both nonzero)."""
+import numpy as np
+import pytest
+
+import bench
+from tests._entropy import kron_q
+
+
+@pytest.mark.parametrize("d, p, kind", [(3, 2, 0), (3, 4, 0), (3, 3, 1), (2, 5, 1), (2, 6, 0)])
+def test_pairs_per_element_matches_q_nonzeros(d, p, kind):
+    off = 0
+    diag = 0
+    for m in range(d):
+        Q = kron_q(d, p, kind, m)
+        # the oracle's negative-sum diagonal leaves round-off where the exact
+        # entry is zero (interior Gauss-Lobatto nodes, the middle Gauss node)
+        nz = np.abs(Q) > 1e-12 * np.abs(Q).max()
+        off += int(nz.sum() - np.trace(nz))
+        diag += int(np.trace(nz))
+    assert off % 2 == 0
+    assert bench.pairs_per_element(d, p) == off // 2
+    # diagonal terms: Gauss-Lobatto only at the two endpoints of each line
+    n = p + 1
+    lines = d * n ** (d - 1)
+    if kind == 0:
+        assert diag == 2 * lines
+    else:
+        assert diag == lines * sum(1 for a in range(n) if not (n % 2 == 1 and a == n // 2))
+
+
+def test_bytes_per_node():
+    assert bench.bytes_per_node("fp32k", 3) == 112
+    assert bench.bytes_per_node("fp64", 3) == 152
+    assert bench.bytes_per_node("fp32k", 2) == 2 * 4 * 4 + 4 * 8
+
+
+def test_flops_per_element_composition():
+    d, p = 3, 4
+    n = p + 1
+    lines = d * n ** (d - 1)
+    expected = bench.pairs_per_element(d, p) * bench.PAIR_FLOPS + lines * 2 * bench.GAMMA_DIAG \
+        + n ** d * (bench.NODE_FLOPS + 10 * d)
+    assert bench.flops_per_element(d, p, 0) == expected
+    # Gauss: a diagonal term at every node of every line
+    assert bench.flops_per_element(d, p, 1) - bench.flops_per_element(d, p, 0) == lines * (n - 2) * bench.GAMMA_DIAG
