@@ -438,6 +438,36 @@ def other_configs(torch, A, I, api, stream, hbm_peak):
     return out
 
 
+def fig1_gpu(torch, A, stream):
+    """The paper's timing experiment (Section 3, Fig. 1) on the GPU: the
+    generic Hadamard product sum_m (D_m o c c^T) 1, dense and sum-factorized,
+    p = 3..15, c ~ U[1e-8, 30]; enough elements per launch to fill the GPU
+    (about four million nodes); time per element and the log-log slopes
+    against n = p + 1 (the paper: 6 and 4 on one CPU core)."""
+    sh = stream.cuda_stream
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    ps, t_sf, t_dn = list(range(3, 16)), [], []
+    for p in ps:
+        n3 = (p + 1) ** 3
+        E = max(1, (4 << 20) // n3)
+        c = torch.rand((E, n3), dtype=torch.float64, device="cuda", generator=gen) * 30.0 + 1e-8
+        y = torch.empty_like(c)
+        _, ms = timed_launches(lambda: A.sfh_fig1_hadamard(p, E, c.data_ptr(), y.data_ptr(), False, sh), 10, 2,
+                               stream, torch)
+        t_sf.append(ms * 1e3 / E)
+        _, ms = timed_launches(lambda: A.sfh_fig1_hadamard(p, E, c.data_ptr(), y.data_ptr(), True, sh), 2, 1,
+                               stream, torch)
+        t_dn.append(ms * 1e3 / E)
+        del c, y
+    n = np.log(np.array(ps) + 1.0)
+    big = np.array(ps) >= 7   # the asymptotic range
+    return {"p": ps, "sf_us_per_element": t_sf, "dense_us_per_element": t_dn,
+            "slope_sf_p7_15": float(np.polyfit(n[big], np.log(np.array(t_sf)[big]), 1)[0]),
+            "slope_dense_p7_15": float(np.polyfit(n[big], np.log(np.array(t_dn)[big]), 1)[0]),
+            "dense_over_sf_p15": t_dn[-1] / t_sf[-1]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -611,6 +641,7 @@ def main():
         variants["vjp_fp64"] = {"element_dof_per_s": dof / (tv * 1e-3), "ms": tv, "forward_fp64_ms": t64}
         assert ctx.check() == A.SFH_OK
         variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
+        variants["fig1_gpu"] = fig1_gpu(torch, A, stream)
         if not args.no_serve:
             variants["serve"] = serve_bench(torch, A, I, api)
             variants["serve_vjp20"] = serve_bench(torch, A, I, api, n_req=1000, loads=(0.8,), vjp_share=0.2)

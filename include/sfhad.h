@@ -184,6 +184,18 @@ sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, double *w, do
  * ("" if none).  Never NULL. */
 const char *sfh_last_error(void);
 
+/* The generic Hadamard product of the paper's timing experiment (Section 3,
+ * Fig. 1): for each of n_elem elements of (p+1)^3 Gauss-Lobatto nodes
+ * (x fastest), y = sum_{m=1..3} (D_m o C) 1 with C = c c^T and D_m the
+ * derivative of the collocated Lagrange basis along direction m (the factor
+ * D in the m-th position of D (x) I (x) I, Eq. 5 without weights).
+ * dense = 0: the sum-factorized O(n^{d+1}) evaluation (Section 2);
+ * dense != 0: the direct O(n^{2d}) evaluation over all columns.
+ * p in [1, 15]; c, y: device double [n_elem][(p+1)^3], 8-byte aligned, y
+ * must not overlap c.  Asynchronous on `stream`; argument errors
+ * (SFH_EINVAL) before any launch, SFH_ECUDA if the launch fails. */
+sfh_status sfh_fig1_hadamard(int p, int64_t n_elem, const double *c, double *y, int dense, sfh_stream_t stream);
+
 /* Library version as major * 10000 + minor * 100 + patch. */
 int sfh_version(void);
 

@@ -67,6 +67,7 @@ _SIGS = {
     "sfh_operator_tables": [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp],
     "sfh_peak_fma": [ctypes.c_int, dp, dp],
     "sfh_entropy_residual": [vp, i64, vp, vp, vp, ctypes.c_int, vp, vp],
+    "sfh_fig1_hadamard": [ctypes.c_int, i64, vp, vp, ctypes.c_int, vp],
     "sfh_selftest_bounded_wait": [ctypes.c_int64, ctypes.c_void_p, dp],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
@@ -166,6 +167,10 @@ def sfh_operator_tables(p: int, nodes: int):
 
 def sfh_entropy_residual(ctx: int, n_elem: int, u: int, Ja: int, r: int, r_prec: int, out: int, stream: int = 0):
     _call("sfh_entropy_residual", ctx, n_elem, u, Ja, r, r_prec, out, stream)
+
+
+def sfh_fig1_hadamard(p: int, n_elem: int, c: int, y: int, dense: bool, stream: int = 0):
+    _call("sfh_fig1_hadamard", p, n_elem, c, y, 1 if dense else 0, stream)
 
 
 def sfh_peak_fma(prec: int):

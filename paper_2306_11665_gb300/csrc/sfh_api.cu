@@ -61,10 +61,10 @@ void legendre2(int k, long double x, long double &Pk, long double &Pkm1) {
     Pkm1 = a;
 }
 
-bool make_tables(int p, int kind, long double *x, long double *w, long double *D) {
+bool make_tables(int p, int kind, long double *x, long double *w, long double *D, int pmax = sfh::NMAX - 1) {
     const int n = p + 1;
     const long double PI = 3.141592653589793238462643383279502884L;
-    if (p < 1 || p > sfh::NMAX - 1) return false;
+    if (p < 1 || p > pmax) return false;
     if (kind == SFH_NODES_GAUSS) {
         for (int j = 0; j < n; ++j) {
             long double xx = -cosl(PI * (4 * j + 3) / (4 * n + 2));
@@ -308,6 +308,27 @@ static sfh_status check_common(const sfh_ctx *c, int64_t n_elem, const void *u, 
     const size_t ub = (size_t)(n_elem * c->nvar * nn) * esz;
     const size_t jb = (size_t)(n_elem * c->d * c->d * nn) * sizeof(double);
     if (overlap(out, ub, u, ub) || overlap(out, ub, Ja, jb)) return fail(SFH_EINVAL, "output overlaps an input");
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_fig1_hadamard(int p, int64_t n_elem, const double *c, double *y, int dense,
+                                        sfh_stream_t stream) {
+    clear_err();
+    constexpr int kPMax = 15;
+    if (p < 1 || p > kPMax) return fail(SFH_EINVAL, "p must be in [1, %d], got %d", kPMax, p);
+    if (n_elem < 0) return fail(SFH_EINVAL, "n_elem must be >= 0");
+    if (n_elem == 0) return SFH_OK;
+    if (!c || !y) return fail(SFH_EINVAL, "null array pointer");
+    if (((uintptr_t)c | (uintptr_t)y) % sizeof(double)) return fail(SFH_EINVAL, "misaligned array pointer");
+    const int n = p + 1;
+    const size_t bytes = (size_t)n_elem * n * n * n * sizeof(double);
+    if (overlap(y, bytes, c, bytes)) return fail(SFH_EINVAL, "output overlaps the input");
+    long double x[kPMax + 1], ww[kPMax + 1], DD[(kPMax + 1) * (kPMax + 1)];
+    if (!make_tables(p, SFH_NODES_GLL, x, ww, DD, kPMax)) return fail(SFH_EINVAL, "table construction failed");
+    double D[(kPMax + 1) * (kPMax + 1)];
+    for (int k = 0; k < n * n; ++k) D[k] = (double)DD[k];
+    const cudaError_t e = sfh::fig1_hadamard(n, dense != 0, c, y, n_elem, D, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "Hadamard kernel launch");
     return SFH_OK;
 }
 

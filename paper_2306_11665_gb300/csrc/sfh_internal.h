@@ -22,6 +22,11 @@ SFH_DECL_VOLUME(volume_mixed_d2, float)
 SFH_DECL_VOLUME(volume_mixed_d3, float)
 #undef SFH_DECL_VOLUME
 
+// Generic Hadamard product of the Fig. 1 experiment (sfh_fig1.cu); D is the
+// n x n Gauss-Lobatto derivative, row-major.
+cudaError_t fig1_hadamard(int n, bool dense, const double *c, double *y, int64_t n_elem, const double *D,
+                          cudaStream_t stream);
+
 // Entropy-identity defect per element (sfh_entropy.cu); r in FP32 or FP64.
 cudaError_t entropy_identity(int d, int n, int flux, const double *u, const double *Ja, const void *r, bool r_fp32,
                              double *out, int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);
