@@ -27,6 +27,7 @@ NODES_GLL = 0
 NODES_GAUSS = 1
 FLUX_BURGERS = 0
 FLUX_EULER = 1
+FLUX_CHANDRASHEKAR = 2
 GAMMA = 1.4
 
 _lib = None

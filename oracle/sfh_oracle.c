@@ -28,6 +28,13 @@
  *     gamma = 1.4, logarithmic means with the near-equal series of Ranocha,
  *     Schlottke-Lakemper, Winters, Faulhaber, Chan, Gassner (2021) (threshold
  *     1e-4 on ((a-b)/(a+b))^2).
+ *   - Euler, second flux: Chandrashekar's entropy-conserving, kinetic-energy-
+ *     preserving flux (Commun. Comput. Phys. 2013), the flux the paper names
+ *     for its TGV runs (Section 3; the pressure fix it cites is not stated in
+ *     the paper and is not applied here).  With beta = rho/p:
+ *     f_rho = {rho}_ln {v.n}, f_m = f_rho {v} + ({rho}/{beta}) n,
+ *     f_E = f_rho (1/((g-1){beta}_ln) - {|v|^2}/2) + {v}.f_m.
+ *     It differs from Ranocha's flux only in the pressure terms.
  *
  * Return codes: 0 = ok, 1 = bad argument, 2 = non-positive density or
  * pressure met (the output is still filled).
@@ -44,6 +51,7 @@
 #define ORC_GAMMA 1.4
 #define ORC_FLUX_BURGERS 0
 #define ORC_FLUX_EULER 1
+#define ORC_FLUX_CHANDRASHEKAR 2
 #define ORC_NODES_GLL 0
 #define ORC_NODES_GAUSS 1
 
@@ -263,6 +271,21 @@ int orc_ec_flux(int d, int flux, const double *ui, const double *uj, const doubl
     int st = euler_prim(d, ui, &ri, vi, &pi) | euler_prim(d, uj, &rj, vj, &pj);
     double rho_ln = orc_logmean(ri, rj);
     double beta_ln = orc_logmean(ri / pi, rj / pj);
+    if (flux == ORC_FLUX_CHANDRASHEKAR) {
+        double vn = 0.0, v2 = 0.0, p_t = (ri + rj) / (ri / pi + rj / pj);   /* {rho} / {beta} */
+        for (int k = 0; k < d; ++k) {
+            vn += 0.5 * (vi[k] + vj[k]) * nv[k];
+            v2 += 0.5 * (vi[k] * vi[k] + vj[k] * vj[k]);
+        }
+        double f_rho = rho_ln * vn, fe = 0.0;
+        F[0] = f_rho;
+        for (int l = 0; l < d; ++l) {
+            F[1 + l] = f_rho * 0.5 * (vi[l] + vj[l]) + p_t * nv[l];
+            fe += 0.5 * (vi[l] + vj[l]) * F[1 + l];
+        }
+        F[d + 1] = f_rho * (1.0 / ((ORC_GAMMA - 1.0) * beta_ln) - 0.5 * v2) + fe;
+        return st;
+    }
     double vni = 0.0, vnj = 0.0, vivj = 0.0;
     for (int k = 0; k < d; ++k) { vni += vi[k] * nv[k]; vnj += vj[k] * nv[k]; vivj += vi[k] * vj[k]; }
     double f_rho = rho_ln * 0.5 * (vni + vnj);
@@ -279,6 +302,7 @@ int orc_ec_flux(int d, int flux, const double *ui, const double *uj, const doubl
  * derivatives above (beta = rho / p). */
 int orc_ec_flux_jac1(int d, int flux, const double *ui, const double *uj, const double *nv, double *J)
 {
+    if (flux == ORC_FLUX_CHANDRASHEKAR) return 1;   /* the adjoint covers Burgers and Ranocha's flux */
     if (flux == ORC_FLUX_BURGERS) {
         double a = ui[0], b = uj[0], S = 0.0;
         for (int k = 0; k < d; ++k) S += nv[k];
@@ -350,8 +374,8 @@ static int check_args(int d, int p, int kind, int nvar, int flux)
     if (d < 2 || d > 3 || p < 1 || p > 8) return 1;
     if (kind != ORC_NODES_GLL && kind != ORC_NODES_GAUSS) return 1;
     if (flux == ORC_FLUX_BURGERS && nvar != 1) return 1;
-    if (flux == ORC_FLUX_EULER && nvar != d + 2) return 1;
-    if (flux != ORC_FLUX_BURGERS && flux != ORC_FLUX_EULER) return 1;
+    if ((flux == ORC_FLUX_EULER || flux == ORC_FLUX_CHANDRASHEKAR) && nvar != d + 2) return 1;
+    if (flux != ORC_FLUX_BURGERS && flux != ORC_FLUX_EULER && flux != ORC_FLUX_CHANDRASHEKAR) return 1;
     return 0;
 }
 
