@@ -34,7 +34,8 @@
  *     the paper and is not applied here).  With beta = rho/p:
  *     f_rho = {rho}_ln {v.n}, f_m = f_rho {v} + ({rho}/{beta}) n,
  *     f_E = f_rho (1/((g-1){beta}_ln) - {|v|^2}/2) + {v}.f_m.
- *     It differs from Ranocha's flux only in the pressure terms.
+ *     It differs from Ranocha's flux only in the pressure terms; the adjoint
+ *     (orc_ec_flux_jac1) covers both.
  *
  * Return codes: 0 = ok, 1 = bad argument, 2 = non-positive density or
  * pressure met (the output is still filled).
@@ -302,7 +303,6 @@ int orc_ec_flux(int d, int flux, const double *ui, const double *uj, const doubl
  * derivatives above (beta = rho / p). */
 int orc_ec_flux_jac1(int d, int flux, const double *ui, const double *uj, const double *nv, double *J)
 {
-    if (flux == ORC_FLUX_CHANDRASHEKAR) return 1;   /* the adjoint covers Burgers and Ranocha's flux */
     if (flux == ORC_FLUX_BURGERS) {
         double a = ui[0], b = uj[0], S = 0.0;
         for (int k = 0; k < d; ++k) S += nv[k];
@@ -331,6 +331,12 @@ int orc_ec_flux_jac1(int d, int flux, const double *ui, const double *uj, const 
     for (int k = 0; k < d; ++k) dfrho_dv[k] = Lr * 0.5 * nv[k];
     double dK_drho = dK_dLb * dLb * (1.0 / pi);
     double dK_dp = dK_dLb * dLb * (-ri / (pi * pi));
+    /* Chandrashekar's pressure average pt = (rho_i + rho_j) / (beta_i + beta_j)
+     * and its derivatives (through rho_i directly and through beta_i) */
+    int ch = flux == ORC_FLUX_CHANDRASHEKAR;
+    double sb = bi + bj, pt = (ri + rj) / sb;
+    double dpt_drho = 1.0 / sb - pt / sb * (1.0 / pi);
+    double dpt_dp = pt / sb * (ri / (pi * pi));
     /* mass */
     dFw[0][0] = dfrho_drho;
     for (int k = 0; k < d; ++k) dFw[0][1 + k] = dfrho_dv[k];
@@ -340,13 +346,20 @@ int orc_ec_flux_jac1(int d, int flux, const double *ui, const double *uj, const 
         dFw[1 + l][0] = dfrho_drho * vavg;
         for (int k = 0; k < d; ++k)
             dFw[1 + l][1 + k] = dfrho_dv[k] * vavg + (k == l ? 0.5 * f_rho : 0.0);
-        dFw[1 + l][d + 1] = 0.5 * nv[l];
+        if (ch) {
+            dFw[1 + l][0] += dpt_drho * nv[l];
+            dFw[1 + l][d + 1] = dpt_dp * nv[l];
+        } else {
+            dFw[1 + l][d + 1] = 0.5 * nv[l];
+        }
     }
-    /* energy */
-    dFw[d + 1][0] = dfrho_drho * K + f_rho * dK_drho;
+    /* energy: pressure work 1/2 (p_i v_j + p_j v_i).n (Ranocha) or
+     * pt {v}.n (Chandrashekar) */
+    double vnavg = 0.5 * (vni + vnj);
+    dFw[d + 1][0] = dfrho_drho * K + f_rho * dK_drho + (ch ? dpt_drho * vnavg : 0.0);
     for (int k = 0; k < d; ++k)
-        dFw[d + 1][1 + k] = dfrho_dv[k] * K + f_rho * 0.5 * vj[k] + 0.5 * pj * nv[k];
-    dFw[d + 1][d + 1] = f_rho * dK_dp + 0.5 * vnj;
+        dFw[d + 1][1 + k] = dfrho_dv[k] * K + f_rho * 0.5 * vj[k] + 0.5 * (ch ? pt : pj) * nv[k];
+    dFw[d + 1][d + 1] = f_rho * dK_dp + (ch ? dpt_dp * vnavg : 0.5 * vnj);
 
     /* dw/du: rho = u0; v_k = u_{1+k}/u0; p = (g-1)(E - |m|^2/(2 rho)) */
     double dwu[5][5];

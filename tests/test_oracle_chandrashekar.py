@@ -112,3 +112,41 @@ def test_pressure_equilibrium_both_fluxes(kind):
     u2, J2 = I.workload(d, p, kind, N)
     r_ra, r_ch = O.volume_sf(d, p, kind, RA, u2, J2), O.volume_sf(d, p, kind, CH, u2, J2)
     assert np.abs(r_ra - r_ch).max() >= 1e-6 * np.abs(r_ra).max()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("spread", [1e-6, 0.01, 0.5])
+def test_flux_jacobian_vs_fd(d, spread):
+    """The adjoint's flux Jacobian (first state) against central differences of
+    the flux itself."""
+    rng = np.random.default_rng(7)
+    for _ in range(10):
+        ui, uj = _state(rng, d, spread), _state(rng, d, spread)
+        nv = rng.uniform(-1, 1, size=d)
+        J = O.ec_flux_jac1(d, CH, ui, uj, nv)
+        for b in range(d + 2):
+            h = 1e-6 * max(1.0, abs(ui[b]))
+            e = np.zeros(d + 2)
+            e[b] = h
+            fd = (O.ec_flux(d, CH, ui + e, uj, nv) - O.ec_flux(d, CH, ui - e, uj, nv)) / (2 * h)
+            np.testing.assert_allclose(J[:, b], fd, rtol=0, atol=2e-8 * (np.abs(fd).max() + 1))
+
+
+@pytest.mark.parametrize("d, kind", [(3, 0), (3, 1), (2, 1)])
+def test_vjp_dense_form_and_fd(d, kind):
+    """Sum-factorized VJP = transpose of the assembled element Jacobian, and
+    directional central differences of the residual."""
+    p = 3
+    u, Ja = I.workload(d, p, kind, 2)
+    lam = I.cotangent(u.shape)
+    g = O.vjp_sf(d, p, kind, CH, u, Ja, lam)
+    g_de = O.vjp_dense(d, p, kind, CH, u, Ja, lam)
+    assert np.abs(g - g_de).max() <= 1e-13 * np.abs(g_de).max()
+    delta = np.random.default_rng(8).standard_normal(u.shape) * np.maximum(1.0, np.abs(u))
+    h = 1e-6
+    fd = np.sum(lam * (O.volume_sf(d, p, kind, CH, u + h * delta, Ja)
+                       - O.volume_sf(d, p, kind, CH, u - h * delta, Ja))) / (2 * h)
+    assert abs(np.sum(g * delta) - fd) <= 1e-6 * abs(fd)
+    # the adjoints of the two fluxes differ (the pressure terms enter them)
+    g_ra = O.vjp_sf(d, p, kind, RA, u, Ja, lam)
+    assert np.abs(g - g_ra).max() >= 1e-6 * np.abs(g_ra).max()
