@@ -640,6 +640,24 @@ def main():
         _, tv = timed_launches(stepvjp, k64, 2, stream, torch)
         variants["vjp_fp64"] = {"element_dof_per_s": dof / (tv * 1e-3), "ms": tv, "forward_fp64_ms": t64}
         assert ctx.check() == A.SFH_OK
+
+        # Chandrashekar's flux (the flux of the paper's TGV runs) on the same workload
+        cch = api.Context(d, p, kind, "euler_chandrashekar")
+        ch = {}
+        for name, prec, src, out in (("fp32k", A.SFH_FP32_KAHAN, tu32, r32), ("fp64", A.SFH_FP64, tu64, r64),
+                                     ("fp32mix", A.SFH_FP32_MIXED, tu32, r32)):
+            def stepch(prec=prec, src=src, out=out):
+                A.sfh_volume_residual(cch.handle, E, src.data_ptr(), tJ.data_ptr(), out.data_ptr(), prec, sh)
+            _, tch = timed_launches(stepch, k64, 2, stream, torch)
+            ch[name] = {"element_dof_per_s": dof / (tch * 1e-3), "ms": tch,
+                        "entropy_identity_defect_max": entropy_defect_max(torch, cch, tu64, tJ, out)}
+
+        def stepchv():
+            A.sfh_vjp(cch.handle, E, tu64.data_ptr(), tJ.data_ptr(), lam.data_ptr(), g.data_ptr(), sh)
+        _, tchv = timed_launches(stepchv, k64, 2, stream, torch)
+        ch["vjp_fp64"] = {"element_dof_per_s": dof / (tchv * 1e-3), "ms": tchv}
+        assert cch.check() == A.SFH_OK
+        variants["chandrashekar"] = ch
         variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
         variants["fig1_gpu"] = fig1_gpu(torch, A, stream)
         if not args.no_serve:

@@ -64,7 +64,13 @@ typedef enum { SFH_NODES_GLL = 0, SFH_NODES_GAUSS = 1 } sfh_nodes;
 
 typedef enum {
     SFH_FLUX_BURGERS = 0,       /* fsharp_k(a, b) = (a^2 + a b + b^2) / 6 in every direction k */
-    SFH_FLUX_EULER_RANOCHA = 1  /* Ranocha EC/KEP flux with logarithmic means, gamma = 1.4 */
+    SFH_FLUX_EULER_RANOCHA = 1, /* Ranocha EC/KEP flux with logarithmic means, gamma = 1.4:
+                                   f_m = f_rho {v} + {p} n, pressure work (p_a v_b + p_b v_a).n / 2 */
+    SFH_FLUX_EULER_CHANDRASHEKAR = 2 /* Chandrashekar's EC/KEP flux (named for the TGV runs of
+                                   Section 3): as Ranocha's but with the pressure average
+                                   {rho}/{beta} (beta = rho/p) and pressure work {rho}/{beta} {v}.n.
+                                   Residual, VJP, entropy identity and the host entry points;
+                                   not served by the serving runtime (Ranocha's flux only) */
 } sfh_flux;
 
 typedef enum {
@@ -79,7 +85,7 @@ typedef struct sfh_ctx sfh_ctx;
 /* Create a context for one element type (Section 2: d directions, n = p + 1
  * nodes on each, collocated Lagrange basis; Eq. 5 operators).
  * d in {2, 3}; p in [1, 8]; nvar must be 1 for SFH_FLUX_BURGERS and d + 2 for
- * SFH_FLUX_EULER_RANOCHA.  Builds the 1D operator tables (nodes, weights,
+ * the Euler fluxes.  Builds the 1D operator tables (nodes, weights,
  * D, Q1 = W D) on the host and allocates the device error word on the
  * current device.  *out is set only on SFH_OK.
  * Errors: SFH_EINVAL for bad arguments; SFH_ECUDA / SFH_EUNSUPPORTED when no

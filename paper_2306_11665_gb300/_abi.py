@@ -20,7 +20,7 @@ SFH_EBUSY, SFH_ENOTREADY, SFH_ETIMEOUT, SFH_EUNSUPPORTED = 5, 6, 7, 8
 STATUS_NAMES = {0: "SFH_OK", 1: "SFH_EINVAL", 2: "SFH_ENOMEM", 3: "SFH_ECUDA", 4: "SFH_EDOMAIN",
                 5: "SFH_EBUSY", 6: "SFH_ENOTREADY", 7: "SFH_ETIMEOUT", 8: "SFH_EUNSUPPORTED"}
 SFH_NODES_GLL, SFH_NODES_GAUSS = 0, 1
-SFH_FLUX_BURGERS, SFH_FLUX_EULER_RANOCHA = 0, 1
+SFH_FLUX_BURGERS, SFH_FLUX_EULER_RANOCHA, SFH_FLUX_EULER_CHANDRASHEKAR = 0, 1, 2
 SFH_FP64, SFH_FP32_KAHAN, SFH_FP32_MIXED = 0, 1, 2
 SFH_REQ_RESIDUAL, SFH_REQ_VJP = 0, 1
 

@@ -10,7 +10,8 @@ import torch
 from . import _abi as A
 
 NODES = {"gll": A.SFH_NODES_GLL, "gauss": A.SFH_NODES_GAUSS}
-FLUX = {"burgers": A.SFH_FLUX_BURGERS, "euler": A.SFH_FLUX_EULER_RANOCHA}
+FLUX = {"burgers": A.SFH_FLUX_BURGERS, "euler": A.SFH_FLUX_EULER_RANOCHA,
+        "euler_chandrashekar": A.SFH_FLUX_EULER_CHANDRASHEKAR}
 PREC = {"fp64": A.SFH_FP64, "fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED}
 PREC_DTYPE = {A.SFH_FP64: torch.float64, A.SFH_FP32_KAHAN: torch.float32, A.SFH_FP32_MIXED: torch.float32}
 

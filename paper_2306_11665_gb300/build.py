@@ -36,6 +36,8 @@ INST = [
     ("vjp_d2", ["-DSFH_INST_VJP", "-DSFH_INST_D=2"]),
     ("vjp_d3", ["-DSFH_INST_VJP", "-DSFH_INST_D=3"]),
 ]
+# Chandrashekar's flux in units of their own (entry points suffixed _ch)
+INST += [(name + "_ch", defs + ["-DSFH_INST_CH"]) for name, defs in list(INST)]
 
 
 def nvcc() -> str:

@@ -207,14 +207,10 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb) {
 cudaError_t launch_volume(sfh_ctx *c, sfh_prec prec, int64_t n_elem, const void *u, const double *Ja, void *r,
                           cudaStream_t s) {
     using namespace sfh;
-    if (prec == SFH_FP64)
-        return c->d == 3 ? volume_fp64_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_d, c->d_err, s)
-                         : volume_fp64_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_d, c->d_err, s);
+    if (prec == SFH_FP64) return volume_fp64_fn(c->d, c->flux)(c->n, c->flux, u, Ja, r, n_elem, c->tab_d, c->d_err, s);
     if (prec == SFH_FP32_KAHAN)
-        return c->d == 3 ? volume_fp32k_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s)
-                         : volume_fp32k_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
-    return c->d == 3 ? volume_mixed_d3(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s)
-                     : volume_mixed_d2(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
+        return volume_fp32k_fn(c->d, c->flux)(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
+    return volume_mixed_fn(c->d, c->flux)(c->n, c->flux, u, Ja, r, n_elem, c->tab_f, c->d_err, s);
 }
 
 }  // namespace
@@ -226,7 +222,8 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
     if (d != 2 && d != 3) return fail(SFH_EINVAL, "d must be 2 or 3, got %d", d);
     if (p < 1 || p > sfh::NMAX - 1) return fail(SFH_EINVAL, "p must be in [1, %d], got %d", sfh::NMAX - 1, p);
     if (nodes != SFH_NODES_GLL && nodes != SFH_NODES_GAUSS) return fail(SFH_EINVAL, "bad node set %d", (int)nodes);
-    if (flux != SFH_FLUX_BURGERS && flux != SFH_FLUX_EULER_RANOCHA) return fail(SFH_EINVAL, "bad flux %d", (int)flux);
+    if (flux != SFH_FLUX_BURGERS && flux != SFH_FLUX_EULER_RANOCHA && flux != SFH_FLUX_EULER_CHANDRASHEKAR)
+        return fail(SFH_EINVAL, "bad flux %d", (int)flux);
     const int want = flux == SFH_FLUX_BURGERS ? 1 : d + 2;
     if (nvar != want) return fail(SFH_EINVAL, "nvar must be %d for this flux and d = %d, got %d", want, d, nvar);
 
@@ -384,8 +381,8 @@ extern "C" sfh_status sfh_vjp(sfh_ctx *c, int64_t n_elem, const double *u, const
     if (overlap(grad_u, ub, lambda, ub)) return fail(SFH_EINVAL, "grad_u overlaps lambda");
     DeviceGuard g(c->device);
     if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
-    cudaError_t e = c->d == 3 ? sfh::vjp_d3(c->n, c->flux, u, Ja, lambda, grad_u, n_elem, c->tab_d, c->d_err, (cudaStream_t)stream)
-                              : sfh::vjp_d2(c->n, c->flux, u, Ja, lambda, grad_u, n_elem, c->tab_d, c->d_err, (cudaStream_t)stream);
+    cudaError_t e = sfh::vjp_fn(c->d, c->flux)(c->n, c->flux, u, Ja, lambda, grad_u, n_elem, c->tab_d, c->d_err,
+                                              (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "vjp kernel launch");
     return SFH_OK;
 }

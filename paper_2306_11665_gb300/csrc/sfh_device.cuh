@@ -17,7 +17,9 @@ namespace sfh {
 constexpr int NMAX = 9;              // p <= 8
 constexpr double kGamma = 1.4;
 constexpr int kFluxBurgers = 0;
-constexpr int kFluxEuler = 1;
+constexpr int kFluxEuler = 1;     // Ranocha's entropy-conserving, kinetic-energy-preserving flux
+constexpr int kFluxEulerCh = 2;   // Chandrashekar's: the same but for the pressure terms
+__host__ __device__ constexpr bool is_euler(int flux) { return flux == kFluxEuler || flux == kFluxEulerCh; }
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
@@ -55,13 +57,13 @@ struct Shape {
     using TJ = typename M::TJ;
     static constexpr int NN = ipow(N, D);
     static constexpr int NLINE = ipow(N, D - 1);
-    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
-    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;   // rho, v[D], p, beta | u
+    static constexpr int NVAR = is_euler(FLUX) ? D + 2 : 1;
+    static constexpr int NP = is_euler(FLUX) ? D + 3 : 1;   // rho, v[D], p, beta | u
     // FP64 Euler keeps FP32 copies of rho and beta (band tests), the mixed
     // mode an FP64 copy of beta: 8 extra bytes per node either way
-    static constexpr bool F64E = sizeof(T) == 8 && FLUX == kFluxEuler;
+    static constexpr bool F64E = sizeof(T) == 8 && is_euler(FLUX);
     static constexpr int NODE_BYTES = (int)sizeof(T) * (NP + NVAR) + (int)sizeof(TJ) * D
-                                      + (((M::mixed || F64E) && FLUX == kFluxEuler) ? 8 : 0);
+                                      + (((M::mixed || F64E) && is_euler(FLUX)) ? 8 : 0);
     static constexpr int SMEM_BUDGET = BUDGET;
     static constexpr int EPB_SMEM = SMEM_BUDGET / (NN * NODE_BYTES) > 0 ? SMEM_BUDGET / (NN * NODE_BYTES) : 1;
     static constexpr int TARGET_LINES = LINES > 0 ? LINES : (NLINE >= 48 ? 256 : 128);

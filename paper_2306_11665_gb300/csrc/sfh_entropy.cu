@@ -31,10 +31,10 @@ constexpr int kEntThreads = 128;
 template <int D, int N, int FLUX>
 struct EntShape {
     static constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
-    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
+    static constexpr int NVAR = is_euler(FLUX) ? D + 2 : 1;
     // per node: flux state (rho, v/2 [D], p, beta, FP32 copies of rho and beta
     // in one word) | u ; entropy variables w [NVAR]; potential psi [D]
-    static constexpr int NS = FLUX == kFluxEuler ? D + 4 : 1;
+    static constexpr int NS = is_euler(FLUX) ? D + 4 : 1;
     static constexpr int PER_NODE = NS + NVAR + D;
     static constexpr size_t SMEM = (size_t)PER_NODE * NN * sizeof(double);
 };
@@ -62,7 +62,7 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
     double lhs = 0.0, rhs = 0.0, scale = 0.0;
     bool bad = false;
     for (int i = tid; i < NN; i += kEntThreads) {
-        if constexpr (FLUX == kFluxEuler) {
+        if constexpr (is_euler(FLUX)) {
             const double rho = ue[i], E = ue[(D + 1) * NN + i];
             double v[D], v2 = 0.0;
 #pragma unroll
@@ -150,7 +150,7 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
                 const double qab = omega * tab.Q1[a * N + b], qba = omega * tab.Q1[b * N + a];
                 if (b == a && qab == 0.0) continue;
                 double F[NVAR];
-                if constexpr (FLUX == kFluxEuler) {
+                if constexpr (is_euler(FLUX)) {
                     auto node = [&](int i) {
                         EulerNodeD<D> nd;
                         nd.rho = sS[i];
@@ -170,7 +170,7 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
                         euler_diag_flux_f64<D>(A, F);
                     } else {
                         const EulerNodeD<D> B = node(ib);
-                        euler_pair_flux_f64<D>(A, B, F);
+                        euler_pair_flux_f64<D, FLUX>(A, B, F);
                     }
                 } else {
                     double Sj = 0.0;
@@ -247,12 +247,18 @@ cudaError_t entropy_identity(int d, int n, int flux, const double *u, const doub
         if (flux == kFluxEuler)
             return r_fp32 ? dispatch_n<3, kFluxEuler, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
                           : dispatch_n<3, kFluxEuler, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
+        if (flux == kFluxEulerCh)
+            return r_fp32 ? dispatch_n<3, kFluxEulerCh, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
+                          : dispatch_n<3, kFluxEulerCh, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
         return r_fp32 ? dispatch_n<3, kFluxBurgers, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
                       : dispatch_n<3, kFluxBurgers, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
     }
     if (flux == kFluxEuler)
         return r_fp32 ? dispatch_n<2, kFluxEuler, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
                       : dispatch_n<2, kFluxEuler, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
+    if (flux == kFluxEulerCh)
+        return r_fp32 ? dispatch_n<2, kFluxEulerCh, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
+                      : dispatch_n<2, kFluxEulerCh, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
     return r_fp32 ? dispatch_n<2, kFluxBurgers, float>(n, u, Ja, r, out, n_elem, tab, err, stream)
                   : dispatch_n<2, kFluxBurgers, double>(n, u, Ja, r, out, n_elem, tab, err, stream);
 }

@@ -1,7 +1,9 @@
-// sfh_inst.cu -- kernel instantiation unit.  Compiled once per (mode, d):
-//   -DSFH_INST_D=<2|3> and one of -DSFH_INST_FP64 / -DSFH_INST_FP32K /
-//   -DSFH_INST_MIXED / -DSFH_INST_VJP.
-// Splitting the instances over several objects keeps the build parallel.
+// sfh_inst.cu -- kernel instantiation unit.  Compiled once per (mode, d,
+// flux family): -DSFH_INST_D=<2|3>, one of -DSFH_INST_FP64 / -DSFH_INST_FP32K
+// / -DSFH_INST_MIXED / -DSFH_INST_VJP, and -DSFH_INST_CH for the units of
+// Chandrashekar's flux (entry points suffixed _ch; the others hold Burgers
+// and Ranocha's flux).  Splitting the instances over several objects keeps
+// the build parallel.
 #include "sfh_internal.h"
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
@@ -13,21 +15,41 @@
 #error "SFH_INST_D must be defined"
 #endif
 
+#include <type_traits>
+
 #define SFH_CAT2(a, b) a##b
 #define SFH_CAT(a, b) SFH_CAT2(a, b)
+#if defined(SFH_INST_CH)
+#define SFH_NAME(base) SFH_CAT(SFH_CAT(base, SFH_INST_D), _ch)
+#else
+#define SFH_NAME(base) SFH_CAT(base, SFH_INST_D)
+#endif
 
 namespace sfh {
 
+// Calls fn(std::integral_constant<int, FLUX>) for the fluxes this unit
+// instantiates.
+template <class Fn>
+static cudaError_t pick_flux(int flux, Fn fn) {
+#if defined(SFH_INST_CH)
+    if (flux == kFluxEulerCh) return fn(std::integral_constant<int, kFluxEulerCh>{});
+#else
+    if (flux == kFluxEuler) return fn(std::integral_constant<int, kFluxEuler>{});
+    if (flux == kFluxBurgers) return fn(std::integral_constant<int, kFluxBurgers>{});
+#endif
+    return cudaErrorInvalidValue;
+}
+
 #if defined(SFH_INST_VJP)
 
-cudaError_t SFH_CAT(vjp_d, SFH_INST_D)(int n, int flux, const double *u, const double *Ja,
-                                       const double *lam, double *g, int64_t n_elem,
-                                       const OpTab<double> &tab, int *err, cudaStream_t stream) {
+cudaError_t SFH_NAME(vjp_d)(int n, int flux, const double *u, const double *Ja, const double *lam, double *g,
+                           int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
-#define SFH_CASE(N)                                                                                     \
-    case N:                                                                                             \
-        return flux == kFluxEuler ? launch_vjp<D, N, kFluxEuler>(u, Ja, lam, g, n_elem, tab, err, stream) \
-                                  : launch_vjp<D, N, kFluxBurgers>(u, Ja, lam, g, n_elem, tab, err, stream);
+#define SFH_CASE(N)                                                                                  \
+    case N:                                                                                          \
+        return pick_flux(flux, [&](auto F) {                                                         \
+            return launch_vjp<D, N, decltype(F)::value>(u, Ja, lam, g, n_elem, tab, err, stream);  \
+        });
     switch (n) {
         SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
         default: return cudaErrorInvalidValue;
@@ -78,13 +100,13 @@ cudaError_t launch_fp64(const void *u, const double *Ja, void *r, int64_t n_elem
 
 #if defined(SFH_INST_FP64)
 using Mode = ModeFP64;
-#define SFH_FN SFH_CAT(volume_fp64_d, SFH_INST_D)
+#define SFH_FN SFH_NAME(volume_fp64_d)
 #elif defined(SFH_INST_FP32K)
 using Mode = ModeFP32K;
-#define SFH_FN SFH_CAT(volume_fp32k_d, SFH_INST_D)
+#define SFH_FN SFH_NAME(volume_fp32k_d)
 #elif defined(SFH_INST_MIXED)
 using Mode = ModeMixed;
-#define SFH_FN SFH_CAT(volume_mixed_d, SFH_INST_D)
+#define SFH_FN SFH_NAME(volume_mixed_d)
 #else
 #error "no instantiation mode"
 #endif
@@ -95,10 +117,11 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
 #if defined(SFH_INST_FP32K)
     // FP32-Kahan: the persistent TMA-staged kernels (a thread per line, or a
     // thread per line and node for 3D Euler at high degree)
-#define SFH_TCASE(N)                                                                                         \
-    case N:                                                                                                  \
-        return flux == kFluxEuler ? launch_fp32k<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream)       \
-                                  : launch_fp32k<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
+#define SFH_TCASE(N)                                                                                   \
+    case N:                                                                                            \
+        return pick_flux(flux, [&](auto F) {                                                           \
+            return launch_fp32k<D, N, decltype(F)::value>(u, Ja, r, n_elem, tab, err, stream);        \
+        });
     switch (n) {
         SFH_TCASE(2) SFH_TCASE(3) SFH_TCASE(4) SFH_TCASE(5) SFH_TCASE(6) SFH_TCASE(7) SFH_TCASE(8) SFH_TCASE(9)
         default: return cudaErrorInvalidValue;
@@ -106,25 +129,29 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
 #undef SFH_TCASE
 #endif
 #if defined(SFH_INST_FP64)
-#define SFH_DCASE(N)                                                                                    \
-    case N:                                                                                             \
-        return flux == kFluxEuler ? launch_fp64<D, N, kFluxEuler>(u, Ja, r, n_elem, tab, err, stream)   \
-                                  : launch_fp64<D, N, kFluxBurgers>(u, Ja, r, n_elem, tab, err, stream);
+#define SFH_DCASE(N)                                                                                   \
+    case N:                                                                                            \
+        return pick_flux(flux, [&](auto F) {                                                           \
+            return launch_fp64<D, N, decltype(F)::value>(u, Ja, r, n_elem, tab, err, stream);         \
+        });
     switch (n) {
         SFH_DCASE(2) SFH_DCASE(3) SFH_DCASE(4) SFH_DCASE(5) SFH_DCASE(6) SFH_DCASE(7) SFH_DCASE(8) SFH_DCASE(9)
         default: return cudaErrorInvalidValue;
     }
 #undef SFH_DCASE
 #endif
-#define SFH_CASE(N)                                                                                              \
-    case N:                                                                                                      \
-        return flux == kFluxEuler ? launch_volume<D, N, kFluxEuler, Mode>(u, Ja, r, n_elem, tab, err, stream)     \
-                                  : launch_volume<D, N, kFluxBurgers, Mode>(u, Ja, r, n_elem, tab, err, stream);
+#if defined(SFH_INST_MIXED)
+#define SFH_CASE(N)                                                                                    \
+    case N:                                                                                             \
+        return pick_flux(flux, [&](auto F) {                                                            \
+            return launch_volume<D, N, decltype(F)::value, Mode>(u, Ja, r, n_elem, tab, err, stream);  \
+        });
     switch (n) {
         SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
         default: return cudaErrorInvalidValue;
     }
 #undef SFH_CASE
+#endif
 }
 
 #endif

@@ -9,8 +9,8 @@
 
 namespace sfh {
 
-// One entry point per (precision mode, dimension) instantiation unit; each
-// dispatches on n = p + 1 (2..9) and the flux.
+// One entry point per (precision mode, dimension, flux family) instantiation
+// unit; each dispatches on n = p + 1 (2..9) and the flux.
 #define SFH_DECL_VOLUME(name, T)                                                                   \
     cudaError_t name(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,     \
                      const OpTab<T> &tab, int *err, cudaStream_t stream);
@@ -20,7 +20,32 @@ SFH_DECL_VOLUME(volume_fp32k_d2, float)
 SFH_DECL_VOLUME(volume_fp32k_d3, float)
 SFH_DECL_VOLUME(volume_mixed_d2, float)
 SFH_DECL_VOLUME(volume_mixed_d3, float)
+// Chandrashekar's flux (flux == kFluxEulerCh only)
+SFH_DECL_VOLUME(volume_fp64_d2_ch, double)
+SFH_DECL_VOLUME(volume_fp64_d3_ch, double)
+SFH_DECL_VOLUME(volume_fp32k_d2_ch, float)
+SFH_DECL_VOLUME(volume_fp32k_d3_ch, float)
+SFH_DECL_VOLUME(volume_mixed_d2_ch, float)
+SFH_DECL_VOLUME(volume_mixed_d3_ch, float)
 #undef SFH_DECL_VOLUME
+
+// The instantiation unit's entry point for a (d, flux).
+using VolumeFn64 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<double> &,
+                                   int *, cudaStream_t);
+using VolumeFn32 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<float> &,
+                                   int *, cudaStream_t);
+inline VolumeFn64 volume_fp64_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_fp64_d3_ch : volume_fp64_d2_ch;
+    return d == 3 ? volume_fp64_d3 : volume_fp64_d2;
+}
+inline VolumeFn32 volume_fp32k_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_fp32k_d3_ch : volume_fp32k_d2_ch;
+    return d == 3 ? volume_fp32k_d3 : volume_fp32k_d2;
+}
+inline VolumeFn32 volume_mixed_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_mixed_d3_ch : volume_mixed_d2_ch;
+    return d == 3 ? volume_mixed_d3 : volume_mixed_d2;
+}
 
 // Generic Hadamard product of the Fig. 1 experiment (sfh_fig1.cu); D is the
 // n x n Gauss-Lobatto derivative, row-major.
@@ -36,13 +61,17 @@ cudaError_t entropy_identity(int d, int n, int flux, const double *u, const doub
                      int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);
 SFH_DECL_VJP(vjp_d2)
 SFH_DECL_VJP(vjp_d3)
+SFH_DECL_VJP(vjp_d2_ch)
+SFH_DECL_VJP(vjp_d3_ch)
 #undef SFH_DECL_VJP
+
+inline cudaError_t (*vjp_fn(int d, int flux))(int, int, const double *, const double *, const double *, double *,
+                                              int64_t, const OpTab<double> &, int *, cudaStream_t) {
+    if (flux == kFluxEulerCh) return d == 3 ? vjp_d3_ch : vjp_d2_ch;
+    return d == 3 ? vjp_d3 : vjp_d2;
+}
 
 // Set the calling thread's message returned by sfh_last_error().
 void set_error_message(const char *msg);
-
-// Elements per CTA of the forward kernel for a (d, n, flux, mode): the unit
-// in which the serving runtime cuts requests into tiles.
-int volume_epb(int mode, int d, int n, int flux);
 
 }  // namespace sfh

@@ -71,7 +71,8 @@ extern "C" sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes n
     sfh::set_error_message("");
     if (d != 2 && d != 3) return na_fail(SFH_EINVAL, "d must be 2 or 3, got %d", d);
     if (p < 1 || p > sfh::NMAX - 1) return na_fail(SFH_EINVAL, "p must be in [1, %d], got %d", sfh::NMAX - 1, p);
-    if (flux != SFH_FLUX_BURGERS && flux != SFH_FLUX_EULER_RANOCHA) return na_fail(SFH_EINVAL, "bad flux %d", (int)flux);
+    if (flux != SFH_FLUX_BURGERS && flux != SFH_FLUX_EULER_RANOCHA && flux != SFH_FLUX_EULER_CHANDRASHEKAR)
+        return na_fail(SFH_EINVAL, "bad flux %d", (int)flux);
     if (prec != SFH_FP64 && prec != SFH_FP32_KAHAN && prec != SFH_FP32_MIXED)
         return na_fail(SFH_EINVAL, "bad precision mode %d", (int)prec);
     if (n_elem < 0) return na_fail(SFH_EINVAL, "n_elem must be >= 0");
@@ -126,14 +127,11 @@ extern "C" sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes n
         (e = cudaMemcpyAsync(dj, Ja_host, jb, cudaMemcpyHostToDevice, s)) != cudaSuccess)
         return na_fail(SFH_ECUDA, "staging copy: %s", cudaGetErrorString(e));
     if (prec == SFH_FP64)
-        e = d == 3 ? sfh::volume_fp64_d3(n, flux, du, (const double *)dj, dr, n_elem, tab_d, d_err, s)
-                   : sfh::volume_fp64_d2(n, flux, du, (const double *)dj, dr, n_elem, tab_d, d_err, s);
+        e = sfh::volume_fp64_fn(d, flux)(n, flux, du, (const double *)dj, dr, n_elem, tab_d, d_err, s);
     else if (prec == SFH_FP32_KAHAN)
-        e = d == 3 ? sfh::volume_fp32k_d3(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s)
-                   : sfh::volume_fp32k_d2(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s);
+        e = sfh::volume_fp32k_fn(d, flux)(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s);
     else
-        e = d == 3 ? sfh::volume_mixed_d3(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s)
-                   : sfh::volume_mixed_d2(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s);
+        e = sfh::volume_mixed_fn(d, flux)(n, flux, du, (const double *)dj, dr, n_elem, tab_f, d_err, s);
     if (e != cudaSuccess) return na_fail(SFH_ECUDA, "volume kernel launch: %s", cudaGetErrorString(e));
     int h_err = 0;
     if ((e = cudaMemcpyAsync(r_host, dr, ub, cudaMemcpyDeviceToHost, s)) != cudaSuccess ||

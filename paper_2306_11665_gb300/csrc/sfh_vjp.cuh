@@ -24,8 +24,8 @@ template <int D, int N, int FLUX, int BUDGET = 96 * 1024, int LINES = 128>
 struct VjpShape {
     static constexpr int NN = ipow(N, D);
     static constexpr int NLINE = ipow(N, D - 1);
-    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
-    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;
+    static constexpr int NVAR = is_euler(FLUX) ? D + 2 : 1;
+    static constexpr int NP = is_euler(FLUX) ? D + 3 : 1;
     static constexpr int NODE_BYTES = 8 * (2 * NP + NVAR + D);
     static constexpr int EPB_SMEM = BUDGET / (NN * NODE_BYTES) > 0 ? BUDGET / (NN * NODE_BYTES) : 1;
     static constexpr int EPB_LINES = LINES / NLINE > 0 ? LINES / NLINE : 1;
@@ -34,9 +34,10 @@ struct VjpShape {
     static constexpr size_t SMEM = (size_t)EPB * NN * NODE_BYTES;
 };
 
-// Reverse mode of the contracted Ranocha flux: adds d(c^T F)/d(prim) of both
-// states.  prim order: rho, v[0..D-1], p, beta.
-template <int D>
+// Reverse mode of the contracted Euler flux (Ranocha's, or Chandrashekar's
+// with pressure average pt = (rho_a + rho_b) / (beta_a + beta_b)): adds
+// d(c^T F)/d(prim) of both states.  prim order: rho, v[0..D-1], p, beta.
+template <int D, int FLUX>
 __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *PB, const double *n,
                                                const double *c, double *ga, double *gb) {
     const double ra = PA[0], rb = PB[0], pa = PA[D + 1], pb = PB[D + 1];
@@ -68,15 +69,31 @@ __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *P
     }
     const double hK_bar = 0.5 * cE * frho;
     const double Lr_bar = frho_bar * h, h_bar = frho_bar * Lr;
-    const double vna_bar = 0.5 * fma(cE, pb, h_bar);
-    const double vnb_bar = 0.5 * fma(cE, pa, h_bar);
+    double vna_bar, vnb_bar;
+    if constexpr (FLUX == kFluxEulerCh) {
+        // F_m += pt n, F_E += pt h: pt's adjoint goes to rho and beta of both
+        const double sr = ra + rb, sb = PA[D + 2] + PB[D + 2], isb = rcp_nr(sb);
+        double pt = sr * isb;
+        pt = fma(isb, fma(-sb, pt, sr), pt);
+        const double pt_bar = fma(cE, h, pavg_bar);
+        const double sr_bar = pt_bar * isb, sb_bar = -sr_bar * pt;
+        ga[0] += sr_bar;
+        gb[0] += sr_bar;
+        ga[D + 2] += sb_bar;
+        gb[D + 2] += sb_bar;
+        vna_bar = vnb_bar = 0.5 * fma(cE, pt, h_bar);
+    } else {
+        // F_m += {p} n, F_E += (p_a v_b + p_b v_a).n / 2
+        vna_bar = 0.5 * fma(cE, pb, h_bar);
+        vnb_bar = 0.5 * fma(cE, pa, h_bar);
+        ga[D + 1] += 0.5 * fma(cE, vnb, pavg_bar);
+        gb[D + 1] += 0.5 * fma(cE, vna, pavg_bar);
+    }
 #pragma unroll
     for (int k = 0; k < D; ++k) {
         ga[1 + k] += fma(hK_bar, PB[1 + k], vna_bar * n[k]);
         gb[1 + k] += fma(hK_bar, PA[1 + k], vnb_bar * n[k]);
     }
-    ga[D + 1] += 0.5 * fma(cE, vnb, pavg_bar);
-    gb[D + 1] += 0.5 * fma(cE, vna, pavg_bar);
     ga[0] = fma(Lr_bar, Lra, ga[0]);
     gb[0] = fma(Lr_bar, Lrb, gb[0]);
     const double M_bar = cE * frho * (1.0 / (kGamma - 1.0));
@@ -103,7 +120,7 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         const int el = s / NN, i = s - el * NN;
         const double *ue = ub + (int64_t)el * NVAR * NN + i;
         double *pe = sP + el * NP * NN + i;
-        if constexpr (FLUX == kFluxEuler) {
+        if constexpr (is_euler(FLUX)) {
             const double rho = ue[0], E = ue[(D + 1) * NN], irho = rcp_nr(rho);
             double ke = 0.0;
 #pragma unroll
@@ -180,8 +197,8 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
 #pragma unroll
                         for (int v = 0; v < NVAR; ++v) c[v] = fma(qbw, sL[(el * NVAR + v) * NN + ib], qab * LA[v]);
                     }
-                    if constexpr (FLUX == kFluxEuler) {
-                        euler_pair_vjp<D>(PA, PB, n, c, GA, GB);
+                    if constexpr (is_euler(FLUX)) {
+                        euler_pair_vjp<D, FLUX>(PA, PB, n, c, GA, GB);
                     } else {
                         double S = 0.0;
 #pragma unroll
@@ -207,7 +224,7 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         const double *pe = sP + el * NP * NN + i;
         const double *ae = sA + el * NP * NN + i;
         double *ge = gbp + (int64_t)el * NVAR * NN + i;
-        if constexpr (FLUX == kFluxEuler) {
+        if constexpr (is_euler(FLUX)) {
             const double rho = pe[0], p = pe[(D + 1) * NN], beta = pe[(D + 2) * NN];
             const double irho = rcp_nr(rho), ip = rcp_nr(p);
             const double bbar = ae[(D + 2) * NN];

@@ -39,8 +39,12 @@ struct BurgersNode {
     TJ S;            // sum_k Ja^m_k
 };
 
-// Two-point Euler flux contracted with n = Ja^m(a) + Ja^m(b) (Ranocha).
-template <class M, int D>
+// Two-point Euler flux contracted with n = Ja^m(a) + Ja^m(b): Ranocha's
+//   f_rho = {rho}_ln {v.n},  f_m = f_rho {v} + {p} n,
+//   f_E = f_rho (v_a.v_b / 2 + 1/((g-1){beta}_ln)) + (p_a v_b + p_b v_a).n / 2,
+// or Chandrashekar's, which takes pt = {rho}/{beta} = (rho_a + rho_b) /
+// (beta_a + beta_b) for {p} and pt {v}.n for the pressure work.
+template <class M, int D, int FLUX>
 __device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
                                                 const EulerNode<typename M::T, typename M::TJ, D> &B,
                                                 typename M::T F[D + 2]) {
@@ -74,11 +78,27 @@ __device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, t
     }
     const T half = (T)0.5;
     const T frho = Lr * (half * (vna + vnb));
-    const T pavg = half * (A.p + B.p);
+    T pavg;
+    if constexpr (FLUX == kFluxEulerCh) {
+        // (rho_a + rho_b) / (beta_a + beta_b) to within about half an ulp
+        const T sr = A.rho + B.rho, sb = A.beta + B.beta;
+        T isb;
+        if constexpr (sizeof(T) == 8) {
+            isb = rcp_nr(sb);
+        } else {
+            isb = rcp_approx(sb);
+            isb = fma(isb, fma(-sb, isb, (T)1), isb);
+        }
+        pavg = sr * isb;
+        pavg = fma(isb, fma(-sb, pavg, sr), pavg);
+    } else {
+        pavg = half * (A.p + B.p);
+    }
     F[0] = frho;
 #pragma unroll
     for (int l = 0; l < D; ++l) F[1 + l] = frho * (half * (A.v[l] + B.v[l])) + pavg * n[l];
-    F[D + 1] = frho * (half * vv + iLb * (T)(1.0 / (kGamma - 1.0))) + half * (A.p * vnb + B.p * vna);
+    const T work = FLUX == kFluxEulerCh ? pavg * (half * (vna + vnb)) : half * (A.p * vnb + B.p * vna);
+    F[D + 1] = frho * (half * vv + iLb * (T)(1.0 / (kGamma - 1.0))) + work;
 }
 
 // FP64 pair flux: the node carries v/2 (hv) and FP32 copies of rho and beta
@@ -90,7 +110,7 @@ struct EulerNodeD {
     float rf, bf;
 };
 
-template <int D>
+template <int D, int FLUX = kFluxEuler>
 __device__ __forceinline__ void euler_pair_flux_f64(const EulerNodeD<D> &A, const EulerNodeD<D> &B, double F[D + 2]) {
     double n[D];
 #pragma unroll
@@ -105,12 +125,22 @@ __device__ __forceinline__ void euler_pair_flux_f64(const EulerNodeD<D> &A, cons
     const double Lr = ln_mean_f64(A.rho, B.rho, A.rf, B.rf);
     const double iLb = inv_ln_mean_f64(A.beta, B.beta, A.bf, B.bf);
     const double frho = Lr * (hna + hnb);              // {rho}_ln {v.n}
-    const double pavg = 0.5 * (A.p + B.p);
+    double pavg;
+    if constexpr (FLUX == kFluxEulerCh) {
+        // {rho}/{beta} to within about half an ulp (Newton reciprocal, one
+        // residual correction)
+        const double sr = A.rho + B.rho, sb = A.beta + B.beta, isb = rcp_nr(sb);
+        pavg = sr * isb;
+        pavg = fma(isb, fma(-sb, pavg, sr), pavg);
+    } else {
+        pavg = 0.5 * (A.p + B.p);
+    }
     F[0] = frho;
 #pragma unroll
     for (int k = 0; k < D; ++k) F[1 + k] = fma(frho, A.hv[k] + B.hv[k], pavg * n[k]);
     const double K = fma(2.0, hvv, iLb * (1.0 / (kGamma - 1.0)));
-    F[D + 1] = fma(frho, K, fma(A.p, hnb, B.p * hna));
+    if constexpr (FLUX == kFluxEulerCh) F[D + 1] = fma(frho, K, pavg * (hna + hnb));
+    else F[D + 1] = fma(frho, K, fma(A.p, hnb, B.p * hna));
 }
 
 template <int D>
@@ -166,7 +196,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     constexpr bool F64E = S::F64E;
     double *sBd = reinterpret_cast<double *>(smem_raw);
     float *sRF = reinterpret_cast<float *>(smem_raw);
-    constexpr int BD_COUNT = ((M::mixed || F64E) && FLUX == kFluxEuler) ? EPB * NN : 0;
+    constexpr int BD_COUNT = ((M::mixed || F64E) && is_euler(FLUX)) ? EPB * NN : 0;
     TJ *sJ = reinterpret_cast<TJ *>(smem_raw + sizeof(double) * BD_COUNT);
     T *sP = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sJ) + sizeof(TJ) * EPB * D * NN);
     T *sR = sP + EPB * NP * NN;
@@ -179,7 +209,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
         const int el = s / NN, i = s - el * NN;
         const T *ue = ub + (int64_t)el * NVAR * NN + i;
         T *pe = sP + el * NP * NN + i;
-        if constexpr (FLUX == kFluxEuler) {
+        if constexpr (is_euler(FLUX)) {
             // reciprocals refined by Newton steps instead of IEEE divisions
             // (FP64: rcp_nr; FP32: hardware seed + one step); beta = rho / p
             // to within about half an ulp by one residual correction, and in
@@ -289,7 +319,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 #pragma unroll
                     for (int b = a + 1; b < N; ++b) {
                         double F[D + 2];
-                        euler_pair_flux_f64<D>(nd[a], nd[b], F);
+                        euler_pair_flux_f64<D, FLUX>(nd[a], nd[b], F);
                         const double qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
 #pragma unroll
                         for (int v = 0; v < NVAR; ++v) { acc[a][v].add_prod(qab, F[v]); acc[b][v].add_prod(qba, F[v]); }
@@ -302,7 +332,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
                         for (int v = 0; v < NVAR; ++v) acc[a][v].add_prod(qaa, F[v]);
                     }
                 }
-            } else if constexpr (FLUX == kFluxEuler) {
+            } else if constexpr (is_euler(FLUX)) {
                 EulerNode<T, TJ, D> nd[N];
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
@@ -323,7 +353,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 #pragma unroll
                     for (int b = a + 1; b < N; ++b) {
                         T F[D + 2];
-                        euler_pair_flux<M, D>(nd[a], nd[b], F);
+                        euler_pair_flux<M, D, FLUX>(nd[a], nd[b], F);
                         const T qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
 #pragma unroll
                         for (int v = 0; v < NVAR; ++v) { acc[a][v].add_prod(qab, F[v]); acc[b][v].add_prod(qba, F[v]); }

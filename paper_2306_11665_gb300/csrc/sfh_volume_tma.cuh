@@ -38,12 +38,12 @@ namespace sfh {
 // 80, 96, 125, 150, 205, 230 registers for 3D Euler n = 2..9).
 template <int D, int N, int FLUX>
 constexpr int tma_cps() {
-    if (FLUX != kFluxEuler) return 2;
+    if (!is_euler(FLUX)) return 2;
     return N <= (D == 3 ? 6 : 7) ? 2 : 1;
 }
 template <int D, int N, int FLUX>
 constexpr int tma_wps() {
-    if (FLUX != kFluxEuler) return 3;
+    if (!is_euler(FLUX)) return 3;
     if (D == 3) return N <= 3 ? 4 : (N == 4 ? 3 : 2);
     return N <= 4 ? 4 : (N <= 7 ? 2 : 3);
 }
@@ -54,15 +54,15 @@ struct TmaShape {
     static constexpr int WPS = tma_wps<D, N, FLUX>();   // per CTA
     static constexpr int NN = ipow(N, D);
     static constexpr int NLINE = ipow(N, D - 1);
-    static constexpr int NVAR = FLUX == kFluxEuler ? D + 2 : 1;
-    static constexpr int NP = FLUX == kFluxEuler ? D + 3 : 1;      // rho, v/2 [D], p, beta | u
-    static constexpr int NJ = FLUX == kFluxEuler ? D * D : D;       // FP32 metric values kept per node
+    static constexpr int NVAR = is_euler(FLUX) ? D + 2 : 1;
+    static constexpr int NP = is_euler(FLUX) ? D + 3 : 1;      // rho, v/2 [D], p, beta | u
+    static constexpr int NJ = is_euler(FLUX) ? D * D : D;       // FP32 metric values kept per node
     // Euler keeps the FP32 metric rows line-major per direction,
     // [el][m][line][a][k], so that a line's values sit at constant offsets
     // from one base; LJ = floats per line, odd so that the lines of
     // consecutive lanes fall in different banks
     static constexpr int LJ = (N * D) % 2 == 0 ? N * D + 1 : N * D;
-    static constexpr int JF_EL = FLUX == kFluxEuler ? D * NLINE * LJ : D * NN;   // floats per element
+    static constexpr int JF_EL = is_euler(FLUX) ? D * NLINE * LJ : D * NN;   // floats per element
     static constexpr int U_EL = NVAR * NN;                          // floats of u (and r) per element
     static constexpr int J_EL = D * D * NN;                         // doubles of Ja per element
     static constexpr int EL_BYTES = 4 * U_EL + 8 * J_EL + 4 * NP * NN + 4 * JF_EL + 4 * D * U_EL;
@@ -151,7 +151,7 @@ __device__ __forceinline__ void line_geometry(int m, int l, const OpTab<float> &
 // series band.  Kept out of line (one copy per kernel) because it runs only
 // for states with large jumps along a line; the arithmetic is that of the
 // fast path otherwise.
-template <int D, int N, int NN, int NP>
+template <int D, int N, int NN, int NP, int FLUX>
 __device__ __noinline__ void euler_line_general(const float *pe, const float *jl, float *re, int stride, float omega,
                                                 const OpTab<float> &tab) {
     constexpr int NVAR = D + 2;
@@ -181,11 +181,13 @@ __device__ __noinline__ void euler_line_general(const float *pe, const float *jl
             const float Lr = ln_mean(ra, rb), iLb = inv_ln_mean(ba, bb);
             float F[D + 2];
             const float frho = Lr * (hna + hnb);
-            const float pavg = 0.5f * (pa + pb);
+            // Chandrashekar: {rho}/{beta} and its work {rho}/{beta} {v}.n
+            const float pavg = FLUX == kFluxEulerCh ? (ra + rb) * rcp_approx(ba + bb) : 0.5f * (pa + pb);
+            const float work = FLUX == kFluxEulerCh ? pavg * (hna + hnb) : fmaf(pa, hnb, pb * hna);
             F[0] = frho;
 #pragma unroll
             for (int k = 0; k < D; ++k) F[1 + k] = fmaf(frho, hva[k] + hvb[k], pavg * n[k]);
-            F[D + 1] = fmaf(frho, fmaf(2.0f, hvv, iLb * (float)(1.0 / (kGamma - 1.0))), fmaf(pa, hnb, pb * hna));
+            F[D + 1] = fmaf(frho, fmaf(2.0f, hvv, iLb * (float)(1.0 / (kGamma - 1.0))), work);
 #pragma unroll
             for (int v = 0; v < NVAR; ++v) acc[v].add_prod(q, F[v]);
         }
@@ -212,7 +214,7 @@ __device__ __forceinline__ bool fp32_block_convert(const float *U, const double 
         const int el = s / NN, i = s - el * NN;
         const float *ue = U + el * U_EL + i;
         float *pe = sP + el * NP * NN + i;
-        if constexpr (FLUX == kFluxEuler) {
+        if constexpr (is_euler(FLUX)) {
             // per-node divisions to within about half an ulp: with the
             // residual's cancellation, per-node errors act like
             // perturbations of the input state.  q = m / rho is formed as
@@ -264,11 +266,11 @@ __device__ __forceinline__ bool fp32_block_convert(const float *U, const double 
             pe[0] = ue[0];
         }
     }
-    if constexpr (FLUX != kFluxEuler) {
+    if constexpr (!is_euler(FLUX)) {
         for (int s = tid; s < ne * D * NN; s += nthreads) {
             const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
             const double *jm = J + ((el * D + m) * D) * NN + i;
-            static_assert(FLUX == kFluxEuler || S::JF_EL == D * NN, "Burgers metric sums are node-major");
+            static_assert(is_euler(FLUX) || S::JF_EL == D * NN, "Burgers metric sums are node-major");
             float acc = d2f_int(jm[0]);
 #pragma unroll
             for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
@@ -303,7 +305,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
             }
             const float *pe = sP + el * NP * NN + base;
             float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
-            if constexpr (FLUX == kFluxEuler) {
+            if constexpr (is_euler(FLUX)) {
                 // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
                 constexpr int NPAIR = NVAR / 2;
                 KahanF2 accp[N][NPAIR];
@@ -359,7 +361,11 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                         umax = fmaxf(umax, u2.x + u2.y);
                         const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
                         const float frho = m2.x * (hna + hnb);      // {rho}_ln {v.n}
-                        const float pavg = 0.5f * (p[a] + p[b]);
+                        // pressure average: {p} (Ranocha) or {rho}/{beta}
+                        // (Chandrashekar), the latter from the sums and
+                        // reciprocals of the log means
+                        const float pavg = FLUX == kFluxEulerCh ? s2.x * r2.y : 0.5f * (p[a] + p[b]);
+                        const float work = FLUX == kFluxEulerCh ? pavg * (hna + hnb) : fmaf(p[a], hnb, p[b] * hna);
                         float2 F01, F23;
                         F01.x = frho;
                         F01.y = fmaf(frho, hv[a][0] + hv[b][0], pavg * n[0]);
@@ -368,10 +374,10 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                         if constexpr (D == 3) {
                             F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
                             F23.y = fmaf(frho, hv[a][2] + hv[b][2], pavg * n[2]);
-                            FE = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            FE = fmaf(frho, K, work);
                         } else {
                             F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
-                            F23.y = fmaf(frho, K, fmaf(p[a], hnb, p[b] * hna));
+                            F23.y = fmaf(frho, K, work);
                             FE = 0.0f;
                         }
                         const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
@@ -411,7 +417,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                 // domain flag of the node pass reports the state)
                 if (__builtin_expect(!(umax < 1e-2f), 0)) {
                     // rare: redo the whole line with logarithms where needed
-                    euler_line_general<D, N, NN, NP>(pe, jl, re, stride, omega, tab);
+                    euler_line_general<D, N, NN, NP, FLUX>(pe, jl, re, stride, omega, tab);
                 } else {
 #pragma unroll
                     for (int a = 0; a < N; ++a) {

@@ -48,7 +48,8 @@ def test_bad_arguments_rejected(A):
     with pytest.raises(A.SfhError) as e:
         A.sfh_create(4, 3, 0, 6, 1)
     assert e.value.status == A.SFH_EINVAL
-    for args in [(3, 0, 0, 5, 1), (3, 9, 0, 5, 1), (3, 3, 2, 5, 1), (3, 3, 0, 4, 1), (2, 3, 0, 2, 0), (3, 3, 0, 5, 7)]:
+    for args in [(3, 0, 0, 5, 1), (3, 9, 0, 5, 1), (3, 3, 2, 5, 1), (3, 3, 0, 4, 1), (2, 3, 0, 2, 0), (3, 3, 0, 5, 7),
+                 (3, 3, 0, 4, 2), (2, 3, 0, 1, 2), (3, 3, 0, 5, 3)]:
         with pytest.raises(A.SfhError) as e:
             A.sfh_create(*args)
         assert e.value.status == A.SFH_EINVAL, args
@@ -65,6 +66,7 @@ def test_no_device_is_reported_not_crashed(A):
     import torch
     if torch.cuda.is_available():
         pytest.skip("a device is present")
-    with pytest.raises(A.SfhError) as e:
-        A.sfh_create(3, 4, 0, 5, 1)
-    assert e.value.status in (A.SFH_EUNSUPPORTED, A.SFH_ECUDA)
+    for flux in (A.SFH_FLUX_EULER_RANOCHA, A.SFH_FLUX_EULER_CHANDRASHEKAR):
+        with pytest.raises(A.SfhError) as e:
+            A.sfh_create(3, 4, 0, 5, flux)
+        assert e.value.status in (A.SFH_EUNSUPPORTED, A.SFH_ECUDA)
