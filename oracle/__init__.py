@@ -68,6 +68,11 @@ def _load():
         lib.orc_mesh.argtypes = [i, i, i, i, ctypes.c_double, dp, dp]
         lib.orc_fig1_dense.argtypes = [i, dp, dp]
         lib.orc_fig1_sf.argtypes = [i, dp, dp]
+        lib.orc_basis_1d.argtypes = [i, i, i, dp]
+        lib.orc_modal_states.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
+        lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
+        lib.orc_entropy_vars.argtypes = [i, i, dp, dp]
+        lib.orc_entropy_state.argtypes = [i, i, dp, dp]
         _lib = lib
     return _lib
 
@@ -198,3 +203,53 @@ def fig1_sf(p: int, c) -> np.ndarray:
     y = np.zeros_like(c)
     _check(_load().orc_fig1_sf(p, _p(c), _p(y)))
     return y
+
+
+BASIS_LEGENDRE, BASIS_LAGRANGE_GLL, BASIS_LAGRANGE_GAUSS = 0, 1, 2
+
+
+def basis_1d(p: int, kind: int, basis: int) -> np.ndarray:
+    """V1[a, k] = chi_k(xi_a) on the cubature nodes of ``kind``."""
+    n = p + 1
+    V = np.zeros((n, n))
+    _check(_load().orc_basis_1d(p, kind, basis, _p(V)))
+    return V
+
+
+def modal_states(d, p, kind, basis, flux, uhat, allow_domain=False):
+    """(u_v, u~): nodal values V u_hat and the entropy-projected state."""
+    uhat = _f64(uhat)
+    nvar = nvar_of(d, flux)
+    assert uhat.shape[1:] == (nvar, (p + 1) ** d), uhat.shape
+    uv, up = np.zeros_like(uhat), np.zeros_like(uhat)
+    _check(_load().orc_modal_states(d, p, kind, basis, nvar, flux, uhat.shape[0], _p(uhat), _p(uv), _p(up)),
+           allow_domain)
+    return uv, up
+
+
+def volume_modal(d, p, kind, basis, flux, uhat, Ja, allow_domain=False) -> np.ndarray:
+    """Modal volume residual r_hat = V^T r_v(u~) (dense transforms, literal
+    entropy projection)."""
+    uhat, Ja = _f64(uhat), _f64(Ja)
+    nvar = nvar_of(d, flux)
+    assert uhat.shape[1:] == (nvar, (p + 1) ** d) and Ja.shape[0] == uhat.shape[0]
+    r = np.zeros_like(uhat)
+    _check(_load().orc_volume_modal(d, p, kind, basis, nvar, flux, uhat.shape[0], _p(uhat), _p(Ja), _p(r)),
+           allow_domain)
+    return r
+
+
+def entropy_vars(d: int, flux: int, u) -> np.ndarray:
+    """Entropy variables w(u) of one state (Burgers: u)."""
+    u = _f64(u)
+    w = np.zeros_like(u)
+    _check(_load().orc_entropy_vars(d, flux, _p(u), _p(w)))
+    return w
+
+
+def entropy_state(d: int, flux: int, w) -> np.ndarray:
+    """Conservative state u(w) of one vector of entropy variables."""
+    w = _f64(w)
+    u = np.zeros_like(w)
+    _check(_load().orc_entropy_state(d, flux, _p(w), _p(u)))
+    return u

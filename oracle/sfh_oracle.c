@@ -43,7 +43,9 @@
  * Parity status: every exported function is pinned by the CPU tests
  * (dense brute force, textbook nodes, SBP identities, Burgers closed form,
  * free stream, entropy identity, conservation, pressure equilibrium, finite
- * differences).  No function here is "parity unpinned".
+ * differences; for the modal path numpy's Legendre series, quadrature closed
+ * forms, sum-factorized transforms and the entropy gradient).  No function
+ * here is "parity unpinned".
  */
 #include <math.h>
 #include <stdlib.h>
@@ -697,3 +699,232 @@ int orc_fig1_sf(int p, const double *c, double *y)
         }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Modal / uncollocated path (Section 2, Eq. 4 and the theorem after it).    */
+/* The solution lives in a tensor-product basis chi (n = p + 1 functions per */
+/* direction) and is integrated on the volume cubature nodes xi of `kind`.   */
+/* With V = chi(xi) (n^d x n^d, V[i][j] = prod_m V1[a_m(i)][b_m(j)]):         */
+/*   u_v  = V u_hat                     (nodal values on the cubature)       */
+/*   w_v  = w(u_v)                      (entropy variables)                  */
+/*   w~   = V Pi w_v,  Pi = M^{-1} V^T W,  M = V^T W V   (entropy projection) */
+/*   u~   = u(w~)                       (projected conservative state)       */
+/*   r_v  = sum_m (Q_m o F_m(u~)) 1     (the collocated volume term, Eq. 3)  */
+/*   r_hat = V^T r_v                    (tested against chi)                 */
+/* Dense matrices throughout: the basis transform is written as the full     */
+/* Kronecker product, not sum-factorized.                                    */
+/* ------------------------------------------------------------------------ */
+#define ORC_BASIS_LEGENDRE 0        /* orthonormal Legendre, sqrt((2k+1)/2) P_k */
+#define ORC_BASIS_LAGRANGE_GLL 1    /* Lagrange on the p+1 Gauss-Lobatto nodes   */
+#define ORC_BASIS_LAGRANGE_GAUSS 2  /* Lagrange on the p+1 Gauss-Legendre nodes  */
+
+/* 1D basis on the cubature nodes of `kind`: V1[a*n + k] = chi_k(xi_a). */
+int orc_basis_1d(int p, int kind, int basis, double *V1)
+{
+    int n = p + 1;
+    double xi[16], w[16];
+    if (p < 1 || p > 15 || orc_nodes(p, kind, xi, w)) return 1;
+    if (basis == ORC_BASIS_LEGENDRE) {
+        for (int a = 0; a < n; ++a)
+            for (int k = 0; k < n; ++k) {
+                long double P, dP, d2P;
+                legendre_eval(k, (long double)xi[a], &P, &dP, &d2P);
+                V1[a * n + k] = (double)(sqrtl((2.0L * k + 1.0L) / 2.0L) * P);
+            }
+        return 0;
+    }
+    if (basis != ORC_BASIS_LAGRANGE_GLL && basis != ORC_BASIS_LAGRANGE_GAUSS) return 1;
+    double s[16], sw[16];
+    orc_nodes(p, basis == ORC_BASIS_LAGRANGE_GLL ? ORC_NODES_GLL : ORC_NODES_GAUSS, s, sw);
+    for (int a = 0; a < n; ++a)
+        for (int k = 0; k < n; ++k) {
+            long double l = 1.0L;
+            for (int j = 0; j < n; ++j)
+                if (j != k) l *= ((long double)xi[a] - s[j]) / ((long double)s[k] - s[j]);
+            V1[a * n + k] = (double)l;
+        }
+    return 0;
+}
+
+/* Entropy variables w(u) of the flux's entropy: Burgers U = u^2/2 (w = u);
+ * Euler U = -rho s/(g-1), s = ln p - g ln rho:
+ *   w = ((g - s)/(g-1) - rho|v|^2/(2p), rho v/p, -rho/p). */
+static int entropy_w(int d, int flux, const double *u, double *w)
+{
+    if (flux == ORC_FLUX_BURGERS) { w[0] = u[0]; return 0; }
+    double rho, v[3], p;
+    int st = euler_prim(d, u, &rho, v, &p);
+    double v2 = 0.0;
+    for (int k = 0; k < d; ++k) v2 += v[k] * v[k];
+    double s = log(p) - ORC_GAMMA * log(rho);
+    w[0] = (ORC_GAMMA - s) / (ORC_GAMMA - 1.0) - rho * v2 / (2.0 * p);
+    for (int k = 0; k < d; ++k) w[1 + k] = rho * v[k] / p;
+    w[d + 1] = -rho / p;
+    return st;
+}
+
+/* Inverse map u(w): beta = -w_E = rho/p, v = w_m/beta,
+ * s = g - (g-1)(w_0 + beta|v|^2/2), and from s = (1-g) ln rho - ln beta:
+ * rho = exp(-(s + ln beta)/(g-1)), p = rho/beta. */
+static int entropy_u(int d, int flux, const double *w, double *u)
+{
+    if (flux == ORC_FLUX_BURGERS) { u[0] = w[0]; return 0; }
+    double beta = -w[d + 1];
+    if (!(beta > 0.0)) return 2;
+    double v[3], v2 = 0.0;
+    for (int k = 0; k < d; ++k) { v[k] = w[1 + k] / beta; v2 += v[k] * v[k]; }
+    double s = ORC_GAMMA - (ORC_GAMMA - 1.0) * (w[0] + 0.5 * beta * v2);
+    double rho = exp(-(s + log(beta)) / (ORC_GAMMA - 1.0));
+    double p = rho / beta;
+    u[0] = rho;
+    for (int k = 0; k < d; ++k) u[1 + k] = rho * v[k];
+    u[d + 1] = p / (ORC_GAMMA - 1.0) + 0.5 * rho * v2;
+    return 0;
+}
+
+/* Solve A x = b (A: m x m row-major, overwritten) by Gaussian elimination
+ * with partial pivoting; nrhs right-hand sides stored as columns of B
+ * (m x nrhs, row-major, overwritten by the solutions). */
+static int dense_solve(int m, double *A, int nrhs, double *B)
+{
+    for (int c = 0; c < m; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < m; ++r)
+            if (fabs(A[(size_t)r * m + c]) > fabs(A[(size_t)piv * m + c])) piv = r;
+        if (A[(size_t)piv * m + c] == 0.0) return 1;
+        if (piv != c) {
+            for (int k = 0; k < m; ++k) { double t = A[(size_t)c * m + k]; A[(size_t)c * m + k] = A[(size_t)piv * m + k]; A[(size_t)piv * m + k] = t; }
+            for (int k = 0; k < nrhs; ++k) { double t = B[(size_t)c * nrhs + k]; B[(size_t)c * nrhs + k] = B[(size_t)piv * nrhs + k]; B[(size_t)piv * nrhs + k] = t; }
+        }
+        for (int r = c + 1; r < m; ++r) {
+            double f = A[(size_t)r * m + c] / A[(size_t)c * m + c];
+            if (f == 0.0) continue;
+            for (int k = c; k < m; ++k) A[(size_t)r * m + k] -= f * A[(size_t)c * m + k];
+            for (int k = 0; k < nrhs; ++k) B[(size_t)r * nrhs + k] -= f * B[(size_t)c * nrhs + k];
+        }
+    }
+    for (int c = m - 1; c >= 0; --c)
+        for (int k = 0; k < nrhs; ++k) {
+            double s = B[(size_t)c * nrhs + k];
+            for (int j = c + 1; j < m; ++j) s -= A[(size_t)c * m + j] * B[(size_t)j * nrhs + k];
+            B[(size_t)c * nrhs + k] = s / A[(size_t)c * m + c];
+        }
+    return 0;
+}
+
+/* The n^d x n^d Kronecker matrix V[i][j] = prod_m V1[a_m(i)][b_m(j)] and the
+ * cubature weights W_d[i] = prod_m w[a_m(i)]. */
+static void modal_dense(int d, int p, int kind, const double *V1, double *V, double *Wd)
+{
+    int n = p + 1, nn = ipow(n, d);
+    double xi[16], w[16];
+    orc_nodes(p, kind, xi, w);
+    for (int i = 0; i < nn; ++i) {
+        int ai[3]; node_to_multi(i, n, d, ai);
+        Wd[i] = 1.0;
+        for (int m = 0; m < d; ++m) Wd[i] *= w[ai[m]];
+        for (int j = 0; j < nn; ++j) {
+            int bj[3]; node_to_multi(j, n, d, bj);
+            double q = 1.0;
+            for (int m = 0; m < d; ++m) q *= V1[ai[m] * n + bj[m]];
+            V[(size_t)i * nn + j] = q;
+        }
+    }
+}
+
+/* Nodal states of the modal path: u_v = V u_hat and the entropy-projected
+ * u~ = u(V Pi w(u_v)), both [e][var][i]. */
+int orc_modal_states(int d, int p, int kind, int basis, int nvar, int flux, long n_elem,
+                     const double *uhat, double *u_nodes, double *u_proj)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    double V1[256];
+    if (orc_basis_1d(p, kind, basis, V1)) return 1;
+    double *V = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *M = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *Wd = (double *)malloc(sizeof(double) * nn);
+    double *rhs = (double *)malloc(sizeof(double) * (size_t)nn * nvar);
+    double *wv = (double *)malloc(sizeof(double) * (size_t)nn * nvar);
+    if (!V || !M || !Wd || !rhs || !wv) { free(V); free(M); free(Wd); free(rhs); free(wv); return 1; }
+    modal_dense(d, p, kind, V1, V, Wd);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = uhat + e * nvar * nn;
+        double *uv = u_nodes + e * nvar * nn, *up = u_proj + e * nvar * nn;
+        /* u_v = V u_hat */
+        for (int v = 0; v < nvar; ++v)
+            for (int i = 0; i < nn; ++i) {
+                double s = 0.0;
+                for (int j = 0; j < nn; ++j) s += V[(size_t)i * nn + j] * ue[v * nn + j];
+                uv[v * nn + i] = s;
+            }
+        /* w_v = w(u_v) per node, stored [i][var] */
+        for (int i = 0; i < nn; ++i) {
+            double ui[5], wi[5];
+            for (int v = 0; v < nvar; ++v) ui[v] = uv[v * nn + i];
+            st |= entropy_w(d, flux, ui, wi);
+            for (int v = 0; v < nvar; ++v) wv[(size_t)i * nvar + v] = wi[v];
+        }
+        /* M = V^T W V, rhs = V^T W w_v; solve M w_hat = rhs */
+        for (int k = 0; k < nn; ++k) {
+            for (int l = 0; l < nn; ++l) {
+                double s = 0.0;
+                for (int i = 0; i < nn; ++i) s += V[(size_t)i * nn + k] * Wd[i] * V[(size_t)i * nn + l];
+                M[(size_t)k * nn + l] = s;
+            }
+            for (int v = 0; v < nvar; ++v) {
+                double s = 0.0;
+                for (int i = 0; i < nn; ++i) s += V[(size_t)i * nn + k] * Wd[i] * wv[(size_t)i * nvar + v];
+                rhs[(size_t)k * nvar + v] = s;
+            }
+        }
+        if (dense_solve(nn, M, nvar, rhs)) st |= 1;
+        /* w~ = V w_hat, u~ = u(w~) */
+        for (int i = 0; i < nn; ++i) {
+            double wi[5], ui[5];
+            for (int v = 0; v < nvar; ++v) {
+                double s = 0.0;
+                for (int k = 0; k < nn; ++k) s += V[(size_t)i * nn + k] * rhs[(size_t)k * nvar + v];
+                wi[v] = s;
+            }
+            st |= entropy_u(d, flux, wi, ui);
+            for (int v = 0; v < nvar; ++v) up[v * nn + i] = ui[v];
+        }
+    }
+    free(V); free(M); free(Wd); free(rhs); free(wv);
+    return st;
+}
+
+/* The modal volume residual r_hat = V^T r_v(u~) of the path above. */
+int orc_volume_modal(int d, int p, int kind, int basis, int nvar, int flux, long n_elem,
+                     const double *uhat, const double *Ja, double *rhat)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st;
+    size_t tot = (size_t)n_elem * nvar * nn;
+    double *uv = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    double *up = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    double *rv = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    double *V = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *Wd = (double *)malloc(sizeof(double) * nn);
+    double V1[256];
+    if (!uv || !up || !rv || !V || !Wd || orc_basis_1d(p, kind, basis, V1)) {
+        free(uv); free(up); free(rv); free(V); free(Wd); return 1;
+    }
+    st = orc_modal_states(d, p, kind, basis, nvar, flux, n_elem, uhat, uv, up);
+    st |= orc_volume_sf(d, p, kind, nvar, flux, n_elem, up, Ja, rv);
+    modal_dense(d, p, kind, V1, V, Wd);
+    for (long e = 0; e < n_elem; ++e)
+        for (int v = 0; v < nvar; ++v)
+            for (int k = 0; k < nn; ++k) {
+                double s = 0.0;
+                for (int i = 0; i < nn; ++i) s += V[(size_t)i * nn + k] * rv[(e * nvar + v) * nn + i];
+                rhat[(e * nvar + v) * nn + k] = s;
+            }
+    free(uv); free(up); free(rv); free(V); free(Wd);
+    return st;
+}
+
+/* Exported for the tests: entropy variables of one state and the inverse. */
+int orc_entropy_vars(int d, int flux, const double *u, double *w) { return entropy_w(d, flux, u, w); }
+int orc_entropy_state(int d, int flux, const double *w, double *u) { return entropy_u(d, flux, w, u); }

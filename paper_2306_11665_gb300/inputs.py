@@ -22,6 +22,14 @@ Recipe (the paper runs its timing on a warped periodic cube, Section 3):
     own PCG64 stream (seeds 2, 3.., 3+d); then conservative variables.
   * Burgers states: u = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), seed 1.
   * Cotangents: N(0,1), seed 8.
+  * Modal inputs (solution in a basis chi, integrated on the cubature nodes of
+    `kind`): for a Lagrange basis on Gauss-Lobatto or Gauss nodes the
+    coefficients are the state above at those solution nodes; for the
+    orthonormal Legendre basis, mode 0 carries the mean state (rho = 1,
+    v = (0.3, -0.2, 0.1), p = 1; Burgers 0.5) times 2^(d/2) (the constant
+    mode's value is 2^(-d/2)) and every mode k of every variable adds
+    0.04 N(0,1) / (1 + |k|_1)^2 (PCG64 seed 12); Ja is the mesh's metric on
+    the cubature nodes.
 """
 from __future__ import annotations
 
@@ -187,3 +195,37 @@ def workload(d: int, p: int, kind: int, N: int, flux: str = "euler", amp: float 
     else:
         u = euler_state(x, 2 if seed0 is None else seed0)
     return np.ascontiguousarray(u), Ja
+
+
+BASIS_LEGENDRE, BASIS_LAGRANGE_GLL, BASIS_LAGRANGE_GAUSS = 0, 1, 2
+
+
+def modal_workload(d: int, p: int, kind: int, basis: int, N: int, flux: str = "euler", amp: float = 0.1,
+                   n_elem: int | None = None, seed: int = 12):
+    """(u_hat, Ja) of a modal workload: coefficients in the basis, metrics on
+    the cubature nodes of ``kind`` (recipe in the module docstring)."""
+    _, Ja = mesh(d, p, kind, N, amp, n_elem)
+    if basis in (BASIS_LAGRANGE_GLL, BASIS_LAGRANGE_GAUSS):
+        sol = NODES_GLL if basis == BASIS_LAGRANGE_GLL else NODES_GAUSS
+        uhat, _ = workload(d, p, sol, N, flux, amp, n_elem)
+        return uhat, Ja
+    if basis != BASIS_LEGENDRE:
+        raise ValueError(f"unknown basis {basis}")
+    n, E = p + 1, Ja.shape[0]
+    nn = n ** d
+    if flux == "burgers":
+        mean = np.array([0.5])
+    else:
+        v = np.array([0.3, -0.2, 0.1][:d])
+        mean = np.concatenate(([1.0], v, [1.0 / (GAMMA - 1.0) + 0.5 * (v @ v)]))
+    kk = np.zeros(nn)
+    for i in range(nn):
+        a, r = 0, i
+        for _ in range(d):
+            a += r % n
+            r //= n
+        kk[i] = a
+    rng = np.random.Generator(np.random.PCG64(seed))
+    uhat = 0.04 * rng.standard_normal((E, mean.size, nn)) / (1.0 + kk) ** 2
+    uhat[:, :, 0] += mean * 2.0 ** (d / 2.0)
+    return np.ascontiguousarray(uhat), Ja
