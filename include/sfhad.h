@@ -80,6 +80,15 @@ typedef enum {
                             FP64 logarithmic mean in the near-equal band; u, r are float */
 } sfh_prec;
 
+/* Solution basis of the modal / uncollocated entry point (Section 2, Eq. 4
+ * and the theorem after it), n = p + 1 functions per direction, tensor
+ * product, evaluated on the context's cubature nodes. */
+typedef enum {
+    SFH_BASIS_LEGENDRE = 0,       /* orthonormal Legendre sqrt((2k + 1)/2) P_k(xi) */
+    SFH_BASIS_LAGRANGE_GLL = 1,   /* Lagrange polynomials of the p + 1 Gauss-Lobatto nodes */
+    SFH_BASIS_LAGRANGE_GAUSS = 2  /* Lagrange polynomials of the p + 1 Gauss-Legendre nodes */
+} sfh_basis;
+
 typedef struct sfh_ctx sfh_ctx;
 
 /* Create a context for one element type (Section 2: d directions, n = p + 1
@@ -107,6 +116,34 @@ sfh_status sfh_destroy(sfh_ctx *ctx);
  * domain errors are latched for sfh_check(). */
 sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, const double *Ja,
                                void *r, sfh_prec prec, sfh_stream_t stream);
+
+/* Modal / uncollocated volume residual (Section 2: Eq. 4, the theorem on
+ * general bases and its proof).  The solution is given by coefficients in the
+ * basis chi; with V = chi(xi) on the context's n^d cubature nodes (Kronecker
+ * product of the 1D table of sfh_basis_table, x fastest),
+ *   r_hat = V^T r_v(V u_hat),
+ * r_v the collocated volume residual of sfh_volume_residual at the nodal
+ * values.  Both transforms are sum-factorized (d n^{d+1} per variable) and
+ * fused into the residual kernels (the nodal values never reach HBM).  The
+ * entropy projection of the uncollocated scheme, u~ = u(V Pi w(V u_hat)) with
+ * Pi = (V^T W V)^{-1} V^T W, is the identity here: V is square and invertible
+ * (as many cubature nodes as basis functions), so Pi = V^{-1} and u~ = V u_hat.
+ * u_hat, r_hat: device, [n_elem][nvar][n^d] (coefficient index k = k_0 +
+ *       n k_1 + n^2 k_2), double for SFH_FP64, float otherwise; Ja: device
+ *       [n_elem][d][d][n^d] double on the cubature nodes.
+ * r_hat is overwritten and must not overlap the inputs.  Asynchronous.
+ * Errors: SFH_EINVAL (bad basis, precision, sizes, alignment, overlap) before
+ * any launch; SFH_ECUDA if the launch fails; domain errors of the nodal
+ * values are latched for sfh_check(). */
+sfh_status sfh_volume_residual_modal(sfh_ctx *ctx, sfh_basis basis, int64_t n_elem, const void *u_hat,
+                                     const double *Ja, void *r_hat, sfh_prec prec, sfh_stream_t stream);
+
+/* The 1D basis table of the modal entry point on the cubature nodes of
+ * `nodes`: V[a*(p+1) + k] = chi_k(xi_a), host memory of (p+1)^2 doubles,
+ * written by the caller-owned pointer.  No device is needed.
+ * Errors: SFH_EINVAL for p outside [1, 8], an unknown node set or basis, or
+ * V == NULL. */
+sfh_status sfh_basis_table(int p, sfh_nodes nodes, sfh_basis basis, double *V);
 
 /* Vector-Jacobian product of the volume residual with respect to u (FP64):
  * grad_u = (dr/du)^T lambda with Ja held fixed, i.e.

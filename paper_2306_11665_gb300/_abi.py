@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "SFH_OK", 1: "SFH_EINVAL", 2: "SFH_ENOMEM", 3: "SFH_ECUDA", 4
 SFH_NODES_GLL, SFH_NODES_GAUSS = 0, 1
 SFH_FLUX_BURGERS, SFH_FLUX_EULER_RANOCHA, SFH_FLUX_EULER_CHANDRASHEKAR = 0, 1, 2
 SFH_FP64, SFH_FP32_KAHAN, SFH_FP32_MIXED = 0, 1, 2
+SFH_BASIS_LEGENDRE, SFH_BASIS_LAGRANGE_GLL, SFH_BASIS_LAGRANGE_GAUSS = 0, 1, 2
 SFH_REQ_RESIDUAL, SFH_REQ_VJP = 0, 1
 
 
@@ -58,6 +59,8 @@ _SIGS = {
     "sfh_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)],
     "sfh_destroy": [vp],
     "sfh_volume_residual": [vp, i64, vp, vp, vp, ctypes.c_int, vp],
+    "sfh_volume_residual_modal": [vp, ctypes.c_int, i64, vp, vp, vp, ctypes.c_int, vp],
+    "sfh_basis_table": [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp],
     "sfh_vjp": [vp, i64, vp, vp, vp, vp, vp],
     "sfh_check": [vp, vp],
     "sfh_volume_residual_host": [vp, i64, vp, vp, vp, ctypes.c_int],
@@ -127,6 +130,18 @@ def sfh_destroy(ctx: int) -> None:
 
 def sfh_volume_residual(ctx: int, n_elem: int, u: int, Ja: int, r: int, prec: int, stream: int = 0) -> None:
     _call("sfh_volume_residual", ctx, n_elem, u, Ja, r, prec, stream)
+
+
+def sfh_volume_residual_modal(ctx: int, basis: int, n_elem: int, u_hat: int, Ja: int, r_hat: int, prec: int,
+                              stream: int = 0) -> None:
+    _call("sfh_volume_residual_modal", ctx, basis, n_elem, u_hat, Ja, r_hat, prec, stream)
+
+
+def sfh_basis_table(p: int, nodes: int, basis: int):
+    import numpy as np
+    V = np.zeros((p + 1, p + 1))
+    _call("sfh_basis_table", p, nodes, basis, V.ctypes.data_as(dp))
+    return V
 
 
 def sfh_vjp(ctx: int, n_elem: int, u: int, Ja: int, lam: int, grad_u: int, stream: int = 0) -> None:

@@ -12,6 +12,8 @@ from . import _abi as A
 NODES = {"gll": A.SFH_NODES_GLL, "gauss": A.SFH_NODES_GAUSS}
 FLUX = {"burgers": A.SFH_FLUX_BURGERS, "euler": A.SFH_FLUX_EULER_RANOCHA,
         "euler_chandrashekar": A.SFH_FLUX_EULER_CHANDRASHEKAR}
+BASIS = {"legendre": A.SFH_BASIS_LEGENDRE, "lagrange_gll": A.SFH_BASIS_LAGRANGE_GLL,
+         "lagrange_gauss": A.SFH_BASIS_LAGRANGE_GAUSS}
 PREC = {"fp64": A.SFH_FP64, "fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED}
 PREC_DTYPE = {A.SFH_FP64: torch.float64, A.SFH_FP32_KAHAN: torch.float32, A.SFH_FP32_MIXED: torch.float32}
 
@@ -64,6 +66,17 @@ class Context:
         r = torch.empty_like(u) if out is None else out
         A.sfh_volume_residual(self.handle, u.shape[0], u.data_ptr(), Ja.data_ptr(), r.data_ptr(), pr,
                               torch.cuda.current_stream(u.device).cuda_stream)
+        return r
+
+    def volume_residual_modal(self, u_hat: torch.Tensor, Ja: torch.Tensor, basis="legendre", prec="fp64",
+                              out: torch.Tensor | None = None):
+        """r_hat = V^T r_v(V u_hat) for coefficients u_hat in ``basis`` (the
+        modal / uncollocated path), on the current stream."""
+        pr, b = _enum(PREC, prec), _enum(BASIS, basis)
+        self._shape_check(u_hat, Ja, PREC_DTYPE[pr])
+        r = torch.empty_like(u_hat) if out is None else out
+        A.sfh_volume_residual_modal(self.handle, b, u_hat.shape[0], u_hat.data_ptr(), Ja.data_ptr(), r.data_ptr(),
+                                    pr, torch.cuda.current_stream(u_hat.device).cuda_stream)
         return r
 
     def vjp(self, u: torch.Tensor, Ja: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None):

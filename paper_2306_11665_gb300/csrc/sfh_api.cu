@@ -139,7 +139,53 @@ bool make_tables(int p, int kind, long double *x, long double *w, long double *D
     return true;
 }
 
+// Solution basis on the cubature nodes x of a context (Section 2, the
+// uncollocated case): V[a*n + k] = chi_k(x_a) with chi_k the orthonormal
+// Legendre polynomial sqrt((2k + 1)/2) P_k, or the Lagrange polynomial of the
+// k-th Gauss-Lobatto / Gauss solution node (product formula).
+bool make_basis(int p, const long double *x, int basis, long double *V) {
+    const int n = p + 1;
+    if (basis == SFH_BASIS_LEGENDRE) {
+        for (int a = 0; a < n; ++a)
+            for (int k = 0; k < n; ++k) {
+                long double P, Pm;
+                legendre2(k, x[a], P, Pm);
+                V[a * n + k] = sqrtl((2.0L * k + 1.0L) / 2.0L) * P;
+            }
+        return true;
+    }
+    if (basis != SFH_BASIS_LAGRANGE_GLL && basis != SFH_BASIS_LAGRANGE_GAUSS) return false;
+    long double s[sfh::NMAX], sw[sfh::NMAX], sD[sfh::NMAX * sfh::NMAX];
+    if (!make_tables(p, basis == SFH_BASIS_LAGRANGE_GLL ? SFH_NODES_GLL : SFH_NODES_GAUSS, s, sw, sD)) return false;
+    for (int a = 0; a < n; ++a)
+        for (int k = 0; k < n; ++k) {
+            long double l = 1.0L;
+            bool same = false;
+            for (int j = 0; j < n; ++j) {
+                if (j == k) continue;
+                l *= (x[a] - s[j]) / (s[k] - s[j]);
+            }
+            // a solution node that coincides with a cubature node: exact 0/1
+            for (int j = 0; j < n; ++j) same |= (x[a] == s[j]);
+            if (same) l = (x[a] == s[k]) ? 1.0L : 0.0L;
+            V[a * n + k] = l;
+        }
+    return true;
+}
+
 }  // namespace
+
+extern "C" sfh_status sfh_basis_table(int p, sfh_nodes nodes, sfh_basis basis, double *V) {
+    clear_err();
+    if (p < 1 || p > sfh::NMAX - 1) return fail(SFH_EINVAL, "p must be in [1, %d], got %d", sfh::NMAX - 1, p);
+    if (nodes != SFH_NODES_GLL && nodes != SFH_NODES_GAUSS) return fail(SFH_EINVAL, "bad node set %d", (int)nodes);
+    if (!V) return fail(SFH_EINVAL, "V is NULL");
+    long double x[sfh::NMAX], ww[sfh::NMAX], DD[sfh::NMAX * sfh::NMAX], VV[sfh::NMAX * sfh::NMAX];
+    if (!make_tables(p, nodes, x, ww, DD) || !make_basis(p, x, basis, VV))
+        return fail(SFH_EINVAL, "bad basis %d", (int)basis);
+    for (int k = 0; k < (p + 1) * (p + 1); ++k) V[k] = (double)VV[k];
+    return SFH_OK;
+}
 
 extern "C" sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, double *w, double *D,
                                           double *Q1) {
@@ -174,6 +220,9 @@ struct sfh_ctx {
     int *d_err;
     sfh::OpTab<double> tab_d;
     sfh::OpTab<float> tab_f;
+    // solution bases on the cubature nodes (indexed by sfh_basis)
+    sfh::BasisTab<double> basis_d[3];
+    sfh::BasisTab<float> basis_f[3];
     // staging of the host-buffer entry point
     std::mutex host_mu;
     cudaStream_t hs[kHostStages];
@@ -257,6 +306,16 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
             const long double q = ww[a] * DD[a * n + b];
             c->tab_d.Q1[a * n + b] = (double)q;
             c->tab_f.Q1[a * n + b] = (float)q;
+        }
+    }
+    for (int b = 0; b < 3; ++b) {
+        long double VV[sfh::NMAX * sfh::NMAX];
+        memset(&c->basis_d[b], 0, sizeof c->basis_d[b]);
+        memset(&c->basis_f[b], 0, sizeof c->basis_f[b]);
+        make_basis(p, x, b, VV);
+        for (int k = 0; k < n * n; ++k) {
+            c->basis_d[b].V[k] = (double)VV[k];
+            c->basis_f[b].V[k] = (float)VV[k];
         }
     }
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
@@ -367,6 +426,33 @@ extern "C" sfh_status sfh_volume_residual(sfh_ctx *c, int64_t n_elem, const void
     cudaError_t e = launch_volume(c, prec, n_elem, u, Ja, r, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "volume kernel launch");
     (void)mode_of;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_volume_residual_modal(sfh_ctx *c, sfh_basis basis, int64_t n_elem, const void *u_hat,
+                                                const double *Ja, void *r_hat, sfh_prec prec, sfh_stream_t stream) {
+    clear_err();
+    if (prec != SFH_FP64 && prec != SFH_FP32_KAHAN && prec != SFH_FP32_MIXED)
+        return fail(SFH_EINVAL, "bad precision mode %d", (int)prec);
+    if (basis != SFH_BASIS_LEGENDRE && basis != SFH_BASIS_LAGRANGE_GLL && basis != SFH_BASIS_LAGRANGE_GAUSS)
+        return fail(SFH_EINVAL, "bad basis %d", (int)basis);
+    sfh_status st = check_common(c, n_elem, u_hat, Ja, r_hat, elem_size(prec));
+    if (st != SFH_OK || n_elem == 0) return st;
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    using namespace sfh;
+    const cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (prec == SFH_FP64)
+        e = modal_fp64_fn(c->d, c->flux)(c->n, c->flux, u_hat, Ja, r_hat, n_elem, c->tab_d, c->basis_d[basis],
+                                         c->d_err, s);
+    else if (prec == SFH_FP32_KAHAN)
+        e = modal_fp32k_fn(c->d, c->flux)(c->n, c->flux, u_hat, Ja, r_hat, n_elem, c->tab_f, c->basis_f[basis],
+                                          c->d_err, s);
+    else
+        e = modal_mixed_fn(c->d, c->flux)(c->n, c->flux, u_hat, Ja, r_hat, n_elem, c->tab_f, c->basis_f[basis],
+                                          c->d_err, s);
+    if (e != cudaSuccess) return cuda_fail(e, "modal volume kernel launch");
     return SFH_OK;
 }
 

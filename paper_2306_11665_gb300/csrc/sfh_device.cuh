@@ -31,6 +31,44 @@ struct OpTab {
     T w[NMAX];
 };
 
+// 1D basis of a modal / uncollocated solution on the cubature nodes:
+// V[a*n + k] = chi_k(xi_a) (node a, basis function k), a kernel parameter.
+template <typename T>
+struct BasisTab {
+    T V[NMAX * NMAX];
+};
+
+// One pass of the sum-factorized basis transform (Section 2, the theorem on
+// uncollocated bases): along direction m, every line of every
+// element-variable q < nq (layout [q][i], NN values each) is multiplied by V
+// (node values from coefficients) or, TRANSPOSE, by V^T (tests against chi).
+// A thread per (q, line); the line's n inputs in registers, the table indices
+// compile-time constants.
+template <typename T, int D, int N, bool TRANSPOSE, typename TI, typename TO>
+__device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq, const BasisTab<T> &bt, int tid,
+                                           int nthreads) {
+    constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
+    const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
+    for (int t = tid; t < nq * NLINE; t += nthreads) {
+        const int q = t / NLINE, l = t - q * NLINE;
+        int base;
+        if constexpr (D == 3) base = m == 0 ? N * l : (m == 1 ? l % N + N * N * (l / N) : l);
+        else base = m == 0 ? N * l : l;
+        const TI *src = in + (size_t)q * NN + base;
+        TO *dst = out + (size_t)q * NN + base;
+        T x[N];
+#pragma unroll
+        for (int b = 0; b < N; ++b) x[b] = (T)src[b * stride];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            T s = (T)0;
+#pragma unroll
+            for (int b = 0; b < N; ++b) s = fma(TRANSPOSE ? bt.V[b * N + a] : bt.V[a * N + b], x[b], s);
+            dst[a * stride] = (TO)s;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Precision modes.
 //   T  : type of u, r and the flux arithmetic

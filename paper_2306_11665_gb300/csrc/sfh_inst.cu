@@ -1,9 +1,10 @@
 // sfh_inst.cu -- kernel instantiation unit.  Compiled once per (mode, d,
-// flux family): -DSFH_INST_D=<2|3>, one of -DSFH_INST_FP64 / -DSFH_INST_FP32K
-// / -DSFH_INST_MIXED / -DSFH_INST_VJP, and -DSFH_INST_CH for the units of
-// Chandrashekar's flux (entry points suffixed _ch; the others hold Burgers
-// and Ranocha's flux).  Splitting the instances over several objects keeps
-// the build parallel.
+// flux family, nodal or modal): -DSFH_INST_D=<2|3>, one of -DSFH_INST_FP64 /
+// -DSFH_INST_FP32K / -DSFH_INST_MIXED / -DSFH_INST_VJP, -DSFH_INST_CH for the
+// units of Chandrashekar's flux (entry points suffixed _ch; the others hold
+// Burgers and Ranocha's flux), and -DSFH_INST_MODAL for the modal entry
+// points (suffixed _modal).  Splitting the instances over several objects
+// keeps the build parallel.
 #include "sfh_internal.h"
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
@@ -19,10 +20,15 @@
 
 #define SFH_CAT2(a, b) a##b
 #define SFH_CAT(a, b) SFH_CAT2(a, b)
-#if defined(SFH_INST_CH)
-#define SFH_NAME(base) SFH_CAT(SFH_CAT(base, SFH_INST_D), _ch)
+#if defined(SFH_INST_MODAL)
+#define SFH_MSUF _modal
 #else
-#define SFH_NAME(base) SFH_CAT(base, SFH_INST_D)
+#define SFH_MSUF
+#endif
+#if defined(SFH_INST_CH)
+#define SFH_NAME(base) SFH_CAT(SFH_CAT(SFH_CAT(base, SFH_INST_D), _ch), SFH_MSUF)
+#else
+#define SFH_NAME(base) SFH_CAT(SFH_CAT(base, SFH_INST_D), SFH_MSUF)
 #endif
 
 namespace sfh {
@@ -111,48 +117,55 @@ using Mode = ModeMixed;
 #error "no instantiation mode"
 #endif
 
+#if defined(SFH_INST_MODAL)
+// Modal / uncollocated entry: u holds basis coefficients, r receives V^T r_v
+// (the basis transforms fused into the kernels).  FP32-Kahan always takes the
+// persistent line kernel.
+cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,
+                   const OpTab<typename Mode::T> &tab, const BasisTab<typename Mode::T> &bt, int *err,
+                   cudaStream_t stream) {
+    constexpr int D = SFH_INST_D;
+#if defined(SFH_INST_FP32K)
+#define SFH_MCALL(N, F) launch_volume_fp32_tma<D, N, F, true>(u, Ja, r, n_elem, tab, err, stream, &bt)
+#elif defined(SFH_INST_FP64)
+#define SFH_MCALL(N, F) launch_volume_modal<D, N, F, Mode, Fp64Shape<D, N, F>>(u, Ja, r, n_elem, tab, bt, err, stream)
+#else
+#define SFH_MCALL(N, F) launch_volume_modal<D, N, F, Mode>(u, Ja, r, n_elem, tab, bt, err, stream)
+#endif
+#define SFH_CASE(N)                                                                                    \
+    case N:                                                                                            \
+        return pick_flux(flux, [&](auto F) { return SFH_MCALL(N, decltype(F)::value); });
+    switch (n) {
+        SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
+        default: return cudaErrorInvalidValue;
+    }
+#undef SFH_CASE
+#undef SFH_MCALL
+}
+#else
 cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,
                    const OpTab<typename Mode::T> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
 #if defined(SFH_INST_FP32K)
     // FP32-Kahan: the persistent TMA-staged kernels (a thread per line, or a
     // thread per line and node for 3D Euler at high degree)
-#define SFH_TCASE(N)                                                                                   \
-    case N:                                                                                            \
-        return pick_flux(flux, [&](auto F) {                                                           \
-            return launch_fp32k<D, N, decltype(F)::value>(u, Ja, r, n_elem, tab, err, stream);        \
-        });
-    switch (n) {
-        SFH_TCASE(2) SFH_TCASE(3) SFH_TCASE(4) SFH_TCASE(5) SFH_TCASE(6) SFH_TCASE(7) SFH_TCASE(8) SFH_TCASE(9)
-        default: return cudaErrorInvalidValue;
-    }
-#undef SFH_TCASE
+#define SFH_VCALL(N, F) launch_fp32k<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
+#elif defined(SFH_INST_FP64)
+#define SFH_VCALL(N, F) launch_fp64<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
+#else
+#define SFH_VCALL(N, F) launch_volume<D, N, F, Mode>(u, Ja, r, n_elem, tab, err, stream)
 #endif
-#if defined(SFH_INST_FP64)
-#define SFH_DCASE(N)                                                                                   \
-    case N:                                                                                            \
-        return pick_flux(flux, [&](auto F) {                                                           \
-            return launch_fp64<D, N, decltype(F)::value>(u, Ja, r, n_elem, tab, err, stream);         \
-        });
-    switch (n) {
-        SFH_DCASE(2) SFH_DCASE(3) SFH_DCASE(4) SFH_DCASE(5) SFH_DCASE(6) SFH_DCASE(7) SFH_DCASE(8) SFH_DCASE(9)
-        default: return cudaErrorInvalidValue;
-    }
-#undef SFH_DCASE
-#endif
-#if defined(SFH_INST_MIXED)
 #define SFH_CASE(N)                                                                                    \
-    case N:                                                                                             \
-        return pick_flux(flux, [&](auto F) {                                                            \
-            return launch_volume<D, N, decltype(F)::value, Mode>(u, Ja, r, n_elem, tab, err, stream);  \
-        });
+    case N:                                                                                            \
+        return pick_flux(flux, [&](auto F) { return SFH_VCALL(N, decltype(F)::value); });
     switch (n) {
         SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
         default: return cudaErrorInvalidValue;
     }
 #undef SFH_CASE
-#endif
+#undef SFH_VCALL
 }
+#endif
 
 #endif
 

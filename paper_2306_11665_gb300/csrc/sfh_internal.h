@@ -29,6 +29,41 @@ SFH_DECL_VOLUME(volume_mixed_d2_ch, float)
 SFH_DECL_VOLUME(volume_mixed_d3_ch, float)
 #undef SFH_DECL_VOLUME
 
+// Modal entry points (basis coefficients in, V^T r_v out).
+#define SFH_DECL_MODAL(name, T)                                                                    \
+    cudaError_t name(int n, int flux, const void *u, const double *Ja, void *r, int64_t n_elem,     \
+                     const OpTab<T> &tab, const BasisTab<T> &bt, int *err, cudaStream_t stream);
+SFH_DECL_MODAL(volume_fp64_d2_modal, double)
+SFH_DECL_MODAL(volume_fp64_d3_modal, double)
+SFH_DECL_MODAL(volume_fp32k_d2_modal, float)
+SFH_DECL_MODAL(volume_fp32k_d3_modal, float)
+SFH_DECL_MODAL(volume_mixed_d2_modal, float)
+SFH_DECL_MODAL(volume_mixed_d3_modal, float)
+SFH_DECL_MODAL(volume_fp64_d2_ch_modal, double)
+SFH_DECL_MODAL(volume_fp64_d3_ch_modal, double)
+SFH_DECL_MODAL(volume_fp32k_d2_ch_modal, float)
+SFH_DECL_MODAL(volume_fp32k_d3_ch_modal, float)
+SFH_DECL_MODAL(volume_mixed_d2_ch_modal, float)
+SFH_DECL_MODAL(volume_mixed_d3_ch_modal, float)
+#undef SFH_DECL_MODAL
+
+using ModalFn64 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<double> &,
+                                  const BasisTab<double> &, int *, cudaStream_t);
+using ModalFn32 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<float> &,
+                                  const BasisTab<float> &, int *, cudaStream_t);
+inline ModalFn64 modal_fp64_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_fp64_d3_ch_modal : volume_fp64_d2_ch_modal;
+    return d == 3 ? volume_fp64_d3_modal : volume_fp64_d2_modal;
+}
+inline ModalFn32 modal_fp32k_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_fp32k_d3_ch_modal : volume_fp32k_d2_ch_modal;
+    return d == 3 ? volume_fp32k_d3_modal : volume_fp32k_d2_modal;
+}
+inline ModalFn32 modal_mixed_fn(int d, int flux) {
+    if (flux == kFluxEulerCh) return d == 3 ? volume_mixed_d3_ch_modal : volume_mixed_d2_ch_modal;
+    return d == 3 ? volume_mixed_d3_modal : volume_mixed_d2_modal;
+}
+
 // The instantiation unit's entry point for a (d, flux).
 using VolumeFn64 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<double> &,
                                    int *, cudaStream_t);

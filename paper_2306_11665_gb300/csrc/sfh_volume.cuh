@@ -181,11 +181,15 @@ __device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, t
 // the whole CTA (any blockDim; every thread must call it).  smem_raw holds
 // Shape::SMEM bytes.  Used by volume_kernel (one tile per CTA) and by the
 // persistent serving kernel (tiles of many requests).
-template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
+// MODAL: u holds basis coefficients (bt the basis on the cubature nodes); the
+// nodal values V u_hat are formed in shared memory before the node pass and
+// r receives V^T r_v (the residual and primitive buffers serve as scratch).
+template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>, bool MODAL = false>
 __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
                                             typename M::T *__restrict__ r, int64_t e0, int ne,
                                             const OpTab<typename M::T> &tab, int *__restrict__ err,
-                                            unsigned char *smem_raw) {
+                                            unsigned char *smem_raw,
+                                            const BasisTab<typename M::T> *bt = nullptr) {
     using T = typename M::T;
     using TJ = typename M::TJ;
     using Acc = typename AccOf<M>::type;
@@ -202,8 +206,25 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     T *sR = sP + EPB * NP * NN;
 
     const T *ub = u + e0 * NVAR * NN;
+    if constexpr (MODAL) {
+        // nodal values u_v = V u_hat, ending in sR ([el][var][i])
+        if constexpr (D == 3) {
+            basis_pass<T, D, N, false>(ub, sR, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, false>(sR, sP, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, false>(sP, sR, 2, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+        } else {
+            basis_pass<T, D, N, false>(ub, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, false>(sP, sR, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+        }
+        __syncthreads();
+        ub = sR;
+    }
 
-    // ---- 1. stage primitives, zero the residual
+    // ---- 1. stage primitives, zero the residual (each node's thread reads
+    //      its state before zeroing the same slots, also when it sits in sR)
     bool bad = false;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
@@ -400,9 +421,24 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     }
     __syncthreads();
 
-    // ---- 3. write r (layout [el][v][i] matches the global layout)
+    // ---- 3. write r (layout [el][v][i] matches the global layout); modal:
+    //      r_hat = V^T r_v
     T *rb = r + e0 * NVAR * NN;
-    for (int s = threadIdx.x; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
+    if constexpr (MODAL) {
+        if constexpr (D == 3) {
+            basis_pass<T, D, N, true>(sR, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, true>(sP, sR, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, true>(sR, rb, 2, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+        } else {
+            basis_pass<T, D, N, true>(sR, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            __syncthreads();
+            basis_pass<T, D, N, true>(sP, rb, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+        }
+    } else {
+        for (int s = threadIdx.x; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
+    }
 }
 
 template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
@@ -414,6 +450,34 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
     volume_tile<D, N, FLUX, M, S>(u, Ja, r, e0, ne, tab, err, smem_raw);
+}
+
+template <int D, int N, int FLUX, class M, class S>
+__global__ void __launch_bounds__(S::THREADS)
+volume_modal_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
+                    typename M::T *__restrict__ r, int64_t n_elem,
+                    const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err,
+                    const __grid_constant__ BasisTab<typename M::T> bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
+    const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
+    volume_tile<D, N, FLUX, M, S, true>(u, Ja, r, e0, ne, tab, err, smem_raw, &bt);
+}
+
+template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
+cudaError_t launch_volume_modal(const void *u, const double *Ja, void *r, int64_t n_elem,
+                                const OpTab<typename M::T> &tab, const BasisTab<typename M::T> &bt, int *err,
+                                cudaStream_t stream) {
+    auto kern = volume_modal_kernel<D, N, FLUX, M, S>;
+    static_assert(S::SMEM <= 227 * 1024, "shared memory");
+    if (S::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (n_elem + S::EPB - 1) / S::EPB;
+    kern<<<(unsigned)blocks, S::THREADS, S::SMEM, stream>>>(
+        static_cast<const typename M::T *>(u), Ja, static_cast<typename M::T *>(r), n_elem, tab, err, bt);
+    return cudaGetLastError();
 }
 
 // Host-side launcher for one (D, N, FLUX, mode) instance and tile shape.

@@ -467,11 +467,14 @@ __device__ __forceinline__ void fp32_block_store(const float *sR, float *gR, int
     }
 }
 
-template <int D, int N, int FLUX>
-__global__ void __launch_bounds__(TmaShape<D, N, FLUX>::THREADS) __maxnreg__((TmaShape<D, N, FLUX>::MAXREG))
-volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ Ja, float *__restrict__ r,
-                       int64_t n_elem, const __grid_constant__ OpTab<float> tab, int *__restrict__ err,
-                       int aligned_bases) {
+// The persistent kernel's body.  MODAL: u holds basis coefficients and r
+// receives V^T r_v; the transforms run in shared memory (the directions'
+// residual slices serve as scratch), so HBM traffic is that of the nodal
+// residual.
+template <int D, int N, int FLUX, bool MODAL>
+__device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const double *__restrict__ Ja,
+                                              float *__restrict__ r, int64_t n_elem, const OpTab<float> &tab,
+                                              int *__restrict__ err, int aligned_bases, const BasisTab<float> *bt) {
     using S = TmaShape<D, N, FLUX>;
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, NJ = S::NJ, EPB = S::EPB;
     constexpr int U_EL = S::U_EL, J_EL = S::J_EL;
@@ -525,9 +528,22 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
             return;
         }
 
-        // ---- 2. primitives and FP32 metrics
-        const bool bad = fp32_block_convert<S, D, N, FLUX>(rawU + cur.offU, rawJ + cur.offJ, ne, sP, sJF, tid,
-                                                           S::THREADS);
+        // ---- 2. (modal: nodal values u_v = V u_hat into the last residual
+        //      slice) primitives and FP32 metrics
+        const float *uin = rawU + cur.offU;
+        if constexpr (MODAL) {
+            float *s0 = sR, *s1 = sR + EPB * U_EL, *s2 = sR + 2 * EPB * U_EL;
+            basis_pass<float, D, N, false>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
+            __syncthreads();
+            basis_pass<float, D, N, false>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS);
+            __syncthreads();
+            if constexpr (D == 3) {
+                basis_pass<float, D, N, false>(s1, s2, 2, ne * NVAR, *bt, tid, S::THREADS);
+                __syncthreads();
+            }
+            uin = D == 3 ? s2 : s1;
+        }
+        const bool bad = fp32_block_convert<S, D, N, FLUX>(uin, rawJ + cur.offJ, ne, sP, sJF, tid, S::THREADS);
         if (bad) atomicOr(err, kErrDomain);
         __syncthreads();
 
@@ -546,29 +562,74 @@ volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ J
         fp32_block_sweep<S, D, N, FLUX>(tid, ne, sP, sJF, sR, tab);
         __syncthreads();
 
-        // ---- 5. sum the directions in a fixed order and store r
-        fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, S::THREADS);
+        // ---- 5. sum the directions in a fixed order and store r (modal:
+        //      r_v into slice 0, then r_hat = V^T r_v pass by pass)
+        if constexpr (MODAL) {
+            float *s0 = sR, *s1 = sR + EPB * U_EL, *s2 = sR + 2 * EPB * U_EL;
+            fp32_block_store<S, D>(sR, s0, ne, tid, S::THREADS);
+            __syncthreads();
+            float *gR = r + cur.e0 * U_EL;
+            if constexpr (D == 3) {
+                basis_pass<float, D, N, true>(s0, s1, 0, ne * NVAR, *bt, tid, S::THREADS);
+                __syncthreads();
+                basis_pass<float, D, N, true>(s1, s2, 1, ne * NVAR, *bt, tid, S::THREADS);
+                __syncthreads();
+                basis_pass<float, D, N, true>(s2, gR, 2, ne * NVAR, *bt, tid, S::THREADS);
+            } else {
+                basis_pass<float, D, N, true>(s0, s1, 0, ne * NVAR, *bt, tid, S::THREADS);
+                __syncthreads();
+                basis_pass<float, D, N, true>(s1, gR, 1, ne * NVAR, *bt, tid, S::THREADS);
+            }
+        } else {
+            fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, S::THREADS);
+        }
         cur = nx;
     }
 }
 
-// grid: one resident CTA per SM slot (persistent); occupancy is queried once
 template <int D, int N, int FLUX>
+__global__ void __launch_bounds__(TmaShape<D, N, FLUX>::THREADS) __maxnreg__((TmaShape<D, N, FLUX>::MAXREG))
+volume_fp32_tma_kernel(const float *__restrict__ u, const double *__restrict__ Ja, float *__restrict__ r,
+                       int64_t n_elem, const __grid_constant__ OpTab<float> tab, int *__restrict__ err,
+                       int aligned_bases) {
+    fp32_tma_body<D, N, FLUX, false>(u, Ja, r, n_elem, tab, err, aligned_bases, nullptr);
+}
+
+template <int D, int N, int FLUX>
+__global__ void __launch_bounds__(TmaShape<D, N, FLUX>::THREADS) __maxnreg__((TmaShape<D, N, FLUX>::MAXREG))
+volume_fp32_tma_modal_kernel(const float *__restrict__ u, const double *__restrict__ Ja, float *__restrict__ r,
+                             int64_t n_elem, const __grid_constant__ OpTab<float> tab, int *__restrict__ err,
+                             int aligned_bases, const __grid_constant__ BasisTab<float> bt) {
+    fp32_tma_body<D, N, FLUX, true>(u, Ja, r, n_elem, tab, err, aligned_bases, &bt);
+}
+
+// grid: one resident CTA per SM slot (persistent); occupancy is queried once
+// per device.  bt != nullptr selects the modal kernel.
+template <int D, int N, int FLUX, bool MODAL = false>
 cudaError_t launch_volume_fp32_tma(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab,
-                                   int *err, cudaStream_t stream) {
+                                   int *err, cudaStream_t stream, const BasisTab<float> *bt = nullptr) {
     using S = TmaShape<D, N, FLUX>;
-    auto kern = volume_fp32_tma_kernel<D, N, FLUX>;
     static_assert(S::SMEM <= 227 * 1024, "shared memory");
     static int cache_per_sm[kMaxDevices], cache_sms[kMaxDevices];
     int per_sm = 0, sms = 0;
-    const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
-    if (e0 != cudaSuccess) return e0;
-    const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
-    const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
     const int aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(Ja) |
                           reinterpret_cast<uintptr_t>(r)) & 15) == 0;
-    kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja, static_cast<float *>(r),
-                                                         n_elem, tab, err, aligned);
+    const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
+    if constexpr (MODAL) {
+        auto kern = volume_fp32_tma_modal_kernel<D, N, FLUX>;
+        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
+        if (e0 != cudaSuccess) return e0;
+        const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
+        kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja,
+                                                             static_cast<float *>(r), n_elem, tab, err, aligned, *bt);
+    } else {
+        auto kern = volume_fp32_tma_kernel<D, N, FLUX>;
+        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
+        if (e0 != cudaSuccess) return e0;
+        const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
+        kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja,
+                                                             static_cast<float *>(r), n_elem, tab, err, aligned);
+    }
     return cudaGetLastError();
 }
 

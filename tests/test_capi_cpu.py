@@ -70,3 +70,18 @@ def test_no_device_is_reported_not_crashed(A):
         with pytest.raises(A.SfhError) as e:
             A.sfh_create(3, 4, 0, 5, flux)
         assert e.value.status in (A.SFH_EUNSUPPORTED, A.SFH_ECUDA)
+
+
+def test_basis_table_matches_the_oracle(A):
+    """The library's modal basis tables (host code, no device) against the
+    oracle's: orthonormal Legendre and the two Lagrange bases on both
+    cubature node sets."""
+    import oracle as O
+    for p in (1, 4, 8):
+        for kind in (0, 1):
+            for basis in (A.SFH_BASIS_LEGENDRE, A.SFH_BASIS_LAGRANGE_GLL, A.SFH_BASIS_LAGRANGE_GAUSS):
+                V = A.sfh_basis_table(p, kind, basis)
+                assert np.abs(V - O.basis_1d(p, kind, basis)).max() <= 1e-14, (p, kind, basis)
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_basis_table(4, 0, 3)
+    assert e.value.status == A.SFH_EINVAL

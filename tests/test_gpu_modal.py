@@ -1,0 +1,163 @@
+"""GPU parity of the modal / uncollocated entry point
+(sfh_volume_residual_modal: r_hat = V^T r_v(V u_hat), transforms fused into
+the residual kernels) against the oracle's modal path (dense Kronecker
+transforms, literal entropy projection).
+
+Bars: FP64 1e-12 per variable; FP32 modes 2e-5 in the global relative max
+norm and, per variable, max(2e-5, 6 x the input-rounding floor, 2.5 u32
+kappa_v) with kappa_v the cancellation ratio of the modal residual,
+max_k sum_i |V_ik| S_v,i / max_k |r_hat_k,v|, S_v,i = sum_{m,j} |Q_m,ij F_m,ij,v|
+(the sums the residual and its transform cancel)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2306_11665_gb300 import _abi as A
+from paper_2306_11665_gb300 import api
+from paper_2306_11665_gb300 import inputs as I
+from tests._entropy import kron_q
+from tests._helpers import fp32_check, rel_err_per_var
+
+pytestmark = pytest.mark.gpu
+
+LEG, LGLL, LGAUSS = I.BASIS_LEGENDRE, I.BASIS_LAGRANGE_GLL, I.BASIS_LAGRANGE_GAUSS
+FLUX = {"euler": O.FLUX_EULER, "euler_chandrashekar": O.FLUX_CHANDRASHEKAR, "burgers": O.FLUX_BURGERS}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2306_11665_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+
+
+def run_modal(ctx, uhat, Ja, basis, prec):
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ut = torch.from_numpy(np.ascontiguousarray(uhat, dtype=np.float64)).to(dt).cuda()
+    r = ctx.volume_residual_modal(ut, torch.from_numpy(Ja).cuda(), basis, prec)
+    return r.double().cpu().numpy(), ctx.check()
+
+
+def kappa_modal(d, p, kind, basis, flux, uhat, Ja, rhat, n_el=3):
+    E = min(uhat.shape[0], n_el)
+    _, up = O.modal_states(d, p, kind, basis, flux, uhat[:E])
+    V1 = O.basis_1d(p, kind, basis)
+    V = V1
+    for _ in range(d - 1):
+        V = np.kron(V1, V)
+    S = np.zeros(up.shape)
+    for e in range(E):
+        for m in range(d):
+            Q = kron_q(d, p, kind, m)
+            rows, cols = np.nonzero(Q)
+            for i, j in zip(rows, cols):
+                F = O.ec_flux(d, flux, up[e, :, i], up[e, :, j], Ja[e, m, :, i] + Ja[e, m, :, j])
+                S[e, :, i] += abs(Q[i, j]) * np.abs(F)
+    T = np.einsum("ik,evi->evk", np.abs(V), S)
+    return [T[:, v].max() / np.abs(rhat[:E, v]).max() for v in range(uhat.shape[1])]
+
+
+def check(d, p, kind, basis, flux_name, N=None, precs=("fp64", "fp32k", "fp32mix")):
+    fl = FLUX[flux_name]
+    N = N or (2 if (d == 3 and p >= 6) else 3)
+    uhat, Ja = I.modal_workload(d, p, kind, basis, N, flux="burgers" if fl == O.FLUX_BURGERS else "euler")
+    ref = O.volume_modal(d, p, kind, basis, fl, uhat, Ja)
+    ctx = api.Context(d, p, kind, flux_name)
+    out = {}
+    for prec in precs:
+        if prec == "fp64":
+            got, st = run_modal(ctx, uhat, Ja, basis, prec)
+            assert st == A.SFH_OK
+            out[prec] = rel_err_per_var(got, ref)
+            assert out[prec] <= 1e-12, (prec, out[prec])
+        else:
+            u32 = I.to_fp32(uhat)
+            ref_w = O.volume_modal(d, p, kind, basis, fl, u32.astype(np.float64), Ja)
+            got, st = run_modal(ctx, u32, Ja, basis, prec)
+            assert st == A.SFH_OK
+            out[prec] = fp32_check(got, ref, ref_w, lambda: kappa_modal(d, p, kind, basis, fl, uhat, Ja, ref))
+    return out
+
+
+@pytest.mark.parametrize("d", [2, 3])
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_legendre_euler_all_modes(d, kind, p):
+    check(d, p, kind, LEG, "euler")
+
+
+@pytest.mark.parametrize("d, kind, basis, p", [(3, 1, LGLL, 4), (3, 0, LGAUSS, 3), (2, 1, LGLL, 6),
+                                               (3, 1, LGLL, 7), (2, 0, LGAUSS, 8)])
+def test_uncollocated_lagrange_bases(d, kind, basis, p):
+    check(d, p, kind, basis, "euler")
+
+
+@pytest.mark.parametrize("d, kind, p", [(3, 0, 4), (3, 1, 7), (2, 1, 3)])
+def test_chandrashekar_and_burgers(d, kind, p):
+    check(d, p, kind, LEG, "euler_chandrashekar")
+    check(d, p, kind, LEG, "burgers")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32k"])
+@pytest.mark.parametrize("d, kind, p", [(3, 0, 4), (3, 1, 2), (2, 1, 5)])
+def test_collocated_basis_matches_the_nodal_entry_point(prec, d, kind, p):
+    """With the Lagrange basis of the cubature nodes V = I: the modal entry
+    point gives the nodal residual (FP32: bit for bit, same kernel and sums)."""
+    basis = LGLL if kind == 0 else LGAUSS
+    u, Ja = I.workload(d, p, kind, 3)
+    ctx = api.Context(d, p, kind, "euler")
+    src = u if prec == "fp64" else I.to_fp32(u)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    ut = torch.from_numpy(np.ascontiguousarray(src)).to(dt).cuda()
+    Jt = torch.from_numpy(Ja).cuda()
+    rn = ctx.volume_residual(ut, Jt, prec).double().cpu().numpy()
+    rm = ctx.volume_residual_modal(ut, Jt, basis, prec).double().cpu().numpy()
+    if prec == "fp32k":
+        assert np.array_equal(rn, rm)
+    else:
+        assert rel_err_per_var(rm, rn) <= 1e-12
+
+
+def test_full_size_p4_32cubed_sampled():
+    """3D Euler p = 4, Legendre coefficients on 32^3 warped elements with
+    Gauss-Lobatto cubature (the benchmark's shape), sampled elements
+    recomputed by the oracle."""
+    d, p, kind = 3, 4, 0
+    uhat, Ja = I.modal_workload(d, p, kind, LEG, 32)
+    E = uhat.shape[0]
+    rng = np.random.default_rng(51)
+    idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, size=48, replace=False)]))
+    ref = O.volume_modal(d, p, kind, LEG, O.FLUX_EULER, uhat[idx], Ja[idx])
+    ref_w = O.volume_modal(d, p, kind, LEG, O.FLUX_EULER, I.to_fp32(uhat[idx]).astype(np.float64), Ja[idx])
+    ctx = api.Context(d, p, kind, "euler")
+    for prec in ("fp64", "fp32k", "fp32mix"):
+        got, st = run_modal(ctx, uhat if prec == "fp64" else I.to_fp32(uhat), Ja, LEG, prec)
+        assert st == A.SFH_OK
+        if prec == "fp64":
+            assert rel_err_per_var(got[idx], ref) <= 1e-12
+        else:
+            fp32_check(got[idx], ref, ref_w,
+                       lambda: kappa_modal(d, p, kind, LEG, O.FLUX_EULER, uhat[idx], Ja[idx], ref))
+
+
+def test_errors_and_domain():
+    uhat, Ja = I.modal_workload(3, 3, 1, LEG, 2)
+    ctx = api.Context(3, 3, 1, "euler")
+    ut, Jt = torch.from_numpy(uhat).cuda(), torch.from_numpy(Ja).cuda()
+    r = torch.empty_like(ut)
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual_modal(ctx.handle, 3, ut.shape[0], ut.data_ptr(), Jt.data_ptr(), r.data_ptr(), A.SFH_FP64)
+    assert e.value.status == A.SFH_EINVAL
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual_modal(ctx.handle, 0, ut.shape[0], ut.data_ptr(), Jt.data_ptr(), ut.data_ptr(), A.SFH_FP64)
+    assert e.value.status == A.SFH_EINVAL
+    bad = uhat.copy()
+    bad[1, 0, 0] = -bad[1, 0, 0]          # negative mean density in element 1
+    for prec in ("fp64", "fp32k", "fp32mix"):
+        _, st = run_modal(ctx, bad if prec == "fp64" else I.to_fp32(bad), Ja, LEG, prec)
+        assert st == A.SFH_EDOMAIN, prec
+        assert ctx.check() == A.SFH_OK     # the error word is cleared by the read
+    # empty input is a no-op
+    A.sfh_volume_residual_modal(ctx.handle, 0, 0, ut.data_ptr(), Jt.data_ptr(), r.data_ptr(), A.SFH_FP64)
+
