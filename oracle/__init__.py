@@ -70,7 +70,7 @@ def _load():
         lib.orc_fig1_sf.argtypes = [i, dp, dp]
         lib.orc_basis_1d.argtypes = [i, i, i, dp]
         lib.orc_modal_states.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
-        lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
+        lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, i, L, dp, dp, dp]
         lib.orc_entropy_vars.argtypes = [i, i, dp, dp]
         lib.orc_entropy_state.argtypes = [i, i, dp, dp]
         _lib = lib
@@ -227,15 +227,15 @@ def modal_states(d, p, kind, basis, flux, uhat, allow_domain=False):
     return uv, up
 
 
-def volume_modal(d, p, kind, basis, flux, uhat, Ja, allow_domain=False) -> np.ndarray:
+def volume_modal(d, p, kind, basis, flux, uhat, Ja, allow_domain=False, project=True) -> np.ndarray:
     """Modal volume residual r_hat = V^T r_v(u~) (dense transforms, literal
-    entropy projection)."""
+    entropy projection; project=False evaluates the flux at u_v = V u_hat)."""
     uhat, Ja = _f64(uhat), _f64(Ja)
     nvar = nvar_of(d, flux)
     assert uhat.shape[1:] == (nvar, (p + 1) ** d) and Ja.shape[0] == uhat.shape[0]
     r = np.zeros_like(uhat)
-    _check(_load().orc_volume_modal(d, p, kind, basis, nvar, flux, uhat.shape[0], _p(uhat), _p(Ja), _p(r)),
-           allow_domain)
+    _check(_load().orc_volume_modal(d, p, kind, basis, nvar, flux, int(bool(project)), uhat.shape[0], _p(uhat),
+                                    _p(Ja), _p(r)), allow_domain)
     return r
 
 

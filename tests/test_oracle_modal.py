@@ -164,3 +164,18 @@ def test_modal_entropy_identity(d, kind, basis):
         lhs, rhs = np.sum(what * rhat[e]), np.sum(w * rv[e])
         assert abs(lhs - rhs) <= 1e-11 * np.sum(np.abs(w * rv[e]))
         assert identity_residual(d, p, kind, O.FLUX_EULER, up[e], Ja[e], rv[e]) <= 1e-12
+
+
+@pytest.mark.parametrize("d, kind, basis", [(3, 1, LEG), (3, 0, LGLL), (2, 1, LEG)])
+def test_projection_round_off_in_the_residual(d, kind, basis):
+    """Skipping the projection changes r_hat only by its round-off amplified by
+    the residual's cancellation: within 1e-11 relative per variable, while
+    an actual change of the state (1e-8 relative) moves it by far more."""
+    p = 4
+    uhat, Ja = I.modal_workload(d, p, kind, basis, 2)
+    a = O.volume_modal(d, p, kind, basis, O.FLUX_EULER, uhat, Ja)
+    b = O.volume_modal(d, p, kind, basis, O.FLUX_EULER, uhat, Ja, project=False)
+    den = np.abs(a).max(axis=(0, 2))
+    assert np.all(np.abs(a - b).max(axis=(0, 2)) <= 1e-11 * den)
+    c = O.volume_modal(d, p, kind, basis, O.FLUX_EULER, uhat * (1 + 1e-8 * np.cos(np.arange(uhat.size)).reshape(uhat.shape)), Ja)
+    assert np.abs(a - c).max() >= 1e-9 * np.abs(a).max()
