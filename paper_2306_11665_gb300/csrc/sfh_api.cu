@@ -317,6 +317,12 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
             c->basis_d[b].V[k] = (double)VV[k];
             c->basis_f[b].V[k] = (float)VV[k];
         }
+        // chi_0 of the orthonormal Legendre basis is the constant 2^(-1/2)
+        const bool cm = b == SFH_BASIS_LEGENDRE;
+        const long double c0 = powl(2.0L, -0.5L * d);
+        c->basis_d[b].const_mode = c->basis_f[b].const_mode = cm ? 1 : 0;
+        c->basis_d[b].c0 = cm ? (double)c0 : 0.0;
+        c->basis_f[b].c0 = cm ? (float)c0 : 0.0f;
     }
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) {

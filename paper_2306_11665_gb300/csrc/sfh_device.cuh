@@ -33,20 +33,32 @@ struct OpTab {
 
 // 1D basis of a modal / uncollocated solution on the cubature nodes:
 // V[a*n + k] = chi_k(xi_a) (node a, basis function k), a kernel parameter.
+// const_mode: chi_0 is the constant c0^(1/d) (orthonormal Legendre): the
+// forward transform then takes the element's constant part c = u_hat_0 c0
+// out of the sums and adds it back at the end, so that the rounding of the
+// sums scales with the (small) non-constant part of the state.
 template <typename T>
 struct BasisTab {
     T V[NMAX * NMAX];
+    T c0;             // chi_0^d (const_mode only)
+    int const_mode;
 };
+
+// Role of a forward pass in the constant-part split (const_mode bases).
+constexpr int kPassPlain = 0, kPassFirst = 1, kPassLast = 2;
 
 // One pass of the sum-factorized basis transform (Section 2, the theorem on
 // uncollocated bases): along direction m, every line of every
 // element-variable q < nq (layout [q][i], NN values each) is multiplied by V
 // (node values from coefficients) or, TRANSPOSE, by V^T (tests against chi).
 // A thread per (q, line); the line's n inputs in registers, the table indices
-// compile-time constants.
-template <typename T, int D, int N, bool TRANSPOSE, typename TI, typename TO>
+// compile-time constants.  ROLE (forward, const_mode): kPassFirst drops the
+// constant coefficient u_hat_0 (read from `coef`, the pass-0 input), kPassLast
+// adds c = u_hat_0 c0 to every output.
+template <typename T, int D, int N, bool TRANSPOSE, int ROLE = kPassPlain, typename TI, typename TO,
+          typename TC = TI>
 __device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq, const BasisTab<T> &bt, int tid,
-                                           int nthreads) {
+                                           int nthreads, const TC *coef = nullptr) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
     for (int t = tid; t < nq * NLINE; t += nthreads) {
@@ -59,11 +71,19 @@ __device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq,
         T x[N];
 #pragma unroll
         for (int b = 0; b < N; ++b) x[b] = (T)src[b * stride];
+        if constexpr (ROLE == kPassFirst) {
+            if (bt.const_mode && base == 0) x[0] = (T)0;   // coefficient (0, .., 0) sits on line 0, b = 0
+        }
+        T c = (T)0;
+        if constexpr (ROLE == kPassLast) {
+            if (bt.const_mode) c = (T)coef[(size_t)q * NN] * bt.c0;
+        }
 #pragma unroll
         for (int a = 0; a < N; ++a) {
             T s = (T)0;
 #pragma unroll
             for (int b = 0; b < N; ++b) s = fma(TRANSPOSE ? bt.V[b * N + a] : bt.V[a * N + b], x[b], s);
+            if constexpr (ROLE == kPassLast) s += c;
             dst[a * stride] = (TO)s;
         }
     }

@@ -209,15 +209,15 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     if constexpr (MODAL) {
         // nodal values u_v = V u_hat, ending in sR ([el][var][i])
         if constexpr (D == 3) {
-            basis_pass<T, D, N, false>(ub, sR, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            basis_pass<T, D, N, false, kPassFirst>(ub, sR, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
             __syncthreads();
             basis_pass<T, D, N, false>(sR, sP, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
             __syncthreads();
-            basis_pass<T, D, N, false>(sP, sR, 2, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            basis_pass<T, D, N, false, kPassLast>(sP, sR, 2, ne * NVAR, *bt, threadIdx.x, blockDim.x, ub);
         } else {
-            basis_pass<T, D, N, false>(ub, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            basis_pass<T, D, N, false, kPassFirst>(ub, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
             __syncthreads();
-            basis_pass<T, D, N, false>(sP, sR, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x);
+            basis_pass<T, D, N, false, kPassLast>(sP, sR, 1, ne * NVAR, *bt, threadIdx.x, blockDim.x, ub);
         }
         __syncthreads();
         ub = sR;

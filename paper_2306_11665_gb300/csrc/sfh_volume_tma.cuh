@@ -533,14 +533,16 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
         const float *uin = rawU + cur.offU;
         if constexpr (MODAL) {
             float *s0 = sR, *s1 = sR + EPB * U_EL, *s2 = sR + 2 * EPB * U_EL;
-            basis_pass<float, D, N, false>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
-            __syncthreads();
-            basis_pass<float, D, N, false>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS);
+            basis_pass<float, D, N, false, kPassFirst>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
             __syncthreads();
             if constexpr (D == 3) {
-                basis_pass<float, D, N, false>(s1, s2, 2, ne * NVAR, *bt, tid, S::THREADS);
+                basis_pass<float, D, N, false>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS);
                 __syncthreads();
+                basis_pass<float, D, N, false, kPassLast>(s1, s2, 2, ne * NVAR, *bt, tid, S::THREADS, uin);
+            } else {
+                basis_pass<float, D, N, false, kPassLast>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS, uin);
             }
+            __syncthreads();
             uin = D == 3 ? s2 : s1;
         }
         const bool bad = fp32_block_convert<S, D, N, FLUX>(uin, rawJ + cur.offJ, ne, sP, sJF, tid, S::THREADS);
