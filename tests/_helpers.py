@@ -43,9 +43,9 @@ def rel_err_vars(got, ref):
                      for v in range(ref.shape[1])])
 
 
-def fp32_check(got, ref, ref_w, kappa_fn=None):
-    """The FP32 bars.  (1) 2e-5 in the relative max norm of the residual
-    vector.  (2) Per variable, the largest of
+def fp32_check(got, ref, ref_w, kappa_fn=None, global_bar=2e-5):
+    """The FP32 bars.  (1) 2e-5 (global_bar) in the relative max norm of the
+    residual vector (callers with a derived global bar check it themselves).  (2) Per variable, the largest of
       2e-5;
       6 x that variable's input-rounding floor (ref_w = oracle on the
         FP32-rounded state): FP32 arithmetic moves each node's primitives and
@@ -61,7 +61,7 @@ def fp32_check(got, ref, ref_w, kappa_fn=None):
     bar = np.maximum(2e-5, 6.0 * floor)
     if np.any(pv > bar) and kappa_fn is not None:
         bar = np.maximum(bar, 2.5 * 2.0 ** -24 * np.asarray(kappa_fn()))
-    assert g <= 2e-5, ("global", g)
+    assert g <= global_bar, ("global", g)
     assert np.all(pv <= bar), ("per-variable", pv, bar)
     return {"global": float(g), "per_variable": pv.tolist(), "input_floor": floor.tolist(), "bar": bar.tolist()}
 
