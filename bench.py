@@ -658,6 +658,24 @@ def main():
         ch["vjp_fp64"] = {"element_dof_per_s": dof / (tchv * 1e-3), "ms": tchv}
         assert cch.check() == A.SFH_OK
         variants["chandrashekar"] = ch
+
+        # modal / uncollocated path: orthonormal Legendre coefficients on the
+        # same mesh, transforms fused into the residual kernels
+        uh = I.legendre_coefficients(d, p, E)
+        th64 = torch.from_numpy(uh).to(dev)
+        th32 = th64.float()
+        md = {"basis": "legendre"}
+        for name, prec, src, out, t_nodal in (("fp32k", A.SFH_FP32_KAHAN, th32, r32, t32),
+                                              ("fp64", A.SFH_FP64, th64, r64, t64),
+                                              ("fp32mix", A.SFH_FP32_MIXED, th32, r32, tmix)):
+            def stepm(prec=prec, src=src, out=out):
+                A.sfh_volume_residual_modal(ctx.handle, A.SFH_BASIS_LEGENDRE, E, src.data_ptr(), tJ.data_ptr(),
+                                            out.data_ptr(), prec, sh)
+            _, tm = timed_launches(stepm, k64, 2, stream, torch)
+            md[name] = {"element_dof_per_s": dof / (tm * 1e-3), "ms": tm, "over_nodal": tm / t_nodal}
+        assert ctx.check() == A.SFH_OK
+        variants["modal"] = md
+        del th64, th32
         variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
         variants["fig1_gpu"] = fig1_gpu(torch, A, stream)
         if not args.no_serve:

@@ -211,7 +211,12 @@ def modal_workload(d: int, p: int, kind: int, basis: int, N: int, flux: str = "e
         return uhat, Ja
     if basis != BASIS_LEGENDRE:
         raise ValueError(f"unknown basis {basis}")
-    n, E = p + 1, Ja.shape[0]
+    return legendre_coefficients(d, p, Ja.shape[0], flux, seed), Ja
+
+
+def legendre_coefficients(d: int, p: int, E: int, flux: str = "euler", seed: int = 12) -> np.ndarray:
+    """u_hat[e][var][k] of the orthonormal Legendre recipe (module docstring)."""
+    n = p + 1
     nn = n ** d
     if flux == "burgers":
         mean = np.array([0.5])
@@ -228,4 +233,4 @@ def modal_workload(d: int, p: int, kind: int, basis: int, N: int, flux: str = "e
     rng = np.random.Generator(np.random.PCG64(seed))
     uhat = 0.04 * rng.standard_normal((E, mean.size, nn)) / (1.0 + kk) ** 2
     uhat[:, :, 0] += mean * 2.0 ** (d / 2.0)
-    return np.ascontiguousarray(uhat), Ja
+    return np.ascontiguousarray(uhat)
