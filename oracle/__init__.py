@@ -71,6 +71,7 @@ def _load():
         lib.orc_basis_1d.argtypes = [i, i, i, dp]
         lib.orc_modal_states.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
         lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, i, L, dp, dp, dp]
+        lib.orc_vjp_modal.argtypes = [i, i, i, i, i, i, L, dp, dp, dp, dp]
         lib.orc_entropy_vars.argtypes = [i, i, dp, dp]
         lib.orc_entropy_state.argtypes = [i, i, dp, dp]
         _lib = lib
@@ -253,3 +254,13 @@ def entropy_state(d: int, flux: int, w) -> np.ndarray:
     u = np.zeros_like(w)
     _check(_load().orc_entropy_state(d, flux, _p(w), _p(u)))
     return u
+
+
+def vjp_modal(d, p, kind, basis, flux, uhat, Ja, lamhat) -> np.ndarray:
+    """g_hat = V^T (dr_v/du_v)^T V lambda_hat, the VJP of the modal residual."""
+    uhat, Ja, lamhat = _f64(uhat), _f64(Ja), _f64(lamhat)
+    assert lamhat.shape == uhat.shape
+    g = np.zeros_like(uhat)
+    _check(_load().orc_vjp_modal(d, p, kind, basis, nvar_of(d, flux), flux, uhat.shape[0], _p(uhat), _p(Ja),
+                                 _p(lamhat), _p(g)))
+    return g

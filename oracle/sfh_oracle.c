@@ -931,3 +931,47 @@ int orc_volume_modal(int d, int p, int kind, int basis, int nvar, int flux, int 
 /* Exported for the tests: entropy variables of one state and the inverse. */
 int orc_entropy_vars(int d, int flux, const double *u, double *w) { return entropy_w(d, flux, u, w); }
 int orc_entropy_state(int d, int flux, const double *w, double *u) { return entropy_u(d, flux, w, u); }
+
+/* VJP of the modal residual (Ja fixed): from r_hat = V^T r_v(V u_hat) (the
+ * projection being the identity map for square V, its derivative is the
+ * identity too), g_hat = V^T J_v^T V lambda_hat with J_v = dr_v/du_v at
+ * u_v = V u_hat: lambda_v = V lambda_hat, the nodal VJP, then V^T.  Dense
+ * Kronecker transforms. */
+int orc_vjp_modal(int d, int p, int kind, int basis, int nvar, int flux, long n_elem,
+                  const double *uhat, const double *Ja, const double *lamhat, double *ghat)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    size_t tot = (size_t)n_elem * nvar * nn;
+    double V1[256];
+    double *V = (double *)malloc(sizeof(double) * (size_t)nn * nn);
+    double *Wd = (double *)malloc(sizeof(double) * nn);
+    double *uv = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    double *lv = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    double *gv = (double *)malloc(sizeof(double) * (tot ? tot : 1));
+    if (!V || !Wd || !uv || !lv || !gv || orc_basis_1d(p, kind, basis, V1)) {
+        free(V); free(Wd); free(uv); free(lv); free(gv); return 1;
+    }
+    modal_dense(d, p, kind, V1, V, Wd);
+    for (long e = 0; e < n_elem; ++e)
+        for (int v = 0; v < nvar; ++v)
+            for (int i = 0; i < nn; ++i) {
+                double su = 0.0, sl = 0.0;
+                for (int k = 0; k < nn; ++k) {
+                    su += V[(size_t)i * nn + k] * uhat[(e * nvar + v) * nn + k];
+                    sl += V[(size_t)i * nn + k] * lamhat[(e * nvar + v) * nn + k];
+                }
+                uv[(e * nvar + v) * nn + i] = su;
+                lv[(e * nvar + v) * nn + i] = sl;
+            }
+    st = orc_vjp_sf(d, p, kind, nvar, flux, n_elem, uv, Ja, lv, gv);
+    for (long e = 0; e < n_elem; ++e)
+        for (int v = 0; v < nvar; ++v)
+            for (int k = 0; k < nn; ++k) {
+                double s = 0.0;
+                for (int i = 0; i < nn; ++i) s += V[(size_t)i * nn + k] * gv[(e * nvar + v) * nn + i];
+                ghat[(e * nvar + v) * nn + k] = s;
+            }
+    free(V); free(Wd); free(uv); free(lv); free(gv);
+    return st;
+}

@@ -179,3 +179,33 @@ def test_projection_round_off_in_the_residual(d, kind, basis):
     assert np.all(np.abs(a - b).max(axis=(0, 2)) <= 1e-11 * den)
     c = O.volume_modal(d, p, kind, basis, O.FLUX_EULER, uhat * (1 + 1e-8 * np.cos(np.arange(uhat.size)).reshape(uhat.shape)), Ja)
     assert np.abs(a - c).max() >= 1e-9 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("d, kind, basis, flux", [(3, 1, LEG, O.FLUX_EULER), (3, 0, LGAUSS, O.FLUX_EULER),
+                                                  (2, 1, LEG, O.FLUX_CHANDRASHEKAR), (2, 0, LEG, O.FLUX_BURGERS)])
+def test_modal_vjp_against_finite_differences(d, kind, basis, flux):
+    """g_hat . delta = d/dh lambda_hat . r_hat(u_hat + h delta) by central
+    differences of the modal residual (unprojected and projected alike)."""
+    p = 3
+    fl = "burgers" if flux == O.FLUX_BURGERS else "euler"
+    uhat, Ja = I.modal_workload(d, p, kind, basis, 2, flux=fl)
+    lam = I.cotangent(uhat.shape)
+    g = O.vjp_modal(d, p, kind, basis, flux, uhat, Ja, lam)
+    delta = np.random.default_rng(9).standard_normal(uhat.shape) * np.maximum(0.1, np.abs(uhat))
+    h = 1e-6
+    for project in (False, True):
+        rp = O.volume_modal(d, p, kind, basis, flux, uhat + h * delta, Ja, project=project)
+        rm = O.volume_modal(d, p, kind, basis, flux, uhat - h * delta, Ja, project=project)
+        fd = np.sum(lam * (rp - rm)) / (2 * h)
+        assert abs(np.sum(g * delta) - fd) <= 1e-6 * abs(fd), project
+    # per component on a sample
+    rng = np.random.default_rng(10)
+    for idx in rng.choice(uhat.size, size=12, replace=False):
+        e, v, k = np.unravel_index(idx, uhat.shape)
+        hh = 1e-6 * max(1.0, abs(uhat[e, v, k]))
+        up, um = uhat.copy(), uhat.copy()
+        up[e, v, k] += hh
+        um[e, v, k] -= hh
+        fd = np.sum(lam[e] * (O.volume_modal(d, p, kind, basis, flux, up[e:e + 1], Ja[e:e + 1], project=False)
+                              - O.volume_modal(d, p, kind, basis, flux, um[e:e + 1], Ja[e:e + 1], project=False))) / (2 * hh)
+        assert abs(g[e, v, k] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.abs(g).max())
