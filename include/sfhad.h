@@ -154,6 +154,17 @@ sfh_status sfh_basis_table(int p, sfh_nodes nodes, sfh_basis basis, double *V);
 sfh_status sfh_vjp(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *Ja,
                    const double *lambda, double *grad_u, sfh_stream_t stream);
 
+/* VJP of the modal residual (FP64), Ja fixed: with r_hat = V^T r_v(V u_hat)
+ * as in sfh_volume_residual_modal,
+ *   grad_hat = V^T (dr_v/du_v)^T V lambda_hat,   u_v = V u_hat,
+ * the nodal VJP of sfh_vjp between two sum-factorized transforms, all fused
+ * in one kernel.  u_hat, lambda_hat, grad_hat: device double
+ * [n_elem][nvar][n^d] (coefficients); Ja as above.  grad_hat is overwritten
+ * and must not overlap the inputs.  Asynchronous.  Errors as
+ * sfh_volume_residual_modal. */
+sfh_status sfh_vjp_modal(sfh_ctx *ctx, sfh_basis basis, int64_t n_elem, const double *u_hat, const double *Ja,
+                         const double *lambda_hat, double *grad_hat, sfh_stream_t stream);
+
 /* Entropy identity of the volume term (summation by parts, Tadmor's
  * condition for the symmetric entropy-conservative flux; general SBP form,
  * which for Gauss-Lobatto nodes is the element's boundary entropy flux):

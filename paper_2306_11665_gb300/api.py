@@ -79,6 +79,18 @@ class Context:
                                     pr, torch.cuda.current_stream(u_hat.device).cuda_stream)
         return r
 
+    def vjp_modal(self, u_hat: torch.Tensor, Ja: torch.Tensor, lam_hat: torch.Tensor, basis="legendre",
+                  out: torch.Tensor | None = None):
+        """V^T (dr_v/du_v)^T V lambda_hat (FP64), the VJP of volume_residual_modal."""
+        self._shape_check(u_hat, Ja, torch.float64)
+        if (lam_hat.shape != u_hat.shape or lam_hat.dtype != torch.float64 or not lam_hat.is_contiguous()
+                or not lam_hat.is_cuda):
+            raise ValueError("lambda_hat must be a contiguous float64 CUDA tensor shaped like u_hat")
+        g = torch.empty_like(u_hat) if out is None else out
+        A.sfh_vjp_modal(self.handle, _enum(BASIS, basis), u_hat.shape[0], u_hat.data_ptr(), Ja.data_ptr(),
+                        lam_hat.data_ptr(), g.data_ptr(), torch.cuda.current_stream(u_hat.device).cuda_stream)
+        return g
+
     def vjp(self, u: torch.Tensor, Ja: torch.Tensor, lam: torch.Tensor, out: torch.Tensor | None = None):
         """(dr/du)^T lambda (FP64) on the current stream."""
         self._shape_check(u, Ja, torch.float64)
@@ -134,3 +146,26 @@ class SFHVolume(torch.autograd.Function):
 def volume(u: torch.Tensor, Ja: torch.Tensor, context: Context) -> torch.Tensor:
     """Differentiable FP64 volume residual (autograd through sfh_vjp)."""
     return SFHVolume.apply(u, Ja, context)
+
+
+class SFHVolumeModal(torch.autograd.Function):
+    """r_hat = volume_residual_modal(u_hat; Ja, basis) with the modal adjoint
+    (sfh_vjp_modal) as backward.  FP64 only; Ja receives no gradient."""
+
+    @staticmethod
+    def forward(ctx_, u_hat, Ja, context: Context, basis):
+        u_hat = u_hat.contiguous()
+        ctx_.save_for_backward(u_hat, Ja)
+        ctx_.context, ctx_.basis = context, basis
+        return context.volume_residual_modal(u_hat, Ja, basis, "fp64")
+
+    @staticmethod
+    def backward(ctx_, grad_r):
+        u_hat, Ja = ctx_.saved_tensors
+        g = ctx_.context.vjp_modal(u_hat, Ja, grad_r.contiguous(), ctx_.basis)
+        return g, None, None, None
+
+
+def volume_modal(u_hat: torch.Tensor, Ja: torch.Tensor, context: Context, basis="legendre") -> torch.Tensor:
+    """Differentiable FP64 modal volume residual (autograd through sfh_vjp_modal)."""
+    return SFHVolumeModal.apply(u_hat, Ja, context, basis)

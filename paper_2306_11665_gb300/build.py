@@ -38,9 +38,8 @@ INST = [
 ]
 # Chandrashekar's flux in units of their own (entry points suffixed _ch)
 INST += [(name + "_ch", defs + ["-DSFH_INST_CH"]) for name, defs in list(INST)]
-# modal / uncollocated entry points (suffixed _modal): residual modes only
-INST += [(name + "_modal", defs + ["-DSFH_INST_MODAL"]) for name, defs in list(INST)
-         if "-DSFH_INST_VJP" not in defs]
+# modal / uncollocated entry points (suffixed _modal)
+INST += [(name + "_modal", defs + ["-DSFH_INST_MODAL"]) for name, defs in list(INST)]
 
 
 def nvcc() -> str:

@@ -462,6 +462,26 @@ extern "C" sfh_status sfh_volume_residual_modal(sfh_ctx *c, sfh_basis basis, int
     return SFH_OK;
 }
 
+extern "C" sfh_status sfh_vjp_modal(sfh_ctx *c, sfh_basis basis, int64_t n_elem, const double *u_hat,
+                                    const double *Ja, const double *lambda_hat, double *grad_hat,
+                                    sfh_stream_t stream) {
+    clear_err();
+    if (basis != SFH_BASIS_LEGENDRE && basis != SFH_BASIS_LAGRANGE_GLL && basis != SFH_BASIS_LAGRANGE_GAUSS)
+        return fail(SFH_EINVAL, "bad basis %d", (int)basis);
+    sfh_status st = check_common(c, n_elem, u_hat, Ja, grad_hat, sizeof(double));
+    if (st != SFH_OK || n_elem == 0) return st;
+    if (!lambda_hat) return fail(SFH_EINVAL, "lambda_hat is NULL");
+    if ((uintptr_t)lambda_hat % sizeof(double)) return fail(SFH_EINVAL, "misaligned lambda_hat");
+    const size_t ub = (size_t)(n_elem * c->nvar * sfh::ipow(c->n, c->d)) * sizeof(double);
+    if (overlap(grad_hat, ub, lambda_hat, ub)) return fail(SFH_EINVAL, "grad_hat overlaps lambda_hat");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    cudaError_t e = sfh::vjp_modal_fn(c->d, c->flux)(c->n, c->flux, u_hat, Ja, lambda_hat, grad_hat, n_elem,
+                                                    c->tab_d, c->basis_d[basis], c->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "modal vjp kernel launch");
+    return SFH_OK;
+}
+
 extern "C" sfh_status sfh_vjp(sfh_ctx *c, int64_t n_elem, const double *u, const double *Ja, const double *lambda,
                               double *grad_u, sfh_stream_t stream) {
     clear_err();

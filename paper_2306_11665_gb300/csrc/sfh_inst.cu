@@ -48,6 +48,17 @@ static cudaError_t pick_flux(int flux, Fn fn) {
 
 #if defined(SFH_INST_VJP)
 
+#if defined(SFH_INST_MODAL)
+cudaError_t SFH_NAME(vjp_d)(int n, int flux, const double *u, const double *Ja, const double *lam, double *g,
+                           int64_t n_elem, const OpTab<double> &tab, const BasisTab<double> &bt, int *err,
+                           cudaStream_t stream) {
+    constexpr int D = SFH_INST_D;
+#define SFH_CASE(N)                                                                                       \
+    case N:                                                                                               \
+        return pick_flux(flux, [&](auto F) {                                                              \
+            return launch_vjp_modal<D, N, decltype(F)::value>(u, Ja, lam, g, n_elem, tab, bt, err, stream); \
+        });
+#else
 cudaError_t SFH_NAME(vjp_d)(int n, int flux, const double *u, const double *Ja, const double *lam, double *g,
                            int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
@@ -56,6 +67,7 @@ cudaError_t SFH_NAME(vjp_d)(int n, int flux, const double *u, const double *Ja, 
         return pick_flux(flux, [&](auto F) {                                                         \
             return launch_vjp<D, N, decltype(F)::value>(u, Ja, lam, g, n_elem, tab, err, stream);  \
         });
+#endif
     switch (n) {
         SFH_CASE(2) SFH_CASE(3) SFH_CASE(4) SFH_CASE(5) SFH_CASE(6) SFH_CASE(7) SFH_CASE(8) SFH_CASE(9)
         default: return cudaErrorInvalidValue;

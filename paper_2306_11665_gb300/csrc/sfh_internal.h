@@ -100,6 +100,23 @@ SFH_DECL_VJP(vjp_d2_ch)
 SFH_DECL_VJP(vjp_d3_ch)
 #undef SFH_DECL_VJP
 
+#define SFH_DECL_VJP_MODAL(name)                                                                    \
+    cudaError_t name(int n, int flux, const double *u, const double *Ja, const double *lam, double *g, \
+                     int64_t n_elem, const OpTab<double> &tab, const BasisTab<double> &bt, int *err,   \
+                     cudaStream_t stream);
+SFH_DECL_VJP_MODAL(vjp_d2_modal)
+SFH_DECL_VJP_MODAL(vjp_d3_modal)
+SFH_DECL_VJP_MODAL(vjp_d2_ch_modal)
+SFH_DECL_VJP_MODAL(vjp_d3_ch_modal)
+#undef SFH_DECL_VJP_MODAL
+
+inline cudaError_t (*vjp_modal_fn(int d, int flux))(int, int, const double *, const double *, const double *,
+                                                    double *, int64_t, const OpTab<double> &,
+                                                    const BasisTab<double> &, int *, cudaStream_t) {
+    if (flux == kFluxEulerCh) return d == 3 ? vjp_d3_ch_modal : vjp_d2_ch_modal;
+    return d == 3 ? vjp_d3_modal : vjp_d2_modal;
+}
+
 inline cudaError_t (*vjp_fn(int d, int flux))(int, int, const double *, const double *, const double *, double *,
                                               int64_t, const OpTab<double> &, int *, cudaStream_t) {
     if (flux == kFluxEulerCh) return d == 3 ? vjp_d3_ch : vjp_d2_ch;

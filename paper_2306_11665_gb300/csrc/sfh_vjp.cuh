@@ -102,10 +102,15 @@ __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *P
 }
 
 // One tile of ne (<= EPB) elements from e0, processed by the whole CTA.
-template <int D, int N, int FLUX, class S = VjpShape<D, N, FLUX>>
+// MODAL: u and lambda hold basis coefficients (bt the basis on the cubature
+// nodes) and g receives V^T J^T V lambda_hat, the VJP of the modal residual
+// V^T r_v(V u_hat): the transforms run in shared memory (the primitive,
+// adjoint and lambda buffers serve as scratch).
+template <int D, int N, int FLUX, class S = VjpShape<D, N, FLUX>, bool MODAL = false>
 __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const double *__restrict__ Ja,
                                          const double *__restrict__ lam, double *__restrict__ g, int64_t e0, int ne,
-                                         const OpTab<double> &tab, int *__restrict__ err, unsigned char *smem_raw) {
+                                         const OpTab<double> &tab, int *__restrict__ err, unsigned char *smem_raw,
+                                         const BasisTab<double> *bt = nullptr) {
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
     double *sP = reinterpret_cast<double *>(smem_raw);   // [EPB][NP][NN]
     double *sA = sP + EPB * NP * NN;                       // [EPB][NP][NN] adjoints of primitives
@@ -114,6 +119,33 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
 
     const double *ub = u + e0 * NVAR * NN;
     const double *lb = lam + e0 * NVAR * NN;
+    if constexpr (MODAL) {
+        // lambda_v = V lambda_hat into sL, then u_v = V u_hat into sA ([el][var][i])
+        const int nq = ne * NVAR, t = threadIdx.x, nt = blockDim.x;
+        if constexpr (D == 3) {
+            basis_pass<double, D, N, false, kPassFirst>(lb, sL, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false>(sL, sP, 1, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassLast>(sP, sL, 2, nq, *bt, t, nt, lb);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassFirst>(ub, sA, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false>(sA, sP, 1, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassLast>(sP, sA, 2, nq, *bt, t, nt, ub);
+        } else {
+            basis_pass<double, D, N, false, kPassFirst>(lb, sP, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassLast>(sP, sL, 1, nq, *bt, t, nt, lb);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassFirst>(ub, sP, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, false, kPassLast>(sP, sA, 1, nq, *bt, t, nt, ub);
+        }
+        __syncthreads();
+        ub = sA;
+    }
 
     bool bad = false;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
@@ -140,12 +172,20 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         } else {
             pe[0] = ue[0];
         }
+        if constexpr (!MODAL) {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) sA[(el * NP + q) * NN + i] = 0.0;
+            for (int q = 0; q < NP; ++q) sA[(el * NP + q) * NN + i] = 0.0;
 #pragma unroll
-        for (int v = 0; v < NVAR; ++v) sL[(el * NVAR + v) * NN + i] = lb[((int64_t)el * NVAR + v) * NN + i];
+            for (int v = 0; v < NVAR; ++v) sL[(el * NVAR + v) * NN + i] = lb[((int64_t)el * NVAR + v) * NN + i];
+        }
     }
     if (bad) atomicOr(err, 1);
+    if constexpr (MODAL) {
+        // u_v sat in sA with the [el][var][i] layout: zero the adjoints only
+        // once every node has read its state
+        __syncthreads();
+        for (int s2 = threadIdx.x; s2 < ne * NP * NN; s2 += blockDim.x) sA[s2] = 0.0;
+    }
 
     const double *Jb = Ja + e0 * D * D * NN;
 #pragma unroll 1
@@ -217,13 +257,15 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
     }
     __syncthreads();
 
-    // ---- 3. primitive adjoints -> conservative adjoints; write g
+    // ---- 3. primitive adjoints -> conservative adjoints; write g (modal:
+    //      g_v into sL, then g_hat = V^T g_v)
     double *gbp = g + e0 * NVAR * NN;
+    double *gdst = MODAL ? sL : gbp;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
         const double *pe = sP + el * NP * NN + i;
         const double *ae = sA + el * NP * NN + i;
-        double *ge = gbp + (int64_t)el * NVAR * NN + i;
+        double *ge = gdst + (int64_t)el * NVAR * NN + i;
         if constexpr (is_euler(FLUX)) {
             const double rho = pe[0], p = pe[(D + 1) * NN], beta = pe[(D + 2) * NN];
             const double irho = rcp_nr(rho), ip = rcp_nr(p);
@@ -245,6 +287,47 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
             ge[0] = ae[0];
         }
     }
+    if constexpr (MODAL) {
+        const int nq = ne * NVAR, t = threadIdx.x, nt = blockDim.x;
+        __syncthreads();
+        if constexpr (D == 3) {
+            basis_pass<double, D, N, true>(sL, sP, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, true>(sP, sL, 1, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, true>(sL, gbp, 2, nq, *bt, t, nt);
+        } else {
+            basis_pass<double, D, N, true>(sL, sP, 0, nq, *bt, t, nt);
+            __syncthreads();
+            basis_pass<double, D, N, true>(sP, gbp, 1, nq, *bt, t, nt);
+        }
+    }
+}
+
+template <int D, int N, int FLUX, class S>
+__global__ void __launch_bounds__(S::THREADS)
+vjp_modal_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const double *__restrict__ lam,
+                 double *__restrict__ g, int64_t n_elem, const __grid_constant__ OpTab<double> tab,
+                 int *__restrict__ err, const __grid_constant__ BasisTab<double> bt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
+    const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
+    vjp_tile<D, N, FLUX, S, true>(u, Ja, lam, g, e0, ne, tab, err, smem_raw, &bt);
+}
+
+template <int D, int N, int FLUX>
+cudaError_t launch_vjp_modal(const double *u, const double *Ja, const double *lam, double *g, int64_t n_elem,
+                             const OpTab<double> &tab, const BasisTab<double> &bt, int *err, cudaStream_t stream) {
+    using S = VjpShape<D, N, FLUX>;
+    auto kern = vjp_modal_kernel<D, N, FLUX, S>;
+    static_assert(S::SMEM <= 227 * 1024, "shared memory");
+    if (S::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t blocks = (n_elem + S::EPB - 1) / S::EPB;
+    kern<<<(unsigned)blocks, S::THREADS, S::SMEM, stream>>>(u, Ja, lam, g, n_elem, tab, err, bt);
+    return cudaGetLastError();
 }
 
 template <int D, int N, int FLUX, class S>

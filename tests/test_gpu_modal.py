@@ -208,3 +208,44 @@ def test_errors_and_domain():
     # empty input is a no-op
     A.sfh_volume_residual_modal(ctx.handle, 0, 0, ut.data_ptr(), Jt.data_ptr(), r.data_ptr(), A.SFH_FP64)
 
+
+
+@pytest.mark.parametrize("d, kind, basis, flux_name, p", [(3, 1, LEG, "euler", 4), (3, 0, LGAUSS, "euler", 3),
+                                                          (2, 1, LEG, "euler_chandrashekar", 5),
+                                                          (3, 1, LEG, "burgers", 2), (3, 0, LEG, "euler", 7),
+                                                          (2, 0, LGLL, "euler", 8)])
+def test_modal_vjp_parity(d, kind, basis, flux_name, p):
+    fl = FLUX[flux_name]
+    N = 2 if (d == 3 and p >= 6) else 3
+    uhat, Ja = I.modal_workload(d, p, kind, basis, N, flux="burgers" if fl == O.FLUX_BURGERS else "euler")
+    lam = I.cotangent(uhat.shape)
+    ref = O.vjp_modal(d, p, kind, basis, fl, uhat, Ja, lam)
+    ctx = api.Context(d, p, kind, flux_name)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
+    got = ctx.vjp_modal(t(uhat), t(Ja), t(lam), basis).cpu().numpy()
+    assert ctx.check() == A.SFH_OK
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_modal_autograd():
+    """torch.autograd through the modal residual: backward calls the modal
+    adjoint; its result against the oracle and a directional difference of
+    the GPU residual."""
+    d, p, kind = 3, 4, 1
+    uhat, Ja = I.modal_workload(d, p, kind, LEG, 2)
+    lam = I.cotangent(uhat.shape, seed=11)
+    ctx = api.Context(d, p, kind, "euler")
+    ut = torch.from_numpy(uhat).cuda().requires_grad_()
+    Jt, lt = torch.from_numpy(Ja).cuda(), torch.from_numpy(lam).cuda()
+    r = api.volume_modal(ut, Jt, ctx, "legendre")
+    (r * lt).sum().backward()
+    g = ut.grad.cpu().numpy()
+    ref = O.vjp_modal(d, p, kind, LEG, O.FLUX_EULER, uhat, Ja, lam)
+    assert np.abs(g - ref).max() <= 1e-12 * np.abs(ref).max()
+    delta = torch.from_numpy(np.random.default_rng(12).standard_normal(uhat.shape)).cuda()
+    h = 1e-6
+    with torch.no_grad():
+        rp = ctx.volume_residual_modal(ut.detach() + h * delta, Jt, "legendre", "fp64")
+        rm = ctx.volume_residual_modal(ut.detach() - h * delta, Jt, "legendre", "fp64")
+    fd = float(((rp - rm) * lt).sum() / (2 * h))
+    assert abs(float((ut.grad * delta).sum()) - fd) <= 1e-6 * abs(fd)
