@@ -673,8 +673,16 @@ def main():
                                             out.data_ptr(), prec, sh)
             _, tm = timed_launches(stepm, k64, 2, stream, torch)
             md[name] = {"element_dof_per_s": dof / (tm * 1e-3), "ms": tm, "over_nodal": tm / t_nodal}
+        lh = torch.from_numpy(I.cotangent(uh.shape, seed=8)).to(dev)
+
+        def stepmv():
+            A.sfh_vjp_modal(ctx.handle, A.SFH_BASIS_LEGENDRE, E, th64.data_ptr(), tJ.data_ptr(), lh.data_ptr(),
+                            g.data_ptr(), sh)
+        _, tmv = timed_launches(stepmv, k64, 2, stream, torch)
+        md["vjp_fp64"] = {"element_dof_per_s": dof / (tmv * 1e-3), "ms": tmv, "over_nodal": tmv / tv}
         assert ctx.check() == A.SFH_OK
         variants["modal"] = md
+        del lh
         del th64, th32
         variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
         variants["fig1_gpu"] = fig1_gpu(torch, A, stream)
