@@ -320,7 +320,10 @@ sfh_status sfh_server_create(const sfh_server_opts *opts, sfh_server **out);
 /* Queue a request (thread-safe).  SFH_ENOMEM if the request alone exceeds
  * the budget, SFH_EINVAL for bad fields; otherwise the request is queued
  * FIFO and *ticket identifies it.  The arrays must stay valid and unchanged
- * until sfh_serve_poll reports the request done. */
+ * until sfh_serve_poll reports the request done.  The server's persistent
+ * kernel may start the request at once and is not ordered against the
+ * caller's streams: device work that writes u, Ja or lambda, or that still
+ * reads or writes out, must be complete before the call. */
 sfh_status sfh_serve_submit(sfh_server *srv, const sfh_request *req, uint64_t *ticket);
 
 /* Non-blocking: SFH_OK and *out filled when the request is done (out->status

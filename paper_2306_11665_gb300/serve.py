@@ -15,8 +15,13 @@ class Server:
         self._keep = {}
 
     def submit(self, kind: int, p: int, nodes: int, prec: int, u: torch.Tensor, Ja: torch.Tensor,
-               out: torch.Tensor, lam: torch.Tensor | None = None) -> int:
-        """Queue one request; the tensors must stay alive and unchanged until it is done."""
+               out: torch.Tensor, lam: torch.Tensor | None = None, sync: bool = True) -> int:
+        """Queue one request; the tensors must stay alive and unchanged until it
+        is done.  The server's kernel is not ordered after torch's streams, so
+        by default the current stream is synchronized first (work that wrote
+        the inputs, or that still uses `out`, completes before the queueing)."""
+        if sync:
+            torch.cuda.current_stream(u.device).synchronize()
         req = A.Request(kind, p, nodes, prec, u.shape[0], u.data_ptr(), Ja.data_ptr(),
                         lam.data_ptr() if lam is not None else None, out.data_ptr())
         t = A.sfh_serve_submit(self.handle, req)
