@@ -479,12 +479,18 @@ def main():
     ap.add_argument("--nodes", default="gll", choices=["gll", "gauss"])
     ap.add_argument("--prec", default="fp32k", choices=["fp32k", "fp64", "fp32mix", "vjp"],
                     help="what the timed step runs (default: the FP32-Kahan residual)")
+    ap.add_argument("--basis", default="nodal", choices=["nodal", "legendre"],
+                    help="timed step on nodal states (default) or the modal path on Legendre coefficients")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.basis != "nodal":
+        # a diagnostic line of the modal kernels: no host-buffer leg and no
+        # oracle baseline (both are of the nodal path)
+        args.no_e2e = args.no_cpu = True
     if args.impl == "reference":
         return run_reference(args)
 
@@ -513,6 +519,8 @@ def main():
         W["N"] = args.N if args.N is not None else W["N"]
         W["kind"] = 0 if args.nodes == "gll" else 1
         W["name"] = f"euler3d_p{W['p']}_{args.nodes}_{W['N']}cubed_warped"
+    if args.basis != "nodal":
+        W["name"] = W["name"] + "_modal_" + args.basis
     d, p, kind, N = W["d"], W["p"], W["kind"], W["N"]
     nn = (p + 1) ** d
     u64, Ja = I.workload(d, p, kind, N, seed0=D.weak_block_seed(rank))   # each rank its own block
@@ -533,9 +541,23 @@ def main():
     sampler = ClockSampler(gpu_idx)
 
     lam_main = torch.from_numpy(I.cotangent(u64.shape, seed=8)).to(dev) if args.prec == "vjp" else None
+    modal = args.basis != "nodal"
+    if modal:
+        # the timed step takes Legendre coefficients of the same size instead
+        tuh64 = torch.from_numpy(I.legendre_coefficients(d, p, E)).to(dev)
+        tuh32 = tuh64.float()
 
     def step32():
-        if args.prec == "fp32k":
+        if modal:
+            pr = {"fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED, "fp64": A.SFH_FP64}.get(args.prec)
+            if pr is None:
+                A.sfh_vjp_modal(ctx.handle, A.SFH_BASIS_LEGENDRE, E, tuh64.data_ptr(), tJ.data_ptr(),
+                                lam_main.data_ptr(), r64.data_ptr(), sh)
+            else:
+                src, out = (tuh64, r64) if pr == A.SFH_FP64 else (tuh32, r32)
+                A.sfh_volume_residual_modal(ctx.handle, A.SFH_BASIS_LEGENDRE, E, src.data_ptr(), tJ.data_ptr(),
+                                            out.data_ptr(), pr, sh)
+        elif args.prec == "fp32k":
             A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_KAHAN, sh)
         elif args.prec == "fp32mix":
             A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_MIXED, sh)
@@ -568,10 +590,13 @@ def main():
     if args.prec == "fp32k":
         b32 = bytes_per_node("fp32k", d) * dof
         roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak, "traffic": measured_traffic(args.prec, p, kind, N),
-                    "peak_source": hbm_src, "kernel": ("volume_fp32_row_kernel<%d>" % (p + 1) if d == 3 and p + 1 in (7, 8)
+                    "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak,
+                    "traffic": None if modal else measured_traffic(args.prec, p, kind, N),
+                    "peak_source": hbm_src,
+                    "kernel": ("volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, p + 1) if modal else
+                               "volume_fp32_row_kernel<%d>" % (p + 1) if d == 3 and p + 1 in (7, 8)
                                else "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1)),
-                    "ncu": measured_counters(args.prec, p, kind, N),
+                    "ncu": None if modal else measured_counters(args.prec, p, kind, N),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     elif args.prec == "fp32mix":
         # the FP64 log means bind the mixed mode: ALU roofline of the FP64 pipe

@@ -249,3 +249,29 @@ def test_modal_autograd():
         rm = ctx.volume_residual_modal(ut.detach() - h * delta, Jt, "legendre", "fp64")
     fd = float(((rp - rm) * lt).sum() / (2 * h))
     assert abs(float((ut.grad * delta).sum()) - fd) <= 1e-6 * abs(fd)
+
+
+@pytest.mark.parametrize("modal", [False, True])
+@pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 3, 1), (2, 6, 1)])
+def test_fp32_unaligned_bases_take_the_plain_load_path(modal, d, p, kind):
+    """u and r 4 bytes past a 16-byte boundary: the persistent FP32 kernel
+    stages with plain loads instead of bulk copies; the result is the same
+    bit for bit (nodal and modal)."""
+    uhat, Ja = I.modal_workload(d, p, kind, LEG, 3)
+    ctx = api.Context(d, p, kind, "euler")
+    u32 = torch.from_numpy(I.to_fp32(uhat)).cuda()
+    Jt = torch.from_numpy(Ja).cuda()
+    n = u32.numel()
+    ub = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    rb = torch.empty(n + 1, dtype=torch.float32, device="cuda")
+    uo, ro = ub[1:].view(u32.shape), rb[1:].view(u32.shape)
+    uo.copy_(u32)
+    assert uo.data_ptr() % 16 != 0 and ro.data_ptr() % 16 != 0
+    if modal:
+        ref = ctx.volume_residual_modal(u32, Jt, "legendre", "fp32k")
+        ctx.volume_residual_modal(uo, Jt, "legendre", "fp32k", out=ro)
+    else:
+        ref = ctx.volume_residual(u32, Jt, "fp32k")
+        ctx.volume_residual(uo, Jt, "fp32k", out=ro)
+    assert ctx.check() == A.SFH_OK
+    assert torch.equal(ref, ro)
