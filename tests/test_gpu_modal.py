@@ -257,9 +257,12 @@ def test_fp32_unaligned_bases_take_the_plain_load_path(modal, d, p, kind):
     """u and r 4 bytes past a 16-byte boundary: the persistent FP32 kernel
     stages with plain loads instead of bulk copies; the result is the same
     bit for bit (nodal and modal)."""
-    uhat, Ja = I.modal_workload(d, p, kind, LEG, 3)
+    if modal:
+        src, Ja = I.modal_workload(d, p, kind, LEG, 3)
+    else:
+        src, Ja = I.workload(d, p, kind, 3)
     ctx = api.Context(d, p, kind, "euler")
-    u32 = torch.from_numpy(I.to_fp32(uhat)).cuda()
+    u32 = torch.from_numpy(I.to_fp32(src)).cuda()
     Jt = torch.from_numpy(Ja).cuda()
     n = u32.numel()
     ub = torch.empty(n + 1, dtype=torch.float32, device="cuda")
