@@ -467,51 +467,45 @@ __device__ __forceinline__ void fp32_block_store(const float *sR, float *gR, int
     }
 }
 
-// FP32 basis-transform pass with packed arithmetic: each task takes the same
-// line of two element-variables (q, q + 1) as the two lanes of FP32x2 FMAs;
-// the per-lane operation order is that of basis_pass (bit-identical
-// results).  NSUM > 1 (backward pass 0): the input is the sum, in a fixed
-// order, of NSUM slices `slice` floats apart (the directions' residuals).
+// FP32 basis-transform pass of the persistent kernel: basis_pass with, for
+// NSUM > 1 (backward pass 0), the input summed in a fixed order over NSUM
+// slices `slice` floats apart (the directions' residuals, in the order of the
+// nodal store).  (Packing two element-variables into FP32x2 lanes measured
+// 6 % slower at p = 4.)
 template <int D, int N, bool TRANSPOSE, int ROLE = kPassPlain, int NSUM = 1>
-__device__ __forceinline__ void basis_pass_f2(const float *in, float *out, int m, int nq, const BasisTab<float> &bt,
-                                              int tid, int nthreads, const float *coef = nullptr, int slice = 0) {
+__device__ __forceinline__ void basis_pass_f(const float *in, float *out, int m, int nq, const BasisTab<float> &bt,
+                                             int tid, int nthreads, const float *coef = nullptr, int slice = 0) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
-    const int npair = (nq + 1) / 2;
-    for (int t = tid; t < npair * NLINE; t += nthreads) {
-        const int qq = t / NLINE, l = t - qq * NLINE;
-        const int q0 = 2 * qq, q1 = q0 + 1 < nq ? q0 + 1 : q0;
+    for (int t = tid; t < nq * NLINE; t += nthreads) {
+        const int q = t / NLINE, l = t - q * NLINE;
         int base;
         if constexpr (D == 3) base = m == 0 ? N * l : (m == 1 ? l % N + N * N * (l / N) : l);
         else base = m == 0 ? N * l : l;
-        const float *s0 = in + q0 * NN + base, *s1 = in + q1 * NN + base;
-        float2 x[N];
+        const float *src = in + q * NN + base;
+        float x[N];
 #pragma unroll
         for (int b = 0; b < N; ++b) {
-            float a0 = s0[b * stride], a1 = s1[b * stride];
+            float a = src[b * stride];
 #pragma unroll
-            for (int k = 1; k < NSUM; ++k) {
-                a0 += s0[k * slice + b * stride];
-                a1 += s1[k * slice + b * stride];
-            }
-            x[b] = f2(a0, a1);
+            for (int k = 1; k < NSUM; ++k) a += src[k * slice + b * stride];
+            x[b] = a;
         }
         if constexpr (ROLE == kPassFirst) {
-            if (bt.const_mode && base == 0) x[0] = f2(0.0f, 0.0f);
+            if (bt.const_mode && base == 0) x[0] = 0.0f;
         }
-        float2 c = f2(0.0f, 0.0f);
+        float c = 0.0f;
         if constexpr (ROLE == kPassLast) {
-            if (bt.const_mode) c = f2(coef[q0 * NN] * bt.c0, coef[q1 * NN] * bt.c0);
+            if (bt.const_mode) c = coef[q * NN] * bt.c0;
         }
-        float *d0 = out + q0 * NN + base, *d1 = out + q1 * NN + base;
+        float *dst = out + q * NN + base;
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-            float2 acc = f2(0.0f, 0.0f);
+            float acc = 0.0f;
 #pragma unroll
-            for (int b = 0; b < N; ++b) acc = fma2(f2s(TRANSPOSE ? bt.V[b * N + a] : bt.V[a * N + b]), x[b], acc);
-            if constexpr (ROLE == kPassLast) acc = add2(acc, c);
-            d0[a * stride] = acc.x;
-            if (q1 != q0) d1[a * stride] = acc.y;
+            for (int b = 0; b < N; ++b) acc = fmaf(TRANSPOSE ? bt.V[b * N + a] : bt.V[a * N + b], x[b], acc);
+            if constexpr (ROLE == kPassLast) acc += c;
+            dst[a * stride] = acc;
         }
     }
 }
@@ -582,14 +576,14 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
         const float *uin = rawU + cur.offU;
         if constexpr (MODAL) {
             float *s0 = sR, *s1 = sR + EPB * U_EL, *s2 = sR + 2 * EPB * U_EL;
-            basis_pass_f2<D, N, false, kPassFirst>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
+            basis_pass_f<D, N, false, kPassFirst>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
             __syncthreads();
             if constexpr (D == 3) {
-                basis_pass_f2<D, N, false>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS);
+                basis_pass_f<D, N, false>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS);
                 __syncthreads();
-                basis_pass_f2<D, N, false, kPassLast>(s1, s2, 2, ne * NVAR, *bt, tid, S::THREADS, uin);
+                basis_pass_f<D, N, false, kPassLast>(s1, s2, 2, ne * NVAR, *bt, tid, S::THREADS, uin);
             } else {
-                basis_pass_f2<D, N, false, kPassLast>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS, uin);
+                basis_pass_f<D, N, false, kPassLast>(s0, s1, 1, ne * NVAR, *bt, tid, S::THREADS, uin);
             }
             __syncthreads();
             uin = D == 3 ? s2 : s1;
@@ -620,15 +614,15 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
             // store) into the free primitive buffer
             float *s0 = sR;
             float *gR = r + cur.e0 * U_EL;
-            basis_pass_f2<D, N, true, kPassPlain, D>(sR, sP, 0, ne * NVAR, *bt, tid, S::THREADS, nullptr,
+            basis_pass_f<D, N, true, kPassPlain, D>(sR, sP, 0, ne * NVAR, *bt, tid, S::THREADS, nullptr,
                                                      EPB * U_EL);
             __syncthreads();
             if constexpr (D == 3) {
-                basis_pass_f2<D, N, true>(sP, s0, 1, ne * NVAR, *bt, tid, S::THREADS);
+                basis_pass_f<D, N, true>(sP, s0, 1, ne * NVAR, *bt, tid, S::THREADS);
                 __syncthreads();
-                basis_pass_f2<D, N, true>(s0, gR, 2, ne * NVAR, *bt, tid, S::THREADS);
+                basis_pass_f<D, N, true>(s0, gR, 2, ne * NVAR, *bt, tid, S::THREADS);
             } else {
-                basis_pass_f2<D, N, true>(sP, gR, 1, ne * NVAR, *bt, tid, S::THREADS);
+                basis_pass_f<D, N, true>(sP, gR, 1, ne * NVAR, *bt, tid, S::THREADS);
             }
         } else {
             fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, S::THREADS);
