@@ -253,6 +253,45 @@ __device__ __forceinline__ double inv_ln_mean_f64(double a, double b, float af, 
     return log(a / b) / d;
 }
 
+// The mixed mode's FP64 logarithmic means inside the band (the caller has
+// tested it on the FP32 values af, bf): their results are rounded to FP32,
+// so about 2^-40 relative accuracy suffices, not FP64's 2^-53.  1/(a + b) is
+// the FP32 hardware reciprocal refined by one FP64 Newton step (2^-22 ->
+// below 2^-43); the series run in FP64 up to u^2, the tail from u^3 in FP32
+// (its rounding weighs below u^3 2^-24 / 20 < 1e-14).  Eleven FP64
+// operations each instead of fifteen.
+__device__ __forceinline__ double ln_mean_mix(double a, double b, float af, float bf) {
+    const double d = a - b, s = a + b;
+    const double r0 = f2d_int(rcp_approx(af + bf));
+    const double rs = fma(r0, fma(-s, r0, 1.0), r0);
+    const double t = d * rs;
+    const double u = t * t;
+    const float uf = d2f_int(u);
+    float T = fmaf(uf, (float)(-25865068.0 / 1915538625.0), (float)(-10719068.0 / 638512875.0));
+    T = fmaf(uf, T, (float)(-10196.0 / 467775.0));
+    T = fmaf(uf, T, (float)(-428.0 / 14175.0));
+    T = fmaf(uf, T, (float)(-44.0 / 945.0));
+    double h = fma(u, f2d_int(T), -4.0 / 45.0);
+    h = fma(u, h, -1.0 / 3.0);
+    return (0.5 * s) * fma(u, h, 1.0);
+}
+__device__ __forceinline__ double inv_ln_mean_mix(double a, double b, float af, float bf) {
+    const double d = a - b, s = a + b;
+    const double r0 = f2d_int(rcp_approx(af + bf));
+    const double rs = fma(r0, fma(-s, r0, 1.0), r0);
+    const double t = d * rs;
+    const double u = t * t;
+    const float uf = d2f_int(u);
+    float T = fmaf(uf, 1.0f / 17.0f, 1.0f / 15.0f);
+    T = fmaf(uf, T, 1.0f / 13.0f);
+    T = fmaf(uf, T, 1.0f / 11.0f);
+    T = fmaf(uf, T, 1.0f / 9.0f);
+    T = fmaf(uf, T, 1.0f / 7.0f);
+    double h = fma(u, f2d_int(T), 1.0 / 5.0);
+    h = fma(u, h, 1.0 / 3.0);
+    return (2.0 * rs) * fma(u, h, 1.0);
+}
+
 // Value and both partial derivatives of {a,b}_ln and of its reciprocal
 // (FP64, for the adjoint), with the band test on FP32 copies af, bf and the
 // series tails from u^5 in FP32 as in ln_mean_f64.  With s = a + b,

@@ -62,15 +62,15 @@ __device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, t
     for (int k = 1; k < D; ++k) { vna += A.v[k] * n[k]; vnb += B.v[k] * n[k]; vv += A.v[k] * B.v[k]; }
     T Lr, iLb;
     if constexpr (M::mixed) {
-        // FP64 logarithmic mean inside the near-equal band (the FP64 routines
-        // of the FP64 kernels: Newton reciprocal, series tail in FP32, band
-        // test on the FP32 values), FP32 outside; widening by integer
-        // conversion keeps the FP64 pipe for the arithmetic
+        // FP64 logarithmic mean inside the near-equal band (band test on the
+        // FP32 values; FP64 arithmetic to the accuracy an FP32 result needs),
+        // FP32 outside; widening by integer conversion keeps the FP64 pipe
+        // for the arithmetic
         const float dr = A.rho - B.rho, sr = A.rho + B.rho;
-        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = d2f_int(ln_mean_f64(f2d_int(A.rho), f2d_int(B.rho), A.rho, B.rho));
+        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = d2f_int(ln_mean_mix(f2d_int(A.rho), f2d_int(B.rho), A.rho, B.rho));
         else Lr = ln_mean(A.rho, B.rho);
         const float db = A.beta - B.beta, sb = A.beta + B.beta;
-        if (db * db < (float)kLnBand * (sb * sb)) iLb = d2f_int(inv_ln_mean_f64(A.beta_d, B.beta_d, A.beta, B.beta));
+        if (db * db < (float)kLnBand * (sb * sb)) iLb = d2f_int(inv_ln_mean_mix(A.beta_d, B.beta_d, A.beta, B.beta));
         else iLb = inv_ln_mean(A.beta, B.beta);
     } else {
         Lr = ln_mean(A.rho, B.rho);
