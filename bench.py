@@ -39,10 +39,11 @@ GAMMA_DIAG = 30          # algorithmic flops of one diagonal (physical-flux) ter
 PAIR_FLOPS = 92          # algorithmic flops of one off-diagonal pair (see flops_per_element)
 NODE_FLOPS = 13          # conservative -> primitive per node
 # FP64 flops of one pair in the mixed mode (both log means inside the near-equal
-# band, where the mixed mode evaluates them in FP64): metric sum 3; ln mean:
-# band test 5, quotient 2, series 14, scaling 2 -> 23; inverse ln mean: band
-# test 5, reciprocal and quotient 3, series 16, scaling 2 -> 26.
-MIX_PAIR_FP64_FLOPS = 52
+# band, where the mixed mode evaluates them in FP64; band tests and series
+# tails in FP32): metric sum 3; each mean: difference and sum 2, one Newton
+# step of the reciprocal 4, quotient and square 2, series 4 + 2, scaling 2
+# -> 16.
+MIX_PAIR_FP64_FLOPS = 35
 
 
 def flops_per_element(d: int, p: int, kind: int) -> float:

@@ -129,6 +129,10 @@ struct Shape {
     static constexpr int EPB = EPB_SMEM < EPB_LINES ? EPB_SMEM : EPB_LINES;
     static constexpr int THREADS = ((EPB * NLINE + 31) / 32) * 32;
     static constexpr size_t SMEM = (size_t)EPB * NN * NODE_BYTES;
+    // resident CTAs asked of the compiler: the mixed mode's FP64 log means
+    // are latency-bound, so at n <= 5 its line body is held to 128 registers
+    // (four warps per sub-partition instead of three)
+    static constexpr int MINB = (M::mixed && N <= 5 && THREADS <= 128) ? 65536 / (THREADS * 128) : 1;
 };
 
 // ---------------------------------------------------------------------------

@@ -442,7 +442,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 }
 
 template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>
-__global__ void __launch_bounds__(S::THREADS)
+__global__ void __launch_bounds__(S::THREADS, S::MINB)
 volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
               typename M::T *__restrict__ r, int64_t n_elem,
               const __grid_constant__ OpTab<typename M::T> tab, int *__restrict__ err) {
