@@ -186,12 +186,12 @@ def test_p6_entropy_identity_and_p7_conservation(d, flux, kind, p):
         assert np.abs(cons_lhs - cons_rhs).max() <= 1e-13 * max(scale, 1.0)
 
 
-def test_p6_lgl_north_star_form():
+def test_p6_lgl_boundary_entropy_flux_form():
     """Gauss-Lobatto: E_m = B_m is diagonal, so the identity becomes
     w^T r = sum_m sum_i (B_m)_ii (w_i . f(u_i; Ja^m(i)) - psi_i . Ja^m(i))
             + sum_m psi^T Q_m Ja^m,
     and the last sum vanishes when the metrics satisfy the discrete identities
-    sum_m D_m Ja^m_k = 0: the benchmark spec's w^T (2 Q o F) 1 = 1^T B F_entropy."""
+    sum_m D_m Ja^m_k = 0: the stated form w^T (2 Q o F) 1 = 1^T B F_entropy."""
     d, p, kind = 3, 4, GLL
     u, Ja = I.workload(d, p, kind, 2)
     r = O.volume_sf(d, p, kind, O.FLUX_EULER, u, Ja)
