@@ -72,6 +72,7 @@ def _load():
         lib.orc_modal_states.argtypes = [i, i, i, i, i, i, L, dp, dp, dp]
         lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, i, L, dp, dp, dp]
         lib.orc_vjp_modal.argtypes = [i, i, i, i, i, i, L, dp, dp, dp, dp]
+        lib.orc_surface_dense.argtypes = [i, i, i, i, i, L, dp, dp, dp, dp, dp]
         lib.orc_entropy_vars.argtypes = [i, i, dp, dp]
         lib.orc_entropy_state.argtypes = [i, i, dp, dp]
         _lib = lib
@@ -264,3 +265,15 @@ def vjp_modal(d, p, kind, basis, flux, uhat, Ja, lamhat) -> np.ndarray:
     _check(_load().orc_vjp_modal(d, p, kind, basis, nvar_of(d, flux), flux, uhat.shape[0], _p(uhat), _p(Ja),
                                  _p(lamhat), _p(g)))
     return g
+
+
+def surface_dense(d, p, kind, flux, u, u_face, nJ):
+    """(r_vol, r_face) of the dense surface Hadamard product (B E) o C of each
+    element's 2d faces; u_face [E][2d][nvar][n^(d-1)], nJ [E][2d][d][n^(d-1)]."""
+    u, u_face, nJ = _f64(u), _f64(u_face), _f64(nJ)
+    nvar = nvar_of(d, flux)
+    E, nf = u.shape[0], (p + 1) ** (d - 1)
+    assert u.shape == (E, nvar, (p + 1) ** d) and u_face.shape == (E, 2 * d, nvar, nf) and nJ.shape == (E, 2 * d, d, nf)
+    rv, rf = np.zeros_like(u), np.zeros_like(u_face)
+    _check(_load().orc_surface_dense(d, p, kind, nvar, flux, E, _p(u), _p(u_face), _p(nJ), _p(rv), _p(rf)))
+    return rv, rf

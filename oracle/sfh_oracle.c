@@ -975,3 +975,77 @@ int orc_vjp_modal(int d, int p, int kind, int basis, int nvar, int flux, long n_
     free(V); free(Wd); free(uv); free(lv); free(gv);
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Surface Hadamard product of one element (Remark 1; the theorem's operator */
+/* with alpha = 0 on the facet cubature; the surface coupling of Chan's     */
+/* hybridised SBP form).  Face (m, side), side 0 at xi_m = -1, side 1 at    */
+/* +1; facet cubature = the tensor product of the 1D nodes in the other    */
+/* directions (lower axis fastest), n^{d-1} nodes f with weights           */
+/* w_f = prod_{k != m} w[b_k(f)].  With the interpolation E = e (x) I (x) I */
+/* (e in position m, e[b] = l_b(-1 or +1)) and a face state u~_f and face  */
+/* normal nJ_f supplied by the caller, the dense Hadamard product          */
+/*   H[f][j] = w_f E[f][j] fsharp(u~_f, u_j) . nJ_f                       */
+/* gives the volume vector r_vol[j] = sum_{faces} sum_f H[f][j] and the    */
+/* face vector r_face[f] = sum_j H[f][j].  Dense: every (f, j) pair, E from */
+/* its Kronecker definition.                                                */
+/* Layouts: u[e][var][i]; u_face[e][face][var][f]; nJ[e][face][k][f];       */
+/* r_vol like u; r_face like u_face; face = 2 m + side.                    */
+/* ------------------------------------------------------------------------ */
+int orc_surface_dense(int d, int p, int kind, int nvar, int flux, long n_elem, const double *u,
+                      const double *u_face, const double *nJ, double *r_vol, double *r_face)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), nf = ipow(n, d - 1), st = 0;
+    double xi[16], w[16], e[2][16];
+    orc_nodes(p, kind, xi, w);
+    for (int side = 0; side < 2; ++side) {
+        double x = side ? 1.0 : -1.0;
+        for (int b = 0; b < n; ++b) {
+            long double l = 1.0L;
+            for (int j = 0; j < n; ++j)
+                if (j != b) l *= ((long double)x - xi[j]) / ((long double)xi[b] - xi[j]);
+            e[side][b] = (double)l;
+        }
+    }
+    for (long el = 0; el < n_elem; ++el) {
+        const double *ue = u + el * nvar * nn;
+        double *rv = r_vol + el * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) rv[q] = 0.0;
+        for (int m = 0; m < d; ++m)
+            for (int side = 0; side < 2; ++side) {
+                int face = 2 * m + side;
+                const double *uf = u_face + (el * 2 * d + face) * nvar * nf;
+                const double *nf_ = nJ + (el * 2 * d + face) * d * nf;
+                double *rf = r_face + (el * 2 * d + face) * nvar * nf;
+                for (int q = 0; q < nvar * nf; ++q) rf[q] = 0.0;
+                for (int f = 0; f < nf; ++f) {
+                    int bf[3]; node_to_multi(f, n, d - 1, bf);   /* the other directions, lower first */
+                    double wf = 1.0;
+                    for (int k = 0; k < d - 1; ++k) wf *= w[bf[k]];
+                    double ufv[5], nv[3];
+                    for (int v = 0; v < nvar; ++v) ufv[v] = uf[v * nf + f];
+                    for (int k = 0; k < d; ++k) nv[k] = nf_[k * nf + f];
+                    for (int j = 0; j < nn; ++j) {
+                        int aj[3]; node_to_multi(j, n, d, aj);
+                        /* E[f][j] = e[a_m(j)] * prod over the other axes of delta */
+                        double E = e[side][aj[m]];
+                        for (int k = 0, t = 0; k < d; ++k) {
+                            if (k == m) continue;
+                            if (aj[k] != bf[t]) E = 0.0;
+                            ++t;
+                        }
+                        double uj[5], F[5];
+                        for (int v = 0; v < nvar; ++v) uj[v] = ue[v * nn + j];
+                        st |= orc_ec_flux(d, flux, ufv, uj, nv, F);
+                        for (int v = 0; v < nvar; ++v) {
+                            double h = wf * E * F[v];
+                            rv[v * nn + j] += h;
+                            rf[v * nf + f] += h;
+                        }
+                    }
+                }
+            }
+    }
+    return st;
+}

@@ -22,6 +22,11 @@ Recipe (the paper runs its timing on a warped periodic cube, Section 3):
     own PCG64 stream (seeds 2, 3.., 3+d); then conservative variables.
   * Burgers states: u = sin(2 pi x) sin(2 pi y) + 0.1 N(0,1), seed 1.
   * Cotangents: N(0,1), seed 8.
+  * Surface inputs: on each face (m, side) of an element the facet
+    cubature points (xi_m = -1 or +1, the 1D nodes in the other directions,
+    lower axis fastest) are mapped by the same warped map; the face state is
+    the same state recipe at those points, the face normal the adjugate of
+    the map's exact Jacobian there, row m, times -1 (side 0) or +1 (side 1).
   * Modal inputs (solution in a basis chi, integrated on the cubature nodes of
     `kind`): for a Lagrange basis on Gauss-Lobatto or Gauss nodes the
     coefficients are the state above at those solution nodes; for the
@@ -234,3 +239,60 @@ def legendre_coefficients(d: int, p: int, E: int, flux: str = "euler", seed: int
     uhat = 0.04 * rng.standard_normal((E, mean.size, nn)) / (1.0 + kk) ** 2
     uhat[:, :, 0] += mean * 2.0 ** (d / 2.0)
     return np.ascontiguousarray(uhat)
+
+
+def surface_workload(d: int, p: int, kind: int, N: int, flux: str = "euler", amp: float = 0.1,
+                     n_elem: int | None = None):
+    """(u, u_face, nJ): the volume state of ``workload``, face states
+    u_face[e][face][var][f] and face normals nJ[e][face][k][f], face = 2 m + side
+    (recipe in the module docstring)."""
+    u, _ = workload(d, p, kind, N, flux, amp, n_elem)
+    n = p + 1
+    nf = n ** (d - 1)
+    E = u.shape[0]
+    xi, _ = nodes_1d(p, kind)
+    e = np.arange(E)
+    ek = [(e // N ** k) % N for k in range(d)]
+    f = np.arange(nf)
+    bf = [(f // n ** k) % n for k in range(d - 1)]
+    X = np.empty((E, 2 * d, d, nf))     # affine coordinates of the face points
+    for m in range(d):
+        others = [k for k in range(d) if k != m]
+        for side in range(2):
+            for k in range(d):
+                xk = np.full(nf, 1.0 if side else -1.0) if k == m else xi[bf[others.index(k)]]
+                X[:, 2 * m + side, k] = (ek[k][:, None] + 0.5 * (xk[None, :] + 1.0)) / N
+    S = np.sin(math.pi * X)
+    C = np.cos(math.pi * X)
+    shift = amp * np.prod(S, axis=2)                      # [E][face][f]
+    x = X + shift[:, :, None, :]
+    # dx_k/dxi_j = (delta_kj + amp pi cos(pi X_j) prod_{l != j} sin(pi X_l)) / (2N)
+    A = np.empty((E, 2 * d, d, d, nf))
+    for j in range(d):
+        dj = amp * math.pi * C[:, :, j] * np.prod(np.delete(S, j, axis=2), axis=2)
+        for k in range(d):
+            A[:, :, k, j] = ((1.0 if k == j else 0.0) + dj) / (2.0 * N)
+    adj = np.empty_like(A)                                   # adj[m][k] = J dxi_m/dx_k
+    if d == 2:
+        adj[:, :, 0, 0] = A[:, :, 1, 1]
+        adj[:, :, 0, 1] = -A[:, :, 0, 1]
+        adj[:, :, 1, 0] = -A[:, :, 1, 0]
+        adj[:, :, 1, 1] = A[:, :, 0, 0]
+    else:
+        for m in range(3):
+            for k in range(3):
+                r = [q for q in range(3) if q != k]
+                c = [q for q in range(3) if q != m]
+                minor = A[:, :, r[0], c[0]] * A[:, :, r[1], c[1]] - A[:, :, r[0], c[1]] * A[:, :, r[1], c[0]]
+                adj[:, :, m, k] = (-1.0) ** (m + k) * minor
+    nJ = np.empty((E, 2 * d, d, nf))
+    for m in range(d):
+        for side in range(2):
+            nJ[:, 2 * m + side] = (1.0 if side else -1.0) * adj[:, 2 * m + side, m]
+    xf = x.reshape(E * 2 * d, d, nf)
+    if flux == "burgers":
+        uf = burgers_state(xf, 13)
+    else:
+        uf = euler_state(xf, 2)
+    u_face = np.ascontiguousarray(uf.reshape(E, 2 * d, -1, nf))
+    return u, u_face, np.ascontiguousarray(nJ)
