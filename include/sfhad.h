@@ -154,6 +154,28 @@ sfh_status sfh_basis_table(int p, sfh_nodes nodes, sfh_basis basis, double *V);
 sfh_status sfh_vjp(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *Ja,
                    const double *lambda, double *grad_u, sfh_stream_t stream);
 
+/* Surface Hadamard product of every element's 2d faces (Remark 1: the
+ * operator of the theorem on general bases with alpha = 0 on the facet
+ * cubature, one-dimensional factors of size 1 x n), FP64.  Face (m, side),
+ * side 0 at xi_m = -1 and side 1 at +1, carries the facet cubature of the
+ * other directions' nodes (n^{d-1} points f, lower axis fastest, weights
+ * w_f = prod w); E = e (x) I (x) I interpolates to it (e[b] = l_b(-+1) in
+ * position m), so face node f couples to the n volume nodes j of its normal
+ * line only (d n^d two-point fluxes per element and face direction; one per
+ * face node on Gauss-Lobatto nodes).  With
+ *   H[f][j] = w_f E[f][j] fsharp(u_face_f, u_j) . nJ_f,
+ *   r_vol[j] = sum over the faces of sum_f H[f][j],  r_face[f] = sum_j H[f][j]
+ * (the volume-to-face coupling of a hybridised SBP discretisation).
+ * u, r_vol: device double [n_elem][nvar][n^d]; u_face, r_face: device double
+ * [n_elem][2d][nvar][n^{d-1}] (face index 2 m + side); nJ_face: device double
+ * [n_elem][2d][d][n^{d-1}], the scaled face normal at each face node, supplied
+ * by the caller (its sign and scaling are the caller's).  Outputs are
+ * overwritten and must not overlap each other or the inputs.  Asynchronous.
+ * Errors: SFH_EINVAL before any launch; SFH_ECUDA; domain errors latched for
+ * sfh_check(). */
+sfh_status sfh_surface_hadamard(sfh_ctx *ctx, int64_t n_elem, const double *u, const double *u_face,
+                                const double *nJ_face, double *r_vol, double *r_face, sfh_stream_t stream);
+
 /* VJP of the modal residual (FP64), Ja fixed: with r_hat = V^T r_v(V u_hat)
  * as in sfh_volume_residual_modal,
  *   grad_hat = V^T (dr_v/du_v)^T V lambda_hat,   u_v = V u_hat,

@@ -62,6 +62,7 @@ _SIGS = {
     "sfh_volume_residual_modal": [vp, ctypes.c_int, i64, vp, vp, vp, ctypes.c_int, vp],
     "sfh_basis_table": [ctypes.c_int, ctypes.c_int, ctypes.c_int, dp],
     "sfh_vjp_modal": [vp, ctypes.c_int, i64, vp, vp, vp, vp, vp],
+    "sfh_surface_hadamard": [vp, i64, vp, vp, vp, vp, vp, vp],
     "sfh_vjp": [vp, i64, vp, vp, vp, vp, vp],
     "sfh_check": [vp, vp],
     "sfh_volume_residual_host": [vp, i64, vp, vp, vp, ctypes.c_int],
@@ -141,6 +142,11 @@ def sfh_volume_residual_modal(ctx: int, basis: int, n_elem: int, u_hat: int, Ja:
 def sfh_vjp_modal(ctx: int, basis: int, n_elem: int, u_hat: int, Ja: int, lam_hat: int, grad_hat: int,
                   stream: int = 0) -> None:
     _call("sfh_vjp_modal", ctx, basis, n_elem, u_hat, Ja, lam_hat, grad_hat, stream)
+
+
+def sfh_surface_hadamard(ctx: int, n_elem: int, u: int, u_face: int, nJ_face: int, r_vol: int, r_face: int,
+                         stream: int = 0) -> None:
+    _call("sfh_surface_hadamard", ctx, n_elem, u, u_face, nJ_face, r_vol, r_face, stream)
 
 
 def sfh_basis_table(p: int, nodes: int, basis: int):

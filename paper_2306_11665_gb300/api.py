@@ -79,6 +79,22 @@ class Context:
                                     pr, torch.cuda.current_stream(u_hat.device).cuda_stream)
         return r
 
+    def surface_hadamard(self, u: torch.Tensor, u_face: torch.Tensor, nJ_face: torch.Tensor):
+        """(r_vol, r_face) of the surface Hadamard product of every element's
+        faces (FP64) on the current stream."""
+        E, d = u.shape[0], self.d
+        nf = (self.p + 1) ** (d - 1)
+        if u.shape != (E, self.nvar, self.n_nodes) or u_face.shape != (E, 2 * d, self.nvar, nf) \
+                or nJ_face.shape != (E, 2 * d, d, nf):
+            raise ValueError("u [E, nvar, n^d], u_face [E, 2d, nvar, n^(d-1)], nJ_face [E, 2d, d, n^(d-1)]")
+        for t in (u, u_face, nJ_face):
+            if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError("inputs must be contiguous float64 CUDA tensors")
+        r_vol, r_face = torch.empty_like(u), torch.empty_like(u_face)
+        A.sfh_surface_hadamard(self.handle, E, u.data_ptr(), u_face.data_ptr(), nJ_face.data_ptr(), r_vol.data_ptr(),
+                               r_face.data_ptr(), torch.cuda.current_stream(u.device).cuda_stream)
+        return r_vol, r_face
+
     def vjp_modal(self, u_hat: torch.Tensor, Ja: torch.Tensor, lam_hat: torch.Tensor, basis="legendre",
                   out: torch.Tensor | None = None):
         """V^T (dr_v/du_v)^T V lambda_hat (FP64), the VJP of volume_residual_modal."""

@@ -53,7 +53,7 @@ def _units():
     units = []
     for name, defs in INST:
         units.append((os.path.join(CSRC, "sfh_inst.cu"), os.path.join(OUT, f"inst_{name}.o"), defs))
-    for src in ("sfh_api.cu", "sfh_serve.cu", "sfh_noalloc.cu", "sfh_entropy.cu", "sfh_fig1.cu"):
+    for src in ("sfh_api.cu", "sfh_serve.cu", "sfh_noalloc.cu", "sfh_entropy.cu", "sfh_fig1.cu", "sfh_surface.cu"):
         units.append((os.path.join(CSRC, src), os.path.join(OUT, src.replace(".cu", ".o")), []))
     return units
 

@@ -223,6 +223,8 @@ struct sfh_ctx {
     // solution bases on the cubature nodes (indexed by sfh_basis)
     sfh::BasisTab<double> basis_d[3];
     sfh::BasisTab<float> basis_f[3];
+    // weights and face-interpolation rows of the surface Hadamard product
+    sfh::SurfTab surf;
     // staging of the host-buffer entry point
     std::mutex host_mu;
     cudaStream_t hs[kHostStages];
@@ -323,6 +325,19 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
         c->basis_d[b].const_mode = c->basis_f[b].const_mode = cm ? 1 : 0;
         c->basis_d[b].c0 = cm ? (double)c0 : 0.0;
         c->basis_f[b].c0 = cm ? (float)c0 : 0.0f;
+    }
+    memset(&c->surf, 0, sizeof c->surf);
+    for (int a = 0; a < n; ++a) {
+        c->surf.w[a] = (double)ww[a];
+        for (int side = 0; side < 2; ++side) {
+            // l_a(-1) / l_a(+1) by the product formula; exactly 0 or 1 where a
+            // node sits at the end point (Gauss-Lobatto)
+            const long double xe = side ? 1.0L : -1.0L;
+            long double l = 1.0L;
+            for (int j = 0; j < n; ++j)
+                if (j != a) l *= (xe - x[j]) / (x[a] - x[j]);
+            c->surf.e[side][a] = (double)l;
+        }
     }
     if ((e = cudaMalloc(&c->d_err, sizeof(int))) != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(error word)"); }
     if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) {
@@ -459,6 +474,33 @@ extern "C" sfh_status sfh_volume_residual_modal(sfh_ctx *c, sfh_basis basis, int
         e = modal_mixed_fn(c->d, c->flux)(c->n, c->flux, u_hat, Ja, r_hat, n_elem, c->tab_f, c->basis_f[basis],
                                           c->d_err, s);
     if (e != cudaSuccess) return cuda_fail(e, "modal volume kernel launch");
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_surface_hadamard(sfh_ctx *c, int64_t n_elem, const double *u, const double *u_face,
+                                           const double *nJ_face, double *r_vol, double *r_face,
+                                           sfh_stream_t stream) {
+    clear_err();
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (n_elem < 0) return fail(SFH_EINVAL, "n_elem must be >= 0, got %lld", (long long)n_elem);
+    if (n_elem == 0) return SFH_OK;
+    if (n_elem > (int64_t)1 << 36) return fail(SFH_EINVAL, "n_elem too large");
+    if (!u || !u_face || !nJ_face || !r_vol || !r_face) return fail(SFH_EINVAL, "null array pointer");
+    if (((uintptr_t)u | (uintptr_t)u_face | (uintptr_t)nJ_face | (uintptr_t)r_vol | (uintptr_t)r_face) % sizeof(double))
+        return fail(SFH_EINVAL, "misaligned array pointer");
+    const size_t nn = (size_t)sfh::ipow(c->n, c->d), nf = (size_t)sfh::ipow(c->n, c->d - 1);
+    const size_t ub = (size_t)n_elem * c->nvar * nn * sizeof(double);
+    const size_t fb = (size_t)n_elem * 2 * c->d * c->nvar * nf * sizeof(double);
+    const size_t jb = (size_t)n_elem * 2 * c->d * c->d * nf * sizeof(double);
+    if (overlap(r_vol, ub, u, ub) || overlap(r_vol, ub, u_face, fb) || overlap(r_vol, ub, nJ_face, jb) ||
+        overlap(r_face, fb, u, ub) || overlap(r_face, fb, u_face, fb) || overlap(r_face, fb, nJ_face, jb) ||
+        overlap(r_vol, ub, r_face, fb))
+        return fail(SFH_EINVAL, "an output overlaps an input or the other output");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    const cudaError_t e = sfh::surface_hadamard(c->d, c->n, c->flux, u, u_face, nJ_face, r_vol, r_face, n_elem,
+                                                c->surf, c->d_err, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "surface kernel launch");
     return SFH_OK;
 }
 

@@ -87,6 +87,16 @@ inline VolumeFn32 volume_mixed_fn(int d, int flux) {
 cudaError_t fig1_hadamard(int n, bool dense, const double *c, double *y, int64_t n_elem, const double *D,
                           cudaStream_t stream);
 
+// Surface Hadamard product (sfh_surface.cu): quadrature weights and the rows
+// interpolating to xi = -1 (side 0) and +1 (side 1), e[side][b] = l_b(-+1).
+struct SurfTab {
+    double w[NMAX];
+    double e[2][NMAX];
+};
+cudaError_t surface_hadamard(int d, int n, int flux, const double *u, const double *u_face, const double *nJ,
+                             double *r_vol, double *r_face, int64_t n_elem, const SurfTab &tab, int *err,
+                             cudaStream_t stream);
+
 // Entropy-identity defect per element (sfh_entropy.cu); r in FP32 or FP64.
 cudaError_t entropy_identity(int d, int n, int flux, const double *u, const double *Ja, const void *r, bool r_fp32,
                              double *out, int64_t n_elem, const OpTab<double> &tab, int *err, cudaStream_t stream);
