@@ -75,24 +75,32 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
 
 # DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one
 # ncu capture of the timed kernel, valid only while the kernel sources are the
-# ones that were profiled (their SHA-1 is recorded with the figure).
+# ones that were profiled (their SHA-1, _kernel_sources_sha1, is recorded with
+# the figure).
 TRAFFIC = {
     # (prec, p, nodes, N): ncu capture of the timed kernel, launch 2 of
     # `bench.py --steps 3 --warmup 1 --no-variants --no-cpu --no-e2e --no-serve`
-    ("fp32k", 4, 0, 32): {"bytes": 377_451_520 + 67_561_984, "sha1": "b34d4e6e3ce5717295b176a0e9c5c36e925065ee",
+    ("fp32k", 4, 0, 32): {"bytes": 377_451_520 + 67_561_984, "sha1": "419dd4f048fa8ff245d1531a58cc8db94222cf41",
                           "counters": {"issue_active_pct": 63.1, "dram_throughput_pct": 33.6, "fma_pipe_pct": 48.6,
                                        "alu_pipe_pct": 25.2, "warps_active_pct": 23.4,
                                        "binding": "instruction issue (FP32 pair arithmetic), not DRAM"}},
 }
 
 
+# The sources that define the timed kernels' code: the persistent FP32 kernel
+# and its building blocks, and the instantiation unit; with the compiler flags.
+# (Other files of the library hold only other kernels and host code.)
+KERNEL_SOURCES = ("sfh_volume_tma.cuh", "sfh_tma.cuh", "sfh_device.cuh", "sfh_inst.cu")
+
+
 def _kernel_sources_sha1():
     import hashlib
+    from paper_2306_11665_gb300 import build as B
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2306_11665_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cuh", ".cu", ".h")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    h.update(repr((B.ARCH, B.FLAGS[:-2])).encode())   # the flags without the include path
     return h.hexdigest()
 
 
