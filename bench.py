@@ -718,6 +718,27 @@ def main():
         variants["modal"] = md
         del lh
         del th64, th32
+        # surface Hadamard product of every element's faces (FP64) on 32^3
+        # elements at p = 4: Gauss-Lobatto (one volume node per face node)
+        # and Gauss (a dense 1 x n interpolation row)
+        sf = {}
+        for kname, knd in (("gll", 0), ("gauss", 1)):
+            su, suf, snj = I.surface_workload(3, 4, knd, 32)
+            cs = api.Context(3, 4, knd, "euler")
+            tsu, tsf, tsj = (torch.from_numpy(a).to(dev) for a in (su, suf, snj))
+            srv, srf = torch.empty_like(tsu), torch.empty_like(tsf)
+
+            def steps(cs=cs, tsu=tsu, tsf=tsf, tsj=tsj, srv=srv, srf=srf):
+                A.sfh_surface_hadamard(cs.handle, tsu.shape[0], tsu.data_ptr(), tsf.data_ptr(), tsj.data_ptr(),
+                                       srv.data_ptr(), srf.data_ptr(), sh)
+            _, ts = timed_launches(steps, k64, 2, stream, torch)
+            fluxes = 2 * 3 * 25 * (1 if knd == 0 else 5) * su.shape[0]
+            sf[kname] = {"ms": ts, "element_dof_per_s": su.shape[0] * 125 / (ts * 1e-3),
+                         "two_point_fluxes_per_launch": fluxes,
+                         "alu_frac_of_fp64_rate": fluxes * PAIR_FLOPS / (ts * 1e-3) / 1.25e12}
+            assert cs.check() == A.SFH_OK
+            del tsu, tsf, tsj, srv, srf
+        variants["surface_fp64"] = sf
         variants["other_configs"] = other_configs(torch, A, I, api, stream, hbm_peak)
         variants["fig1_gpu"] = fig1_gpu(torch, A, stream)
         if not args.no_serve:
