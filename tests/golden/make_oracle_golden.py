@@ -12,8 +12,6 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-import numpy as np  # noqa: E402
-
 import oracle as O  # noqa: E402
 from paper_2306_11665_gb300 import inputs as I  # noqa: E402
 

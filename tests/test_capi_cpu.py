@@ -3,13 +3,12 @@ declares, computes its operator tables on the host (checked against the
 oracle's independent construction) and rejects bad arguments before touching
 a device."""
 import ctypes
-import os
 
 import numpy as np
 import pytest
 
 import oracle as O
-from tests._helpers import ROOT, header_functions
+from tests._helpers import header_functions
 
 
 @pytest.fixture(scope="module")

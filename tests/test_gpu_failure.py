@@ -1,7 +1,6 @@
 """Failure detection on the GPU without a fault: a bounded wait that runs
 out (a barrier phase nothing completes) returns SFH_ETIMEOUT to the host,
 and the context stays usable afterwards."""
-import numpy as np
 import pytest
 import torch
 

@@ -13,7 +13,7 @@ import pytest
 
 import oracle as O
 from paper_2306_11665_gb300 import inputs as I
-from tests._entropy import identity_residual, kron_q
+from tests._entropy import identity_residual
 
 G = O.GAMMA
 CH, RA = O.FLUX_CHANDRASHEKAR, O.FLUX_EULER

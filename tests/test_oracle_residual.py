@@ -11,7 +11,6 @@
   P8  pressure equilibrium of the Ranocha flux: constant v and p give
       r_mom = v r_rho and r_E = |v|^2/2 r_rho.
 """
-import math
 
 import numpy as np
 import pytest

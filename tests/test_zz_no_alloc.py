@@ -10,8 +10,6 @@ fixed device array, which must be refused with a clear error.  This file is
 collected last so that a run stopping at its first failure has already run
 every other test; it also passes alone in a fresh process.
 """
-import ctypes
-
 import numpy as np
 import pytest
 import torch
