@@ -39,32 +39,15 @@ struct BurgersNode {
     TJ S;            // sum_k Ja^m_k
 };
 
-// The mixed mode's two logarithmic means of a pair: FP64 inside the near-equal
-// band (band test on the FP32 values; FP64 arithmetic to the accuracy an FP32
-// result needs), FP32 outside; widening by integer conversion keeps the FP64
-// pipe for the arithmetic.  Returns {rho}_ln and 1/{beta}_ln.
-template <class M, int D>
-__device__ __forceinline__ void mixed_means(const EulerNode<typename M::T, typename M::TJ, D> &A,
-                                            const EulerNode<typename M::T, typename M::TJ, D> &B, float &Lr,
-                                            float &iLb) {
-    const float dr = A.rho - B.rho, sr = A.rho + B.rho;
-    if (dr * dr < (float)kLnBand * (sr * sr)) Lr = d2f_int(ln_mean_mix(f2d_int(A.rho), f2d_int(B.rho), A.rho, B.rho));
-    else Lr = ln_mean(A.rho, B.rho);
-    const float db = A.beta - B.beta, sb = A.beta + B.beta;
-    if (db * db < (float)kLnBand * (sb * sb)) iLb = d2f_int(inv_ln_mean_mix(A.beta_d, B.beta_d, A.beta, B.beta));
-    else iLb = inv_ln_mean(A.beta, B.beta);
-}
-
-// Two-point Euler flux contracted with n = Ja^m(a) + Ja^m(b), given the two
-// logarithmic means Lr = {rho}_ln and iLb = 1/{beta}_ln: Ranocha's
+// Two-point Euler flux contracted with n = Ja^m(a) + Ja^m(b): Ranocha's
 //   f_rho = {rho}_ln {v.n},  f_m = f_rho {v} + {p} n,
 //   f_E = f_rho (v_a.v_b / 2 + 1/((g-1){beta}_ln)) + (p_a v_b + p_b v_a).n / 2,
 // or Chandrashekar's, which takes pt = {rho}/{beta} = (rho_a + rho_b) /
 // (beta_a + beta_b) for {p} and pt {v}.n for the pressure work.
 template <class M, int D, int FLUX>
-__device__ __forceinline__ void euler_pair_flux_lm(const EulerNode<typename M::T, typename M::TJ, D> &A,
-                                                   const EulerNode<typename M::T, typename M::TJ, D> &B,
-                                                   typename M::T Lr, typename M::T iLb, typename M::T F[D + 2]) {
+__device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
+                                                const EulerNode<typename M::T, typename M::TJ, D> &B,
+                                                typename M::T F[D + 2]) {
     using T = typename M::T;
     T n[D];
 #pragma unroll
@@ -77,6 +60,22 @@ __device__ __forceinline__ void euler_pair_flux_lm(const EulerNode<typename M::T
     T vna = A.v[0] * n[0], vnb = B.v[0] * n[0], vv = A.v[0] * B.v[0];
 #pragma unroll
     for (int k = 1; k < D; ++k) { vna += A.v[k] * n[k]; vnb += B.v[k] * n[k]; vv += A.v[k] * B.v[k]; }
+    T Lr, iLb;
+    if constexpr (M::mixed) {
+        // FP64 logarithmic mean inside the near-equal band (band test on the
+        // FP32 values; FP64 arithmetic to the accuracy an FP32 result needs),
+        // FP32 outside; widening by integer conversion keeps the FP64 pipe
+        // for the arithmetic
+        const float dr = A.rho - B.rho, sr = A.rho + B.rho;
+        if (dr * dr < (float)kLnBand * (sr * sr)) Lr = d2f_int(ln_mean_mix(f2d_int(A.rho), f2d_int(B.rho), A.rho, B.rho));
+        else Lr = ln_mean(A.rho, B.rho);
+        const float db = A.beta - B.beta, sb = A.beta + B.beta;
+        if (db * db < (float)kLnBand * (sb * sb)) iLb = d2f_int(inv_ln_mean_mix(A.beta_d, B.beta_d, A.beta, B.beta));
+        else iLb = inv_ln_mean(A.beta, B.beta);
+    } else {
+        Lr = ln_mean(A.rho, B.rho);
+        iLb = inv_ln_mean(A.beta, B.beta);
+    }
     const T half = (T)0.5;
     const T frho = Lr * (half * (vna + vnb));
     T pavg;
@@ -100,21 +99,6 @@ __device__ __forceinline__ void euler_pair_flux_lm(const EulerNode<typename M::T
     for (int l = 0; l < D; ++l) F[1 + l] = frho * (half * (A.v[l] + B.v[l])) + pavg * n[l];
     const T work = FLUX == kFluxEulerCh ? pavg * (half * (vna + vnb)) : half * (A.p * vnb + B.p * vna);
     F[D + 1] = frho * (half * vv + iLb * (T)(1.0 / (kGamma - 1.0))) + work;
-}
-
-// The same with the means computed here.
-template <class M, int D, int FLUX>
-__device__ __forceinline__ void euler_pair_flux(const EulerNode<typename M::T, typename M::TJ, D> &A,
-                                                const EulerNode<typename M::T, typename M::TJ, D> &B,
-                                                typename M::T F[D + 2]) {
-    typename M::T Lr, iLb;
-    if constexpr (M::mixed) {
-        mixed_means<M, D>(A, B, Lr, iLb);
-    } else {
-        Lr = ln_mean(A.rho, B.rho);
-        iLb = inv_ln_mean(A.beta, B.beta);
-    }
-    euler_pair_flux_lm<M, D, FLUX>(A, B, Lr, iLb, F);
 }
 
 // FP64 pair flux: the node carries v/2 (hv) and FP32 copies of rho and beta
@@ -385,30 +369,12 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
                     if constexpr (M::mixed) nd[a].beta_d = sBd[i];
                     else nd[a].beta_d = 0.0;
                 }
-                // mixed mode, n <= 5: all the line's logarithmic means first
-                // (independent FP64 chains the scheduler can overlap: the
-                // FP64 arithmetic is latency-bound), then the FP32 fluxes
-                constexpr bool kMeansFirst = M::mixed && N <= 5;
-                constexpr int NPAIR = N * (N - 1) / 2;
-                float Lm[kMeansFirst ? NPAIR : 1], Im[kMeansFirst ? NPAIR : 1];
-                if constexpr (kMeansFirst) {
-                    int k = 0;
-#pragma unroll
-                    for (int a = 0; a < N; ++a)
-#pragma unroll
-                        for (int b = a + 1; b < N; ++b, ++k) mixed_means<M, D>(nd[a], nd[b], Lm[k], Im[k]);
-                }
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
 #pragma unroll
                     for (int b = a + 1; b < N; ++b) {
                         T F[D + 2];
-                        if constexpr (kMeansFirst) {
-                            const int k = a * N - a * (a + 1) / 2 + (b - a - 1);
-                            euler_pair_flux_lm<M, D, FLUX>(nd[a], nd[b], Lm[k], Im[k], F);
-                        } else {
-                            euler_pair_flux<M, D, FLUX>(nd[a], nd[b], F);
-                        }
+                        euler_pair_flux<M, D, FLUX>(nd[a], nd[b], F);
                         const T qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
 #pragma unroll
                         for (int v = 0; v < NVAR; ++v) { acc[a][v].add_prod(qab, F[v]); acc[b][v].add_prod(qba, F[v]); }
