@@ -66,6 +66,14 @@ def pairs_per_element(d: int, p: int) -> int:
     return d * n ** (d - 1) * n * (n - 1) // 2
 
 
+def surface_fluxes_per_element(d: int, p: int, kind: int) -> int:
+    """Two-point fluxes of the surface Hadamard product of one element: each
+    of the 2d faces' n^(d-1) nodes meets the nonzeros of its interpolation
+    row (one on Gauss-Lobatto nodes, n on Gauss nodes)."""
+    n = p + 1
+    return 2 * d * n ** (d - 1) * (1 if kind == 0 else n)
+
+
 def bytes_per_node(prec: str, d: int = 3) -> int:
     """Algorithmic HBM bytes per node: read u and Ja, write r."""
     nvar = d + 2
@@ -732,7 +740,7 @@ def main():
                 A.sfh_surface_hadamard(cs.handle, tsu.shape[0], tsu.data_ptr(), tsf.data_ptr(), tsj.data_ptr(),
                                        srv.data_ptr(), srf.data_ptr(), sh)
             _, ts = timed_launches(steps, k64, 2, stream, torch)
-            fluxes = 2 * 3 * 25 * (1 if knd == 0 else 5) * su.shape[0]
+            fluxes = surface_fluxes_per_element(3, 4, knd) * su.shape[0]
             sf[kname] = {"ms": ts, "element_dof_per_s": su.shape[0] * 125 / (ts * 1e-3),
                          "two_point_fluxes_per_launch": fluxes,
                          "alu_frac_of_fp64_rate": fluxes * PAIR_FLOPS / (ts * 1e-3) / 1.25e12}

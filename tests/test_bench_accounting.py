@@ -46,3 +46,22 @@ def test_flops_per_element_composition():
     assert bench.flops_per_element(d, p, 0) == expected
     # Gauss: a diagonal term at every node of every line
     assert bench.flops_per_element(d, p, 1) - bench.flops_per_element(d, p, 0) == lines * (n - 2) * bench.GAMMA_DIAG
+
+
+@pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 4, 1), (2, 3, 1), (3, 7, 1), (2, 6, 0)])
+def test_surface_fluxes_match_interpolation_nonzeros(d, p, kind):
+    """The surface product's flux count against the nonzeros of the face
+    interpolation rows l_b(-1), l_b(+1) (numpy polynomial fit through the
+    nodes; Gauss-Lobatto rows are selectors, Gauss rows dense)."""
+    import oracle as O
+    n = p + 1
+    xi, w = np.zeros(n), np.zeros(n)
+    O._check(O._load().orc_nodes(p, kind, O._p(xi), O._p(w)))
+    nnz = 0
+    for b in range(n):
+        y = np.zeros(n)
+        y[b] = 1.0
+        c = np.polynomial.polynomial.polyfit(xi, y, p)
+        for x in (-1.0, 1.0):
+            nnz += abs(np.polynomial.polynomial.polyval(x, c)) > 1e-10
+    assert bench.surface_fluxes_per_element(d, p, kind) == d * n ** (d - 1) * nnz
