@@ -233,12 +233,15 @@ sfh_status sfh_volume_residual_host(sfh_ctx *ctx, int64_t n_elem, const void *u_
  * cudaFree or allocating routine.
  * Limit: 256 + 2 * round256(bytes(u)) + round256(bytes(Ja)) <= 64 MiB (for 3D
  * Euler p = 4: about 4,790 elements in FP32, 3,530 in FP64); larger
- * requests return SFH_EINVAL with the limit in sfh_last_error().
+ * requests return SFH_EINVAL with the limit in sfh_last_error().  The
+ * element count is compared with that limit before any byte count is formed,
+ * so no n_elem (up to INT64_MAX) can wrap the size check.
  * The array keeps the last call's contents (the error word is cleared at the
  * start of each call); calls that overlap on the GPU -- from two host threads
  * or on two streams -- race on it and must be serialized by the caller.  The
  * first call on a device looks up the array's device address (once per
- * device, with that device current).  Synchronous: returns when r_host is
+ * device, with that device current); make that first call before any
+ * stream capture.  Synchronous: returns when r_host is
  * filled.  Errors: SFH_EINVAL, SFH_ECUDA, SFH_EDOMAIN, SFH_ETIMEOUT. */
 sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes nodes, sfh_flux flux, int64_t n_elem,
                                             const void *u_host, const double *Ja_host, void *r_host,

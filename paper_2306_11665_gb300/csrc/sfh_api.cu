@@ -206,6 +206,27 @@ extern "C" sfh_status sfh_operator_tables(int p, sfh_nodes nodes, double *xi, do
     return SFH_OK;
 }
 
+namespace sfh {
+bool op_tables(int p, int nodes, OpTab<double> &tab_d, OpTab<float> &tab_f) {
+    memset(&tab_d, 0, sizeof tab_d);
+    memset(&tab_f, 0, sizeof tab_f);
+    if (p < 1 || p > NMAX - 1 || (nodes != SFH_NODES_GLL && nodes != SFH_NODES_GAUSS)) return false;
+    long double x[NMAX], ww[NMAX], DD[NMAX * NMAX];
+    if (!make_tables(p, nodes, x, ww, DD)) return false;
+    const int n = p + 1;
+    for (int a = 0; a < n; ++a) {
+        tab_d.w[a] = (double)ww[a];
+        tab_f.w[a] = (float)ww[a];
+        for (int b = 0; b < n; ++b) {
+            const long double q = ww[a] * DD[a * n + b];
+            tab_d.Q1[a * n + b] = (double)q;
+            tab_f.Q1[a * n + b] = (float)q;
+        }
+    }
+    return true;
+}
+}  // namespace sfh
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------
@@ -297,19 +318,9 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
     }
     c->stage_bytes = 0;
     const int n = p + 1;
-    memset(&c->tab_d, 0, sizeof c->tab_d);
-    memset(&c->tab_f, 0, sizeof c->tab_f);
+    sfh::op_tables(p, nodes, c->tab_d, c->tab_f);
     long double x[sfh::NMAX], ww[sfh::NMAX], DD[sfh::NMAX * sfh::NMAX];
     make_tables(p, nodes, x, ww, DD);
-    for (int a = 0; a < n; ++a) {
-        c->tab_d.w[a] = (double)ww[a];
-        c->tab_f.w[a] = (float)ww[a];
-        for (int b = 0; b < n; ++b) {
-            const long double q = ww[a] * DD[a * n + b];
-            c->tab_d.Q1[a * n + b] = (double)q;
-            c->tab_f.Q1[a * n + b] = (float)q;
-        }
-    }
     for (int b = 0; b < 3; ++b) {
         long double VV[sfh::NMAX * sfh::NMAX];
         memset(&c->basis_d[b], 0, sizeof c->basis_d[b]);

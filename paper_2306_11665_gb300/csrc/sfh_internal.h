@@ -133,6 +133,13 @@ inline cudaError_t (*vjp_fn(int d, int flux))(int, int, const double *, const do
     return d == 3 ? vjp_d3 : vjp_d2;
 }
 
+// Operator tables of degree p on node set `nodes` (SFH_NODES_*): w and
+// Q1 = diag(w) D (Eq. 5), each entry rounded once from the long-double
+// construction to the table's type.  False for p or nodes out of range.
+// Shared by the contexts and the context-free entry points, so that both
+// compute with the same FP32 and FP64 values.
+bool op_tables(int p, int nodes, OpTab<double> &tab_d, OpTab<float> &tab_f);
+
 // Set the calling thread's message returned by sfh_last_error().
 void set_error_message(const char *msg);
 

@@ -82,39 +82,34 @@ extern "C" sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes n
     const int n = p + 1, nvar = flux == SFH_FLUX_BURGERS ? 1 : d + 2;
     const size_t nn = (size_t)sfh::ipow(n, d);
     const size_t esz = prec == SFH_FP64 ? 8 : 4;
+    // bytes per element (u and r, plus Ja) and the largest element count that
+    // fits, found before any product with n_elem so that no size can wrap
+    const size_t per_elem = 2 * nvar * nn * esz + d * d * nn * sizeof(double);
+    const int64_t max_elem = (int64_t)((SFH_NOALLOC_SCRATCH_BYTES - 256 - 3 * 255) / per_elem);
+    if (n_elem > max_elem)
+        return na_fail(SFH_EINVAL,
+                       "n_elem %lld exceeds the no-allocation entry point's staging array of %u bytes "
+                       "(at most %lld elements of this type)",
+                       (long long)n_elem, SFH_NOALLOC_SCRATCH_BYTES, (long long)max_elem);
     const size_t ub = (size_t)n_elem * nvar * nn * esz, jb = (size_t)n_elem * d * d * nn * sizeof(double);
     const size_t need = 256 + 2 * up256(ub) + up256(jb);
-    if (need > SFH_NOALLOC_SCRATCH_BYTES)
-        return na_fail(SFH_EINVAL,
-                       "n_elem %lld needs %zu bytes of device staging; the no-allocation entry point holds %u "
-                       "(at most %lld elements of this type)",
-                       (long long)n_elem, need, SFH_NOALLOC_SCRATCH_BYTES,
-                       (long long)((SFH_NOALLOC_SCRATCH_BYTES - 256 - 3 * 255) /
-                                   (2 * nvar * nn * esz + d * d * nn * sizeof(double))));
+    if (need > SFH_NOALLOC_SCRATCH_BYTES)   // cannot happen after the element cap; kept as a guard
+        return na_fail(SFH_EINVAL, "n_elem %lld needs %zu bytes of device staging; the array holds %u",
+                       (long long)n_elem, need, SFH_NOALLOC_SCRATCH_BYTES);
 
-    // operator tables on the host stack (no context)
-    double xi[sfh::NMAX], w[sfh::NMAX], D[sfh::NMAX * sfh::NMAX], Q1[sfh::NMAX * sfh::NMAX];
-    sfh_status st = sfh_operator_tables(p, nodes, xi, w, D, Q1);
-    if (st != SFH_OK) return st;
+    // operator tables on the host stack (no context), rounded as a context
+    // rounds them
     sfh::OpTab<double> tab_d;
     sfh::OpTab<float> tab_f;
-    memset(&tab_d, 0, sizeof tab_d);
-    memset(&tab_f, 0, sizeof tab_f);
-    for (int a = 0; a < n; ++a) {
-        tab_d.w[a] = w[a];
-        tab_f.w[a] = (float)w[a];
-        for (int b = 0; b < n; ++b) {
-            tab_d.Q1[a * n + b] = Q1[a * n + b];
-            tab_f.Q1[a * n + b] = (float)Q1[a * n + b];
-        }
-    }
+    if (!sfh::op_tables(p, nodes, tab_d, tab_f)) return na_fail(SFH_EINVAL, "bad node set %d", (int)nodes);
 
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(SFH_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= SFH_NOALLOC_MAX_DEVICES) return na_fail(SFH_EUNSUPPORTED, "device index %d", dev);
     unsigned char *base = nullptr;
-    if ((st = scratch_address(dev, &base)) != SFH_OK) return st;
+    const sfh_status st = scratch_address(dev, &base);
+    if (st != SFH_OK) return st;
     int *d_err = reinterpret_cast<int *>(base);
     unsigned char *du = base + 256;
     unsigned char *dj = du + up256(ub);

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace sfh {
 
 constexpr int kMaxDevices = 64;  // launch facts are cached per device index below this
@@ -87,26 +89,34 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 // SM count of the current device and resident CTAs per SM of a persistent
 // kernel, asked of the runtime once per device (the kernel's dynamic
 // shared-memory limit is raised on that device at the same time) and cached
-// in the caller's per-device arrays.
+// per device.  Both numbers live in one atomic word, (sms << 8) | per_sm,
+// published with a release store and read with an acquire load, so that a
+// thread that sees the word also sees both numbers (the host may be a weakly
+// ordered Arm machine).  Two threads that race on the first call both ask the
+// runtime and store the same word.
+struct LaunchCache {
+    std::atomic<int> packed[kMaxDevices];
+};
+
 template <typename Kern>
-inline cudaError_t persistent_slots(Kern kern, int threads, size_t smem, int *cache_per_sm, int *cache_sms,
-                                    int &per_sm, int &sms) {
+inline cudaError_t persistent_slots(Kern kern, int threads, size_t smem, LaunchCache &cache, int &per_sm, int &sms) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (cache_per_sm[dev] == 0) {
+    int word = cache.packed[dev].load(std::memory_order_acquire);
+    if (word == 0) {
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
         int n = 0, k = 0;
         if ((e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
         if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kern, threads, smem)) != cudaSuccess) return e;
-        if (k < 1) return cudaErrorInvalidConfiguration;
-        cache_sms[dev] = n;
-        cache_per_sm[dev] = k;
+        if (k < 1 || k > 255 || n < 1 || n > (1 << 22)) return cudaErrorInvalidConfiguration;
+        word = (n << 8) | k;
+        cache.packed[dev].store(word, std::memory_order_release);
     }
-    per_sm = cache_per_sm[dev];
-    sms = cache_sms[dev];
+    per_sm = word & 255;
+    sms = word >> 8;
     return cudaSuccess;
 }
 

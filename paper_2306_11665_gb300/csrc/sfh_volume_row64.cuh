@@ -285,9 +285,9 @@ cudaError_t launch_volume_fp64_row(const void *u, const double *Ja, void *r, int
                                    int *err, cudaStream_t stream) {
     using S = Row64Shape<N>;
     auto kern = volume_fp64_row_kernel<N>;
-    static int cache_per_sm[kMaxDevices], cache_sms[kMaxDevices];
+    static LaunchCache cache;
     int per_sm = 0, sms = 0;
-    const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
+    const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache, per_sm, sms);
     if (e0 != cudaSuccess) return e0;
     const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
     const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;

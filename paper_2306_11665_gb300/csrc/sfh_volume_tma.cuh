@@ -654,21 +654,21 @@ cudaError_t launch_volume_fp32_tma(const void *u, const double *Ja, void *r, int
                                    int *err, cudaStream_t stream, const BasisTab<float> *bt = nullptr) {
     using S = TmaShape<D, N, FLUX>;
     static_assert(S::SMEM <= 227 * 1024, "shared memory");
-    static int cache_per_sm[kMaxDevices], cache_sms[kMaxDevices];
+    static LaunchCache cache;
     int per_sm = 0, sms = 0;
     const int aligned = ((reinterpret_cast<uintptr_t>(u) | reinterpret_cast<uintptr_t>(Ja) |
                           reinterpret_cast<uintptr_t>(r)) & 15) == 0;
     const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
     if constexpr (MODAL) {
         auto kern = volume_fp32_tma_modal_kernel<D, N, FLUX>;
-        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
+        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache, per_sm, sms);
         if (e0 != cudaSuccess) return e0;
         const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
         kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja,
                                                              static_cast<float *>(r), n_elem, tab, err, aligned, *bt);
     } else {
         auto kern = volume_fp32_tma_kernel<D, N, FLUX>;
-        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache_per_sm, cache_sms, per_sm, sms);
+        const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache, per_sm, sms);
         if (e0 != cudaSuccess) return e0;
         const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
         kern<<<(unsigned)grid, S::THREADS, S::SMEM, stream>>>(static_cast<const float *>(u), Ja,

@@ -84,3 +84,21 @@ def test_basis_table_matches_the_oracle(A):
     with pytest.raises(A.SfhError) as e:
         A.sfh_basis_table(4, 0, 3)
     assert e.value.status == A.SFH_EINVAL
+
+
+@pytest.mark.parametrize("n_elem", [1 << 62, (1 << 63) - 1, 1 << 40, 1 << 24])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_noalloc_refuses_huge_element_counts_before_any_device_call(A, n_elem, prec):
+    """The allocation-free entry point caps the element count before any
+    product with it (a byte count that wraps would otherwise pass the size
+    check): the refusal is SFH_EINVAL with the cap in the message, and it comes
+    before any CUDA call (on this machine without a GPU a CUDA call would give
+    another status)."""
+    u = np.zeros(16)
+    Ja = np.zeros(16)
+    r = np.zeros(16)
+    st = A.lib().sfh_volume_residual_host_noalloc(3, 4, 0, A.SFH_FLUX_EULER_RANOCHA, n_elem, u.ctypes.data,
+                                                   Ja.ctypes.data, r.ctypes.data, prec, None)
+    assert st == A.SFH_EINVAL
+    msg = A.sfh_last_error()
+    assert "at most" in msg and "elements" in msg
