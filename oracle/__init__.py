@@ -61,7 +61,7 @@ def _load():
         lib.orc_logmean_grad.restype = None
         lib.orc_ec_flux.argtypes = [i, i, dp, dp, dp, dp]
         lib.orc_ec_flux_jac1.argtypes = [i, i, dp, dp, dp, dp]
-        for name in ("orc_volume_sf", "orc_volume_dense"):
+        for name in ("orc_volume_sf", "orc_volume_dense", "orc_volume_absterms"):
             getattr(lib, name).argtypes = [i, i, i, i, i, L, dp, dp, dp]
         for name in ("orc_vjp_sf", "orc_vjp_dense"):
             getattr(lib, name).argtypes = [i, i, i, i, i, L, dp, dp, dp, dp]
@@ -158,6 +158,13 @@ def _volume(fn, d, p, kind, flux, u, Ja, allow_domain=False):
 def volume_sf(d, p, kind, flux, u, Ja, allow_domain=False) -> np.ndarray:
     """Sum-factorized residual r[e][var][i] (Eq. 3 with the Eq. 5 operators)."""
     return _volume(_load().orc_volume_sf, d, p, kind, flux, u, Ja, allow_domain)
+
+
+def volume_absterms(d, p, kind, flux, u, Ja) -> np.ndarray:
+    """S[e][var][i] = sum_m sum_j |Q_m,ij F_m,ij,var| (the terms of Eq. 3 with
+    the Eq. 5 operators in absolute value): the magnitude each residual entry
+    cancels from, the scale of its rounding errors in floating point."""
+    return _volume(_load().orc_volume_absterms, d, p, kind, flux, u, Ja)
 
 
 def volume_dense(d, p, kind, flux, u, Ja) -> np.ndarray:

@@ -435,6 +435,45 @@ int orc_volume_sf(int d, int p, int kind, int nvar, int flux, long n_elem,
     return st;
 }
 
+/* Sum of the absolute terms of the sum-factorized residual (Eq. 3 with     */
+/* Eq. 5), S_i = sum_m sum_j |omega_m(i) Q1[a_m(i)][a_m(j)] F_m(u_i, u_j)|    */
+/* per variable: the magnitude the residual cancels from.  Test             */
+/* infrastructure: rounding errors of a floating-point evaluation of r_i    */
+/* scale with S_i, not with |r_i|.                                          */
+int orc_volume_absterms(int d, int p, int kind, int nvar, int flux, long n_elem,
+                        const double *u, const double *Ja, double *S)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), st = 0;
+    double xi[16], w[16], D[256], Q1[256];
+    orc_op1d(p, kind, xi, w, D, Q1);
+    for (long e = 0; e < n_elem; ++e) {
+        const double *ue = u + e * nvar * nn;
+        const double *Je = Ja + e * d * d * nn;
+        double *se = S + e * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) se[q] = 0.0;
+        for (int m = 0; m < d; ++m) {
+            for (int i = 0; i < nn; ++i) {
+                int ai[3]; node_to_multi(i, n, d, ai);
+                double omega = 1.0;
+                for (int k = 0; k < d; ++k) if (k != m) omega *= w[ai[k]];
+                double ui[5];
+                for (int v = 0; v < nvar; ++v) ui[v] = ue[v * nn + i];
+                for (int b = 0; b < n; ++b) {
+                    int aj[3]; memcpy(aj, ai, sizeof aj); aj[m] = b;
+                    int j = multi_to_node(aj, n, d);
+                    double uj[5], nv[3], F[5];
+                    for (int v = 0; v < nvar; ++v) uj[v] = ue[v * nn + j];
+                    for (int k = 0; k < d; ++k) nv[k] = Je[(m * d + k) * nn + i] + Je[(m * d + k) * nn + j];
+                    st |= orc_ec_flux(d, flux, ui, uj, nv, F);
+                    for (int v = 0; v < nvar; ++v) se[v * nn + i] += fabs(omega * Q1[ai[m] * n + b] * F[v]);
+                }
+            }
+        }
+    }
+    return st;
+}
+
 /* Volume residual, dense (Eq. 1): the full n^d x n^d operators Q_m and the
  * two-point flux over ALL node pairs (i, j), r_i = sum_m sum_j Q_m[i][j] F_m(u_i, u_j).
  * O(n^{2d}) per element: the brute-force form the sum-factorized one replaces. */

@@ -214,3 +214,29 @@ def test_p6_lgl_boundary_entropy_flux_form():
             gcl += np.einsum("ki,ij,kj->", psi, Q, J)
         assert abs(lhs - bnd - gcl) <= 1e-13 * scale
         assert abs(gcl) <= 1e-12 * scale
+
+
+# ----------------------------------------------- absolute terms (error scale)
+@pytest.mark.parametrize("d, flux, kind, p", [(3, O.FLUX_EULER, GLL, 2), (3, O.FLUX_EULER, GAUSS, 3),
+                                              (2, O.FLUX_BURGERS, GLL, 3), (2, O.FLUX_EULER, GAUSS, 2)])
+def test_absterms_against_dense_brute_force(d, flux, kind, p):
+    """S_i = sum_m sum_j |Q_m,ij F_m,ij| from the full Kronecker matrices and
+    a flux evaluation of every (i, j) pair (a path that shares no loop with
+    the sum-factorized routine), and S >= |r| by the triangle inequality."""
+    u, Ja = I.workload(d, p, kind, 2, flux="burgers" if flux == O.FLUX_BURGERS else "euler")
+    u, Ja = u[:2], Ja[:2]
+    S = O.volume_absterms(d, p, kind, flux, u, Ja)
+    nn = u.shape[2]
+    ref = np.zeros_like(u)
+    for e in range(u.shape[0]):
+        for m in range(d):
+            Q = _kron_q(d, p, kind, m)
+            for i in range(nn):
+                for j in range(nn):
+                    if Q[i, j] == 0.0:
+                        continue
+                    F = O.ec_flux(d, flux, u[e, :, i], u[e, :, j], Ja[e, m, :, i] + Ja[e, m, :, j])
+                    ref[e, :, i] += np.abs(Q[i, j] * F)
+    assert _rel(S, ref) <= 1e-14
+    r = O.volume_sf(d, p, kind, flux, u, Ja)
+    assert np.all(S >= np.abs(r) * (1 - 1e-14))
