@@ -38,12 +38,50 @@ METRIC = "element-DOF/s of 3D Euler volume residual"
 GAMMA_DIAG = 30          # algorithmic flops of one diagonal (physical-flux) term incl. accumulation
 PAIR_FLOPS = 92          # algorithmic flops of one off-diagonal pair (see flops_per_element)
 NODE_FLOPS = 13          # conservative -> primitive per node
-# FP64 flops of one pair in the mixed mode (both log means inside the near-equal
-# band, where the mixed mode evaluates them in FP64; band tests and series
-# tails in FP32): metric sum 3; each mean: difference and sum 2, one Newton
-# step of the reciprocal 4, quotient and square 2, series 4 + 2, scaling 2
-# -> 16.
+# FP64 work of the mixed mode.  The thread-per-line kernel (2D, n = 2, 7..9,
+# the modal path): both log means inside the band in FP64 (difference and sum
+# 2, one Newton step of the reciprocal 4, quotient and square 2, series 4 + 2,
+# scaling 2 -> 16 flops each) and the FP64 metric sum (3): 35 flops per pair.
 MIX_PAIR_FP64_FLOPS = 35
+# The warp-specialized kernel (3D Euler, n = 3..6): FP64 only where FP32
+# would lose accuracy -- metric pair sums (3 DADD), the rho mean's sum and
+# scaling (DADD, DMUL), the beta mean's sum, reciprocal Newton step and
+# scaling (DADD, 2 DFMA, DMUL): 9 FP64 instructions, 11 flops (FMA = 2) per
+# pair; per node beta = rho / p in FP64 (2 DFMA, DMUL: 3 instructions, 5 flops).
+MIX_WS_PAIR_FP64 = (11, 9)    # (flops, instructions)
+MIX_WS_NODE_FP64 = (5, 3)
+FP64_TFLOPS = 1.25             # nominal FP64 rate of the recipe table (2 DFMA per clock per SM)
+FP32_LANE_OPS = 152 * 128 * 2.07e9   # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz, one operation per lane
+
+
+def mix_fp64_work(d: int, p: int, kind: int):
+    """(FP64 flops, FP64 instructions) of one element's mixed-mode residual,
+    per the kernel the library launches for (d, p)."""
+    n = p + 1
+    pairs = pairs_per_element(d, p)
+    if d == 3 and 3 <= n <= 6:
+        return (pairs * MIX_WS_PAIR_FP64[0] + n ** d * MIX_WS_NODE_FP64[0],
+                pairs * MIX_WS_PAIR_FP64[1] + n ** d * MIX_WS_NODE_FP64[1])
+    return pairs * MIX_PAIR_FP64_FLOPS, pairs * MIX_PAIR_FP64_FLOPS   # FMA-free count
+
+
+def fp32_pipe_ops_per_element(d: int, p: int, kind: int) -> float:
+    """FP32-pipe operations of one element's FP32-Kahan residual of 3D Euler,
+    counted from the formula as the kernels evaluate it (add, mul, fma one
+    operation each; the reciprocals run on the special-function unit):
+      pair: metric sum 3, v.n_a, v.n_b, v_a.v_b 9, both log means (difference,
+            sum, quotient, square, three-term series, scaling) 16, mass flux 2,
+            mean pressure 2, pressure work 2, momentum 9, energy 2, the ten
+            compensated (Kahan) accumulations 40 -> 86;
+      diagonal term (only where Q1[a][a] != 0): physical flux 30 + Kahan 20;
+      per node: primitives 25, omega scaling and compensated values 10,
+            direction sums 2 per variable."""
+    n = p + 1
+    lines = d * n ** (d - 1)
+    # nonzero diagonal entries of Q1: the endpoints on Gauss-Lobatto nodes;
+    # every node on Gauss nodes but the middle one of an odd count (x = 0)
+    ndiag = 2 if kind == 0 else n - n % 2
+    return pairs_per_element(d, p) * 86 + lines * ndiag * 50 + n ** d * (25 + 10 + 2 * (d + 2))
 
 
 def flops_per_element(d: int, p: int, kind: int) -> float:
@@ -98,7 +136,7 @@ TRAFFIC = {
 # The sources that define the timed kernels' code: the persistent FP32 kernel
 # and its building blocks, and the instantiation unit; with the compiler flags.
 # (Other files of the library hold only other kernels and host code.)
-KERNEL_SOURCES = ("sfh_volume_tma.cuh", "sfh_tma.cuh", "sfh_device.cuh", "sfh_inst.cu")
+KERNEL_SOURCES = ("sfh_volume_ws.cuh", "sfh_volume_tma.cuh", "sfh_tma.cuh", "sfh_device.cuh", "sfh_inst.cu")
 
 
 def _kernel_sources_sha1():
@@ -125,6 +163,30 @@ def measured_counters(prec, p, kind, N):
     if rec and rec["sha1"] == _kernel_sources_sha1() and "counters" in rec:
         return rec["counters"]
     return None
+
+
+def fp32_kernel_name(d: int, p: int, modal: bool = False) -> str:
+    """The kernel the library launches for the FP32-Kahan residual of 3D Euler."""
+    n = p + 1
+    if modal:
+        return "volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, n)
+    if d == 3 and n in (7, 8):
+        return "volume_fp32_row_kernel<%d>" % n
+    if d == 3 and 3 <= n <= 6:
+        return "volume_fp32_ws_kernel<%d,%d,euler>" % (d, n)
+    return "volume_fp32_tma_kernel<%d,%d,euler>" % (d, n)
+
+
+def fp32_roofline(d, p, kind, E, ms, hbm_peak):
+    """The binding roofline of an FP32-Kahan residual (3D Euler), as the
+    larger of the HBM time (algorithmic bytes / measured copy bandwidth) and
+    the FP32-pipe time (formula operations / 152 x 128 lanes x 2.07 GHz)."""
+    nn = (p + 1) ** d
+    t_hbm = bytes_per_node("fp32k", d) * nn * E / (hbm_peak * 1e9)
+    t_alu = fp32_pipe_ops_per_element(d, p, kind) * E / FP32_LANE_OPS
+    t = ms * 1e-3
+    return {"bound": "hbm" if t_hbm >= t_alu else "alu", "t_hbm_ms": t_hbm * 1e3, "t_fp32_pipe_ms": t_alu * 1e3,
+            "frac": max(t_hbm, t_alu) / t, "hbm_frac": t_hbm / t, "fp32_pipe_frac": t_alu / t}
 
 
 def load_peaks():
@@ -277,8 +339,12 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
     in {2..8} (Gauss-Lobatto), 70% FP32 / 30% FP64 residuals (a vjp_share of
     them VJPs instead), states and metrics resident, 40 GB admission budget.
     Capacity = all requests released at once; then Poisson arrivals at the given
-    fractions of capacity; p50/p99 latency = submit -> done.  Baseline: the same
-    requests as serial single-request FP64 launches."""
+    fractions of capacity; p50/p99 latency = submit -> done, split at the
+    device start of the first tile into queueing and execution.  Baselines at
+    every load: the same arrival trace through a FIFO of plain single-request
+    launches on one stream (FP64, and each request's own precision), queueing
+    included; and, without arrivals, the requests one at a time (service
+    times only)."""
     from paper_2306_11665_gb300.serve import Server
     rng = np.random.default_rng(seed)
     dev = torch.device("cuda")
@@ -297,6 +363,8 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
         specs.append((ne, p, prec, vjp))
     outs = []
     reqs = []
+    reqs64 = []   # the same requests as FP64 launches (the plain single-launch FP64 form)
+    o64s = []
     dof = 0
     for ne, p, prec, vjp in specs:
         P = pools[p]
@@ -305,6 +373,12 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
         outs.append(out)
         reqs.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, 0, prec, ne, u.data_ptr(),
                               P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None, out.data_ptr()))
+        o64 = out if u.dtype == torch.float64 else torch.empty((ne,) + tuple(u.shape[1:]), dtype=torch.float64,
+                                                               device=dev)
+        o64s.append(o64)
+        reqs64.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, 0, A.SFH_FP64, ne,
+                                P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None,
+                                o64.data_ptr()))
         dof += ne * (p + 1) ** 3
     res = {"requests": n_req, "dof_total": dof, "vjp_share": vjp_share}
     with Server(hbm_budget_bytes=40 << 30, max_inflight=64, timeout_ms=120000) as srv:
@@ -330,10 +404,24 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
             r = A.sfh_serve_replay(srv.handle, reqs, arr.tolist(), 120000)
             assert all(x.status == A.SFH_OK for x in r)
             lat = np.array([(x.t_done_ns - x.t_submit_ns) * 1e-6 for x in r])
+            queue = np.array([(x.t_start_ns - x.t_submit_ns) * 1e-6 for x in r])   # until the first tile ran
+            run = np.array([(x.t_done_ns - x.t_start_ns) * 1e-6 for x in r])
             span_l = (max(x.t_done_ns for x in r) - min(x.t_submit_ns for x in r)) * 1e-9
-            res[f"load_{int(load * 100)}"] = {"p50_ms": float(np.percentile(lat, 50)),
-                                              "p99_ms": float(np.percentile(lat, 99)),
-                                              "dof_per_s": dof / span_l, "offered_req_per_s": rate}
+            entry = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "queue_p50_ms": float(np.percentile(queue, 50)), "queue_p99_ms": float(np.percentile(queue, 99)),
+                     "exec_p50_ms": float(np.percentile(run, 50)), "exec_p99_ms": float(np.percentile(run, 99)),
+                     "dof_per_s": dof / span_l, "offered_req_per_s": rate}
+            # like for like: the same arrival trace through a FIFO of plain
+            # single-request launches on one stream (queueing included), as
+            # FP64 launches and in each request's own precision
+            for name, rq in (("serial_fp64_fifo", reqs64), ("serial_own_precision_fifo", reqs)):
+                f = A.sfh_serial_replay(rq, arr.tolist(), 120000)
+                assert all(x.status == A.SFH_OK for x in f)
+                fl = np.array([(x.t_done_ns - x.t_submit_ns) * 1e-6 for x in f])
+                fspan = (max(x.t_done_ns for x in f) - min(x.t_submit_ns for x in f)) * 1e-9
+                entry[name] = {"p50_ms": float(np.percentile(fl, 50)), "p99_ms": float(np.percentile(fl, 99)),
+                               "dof_per_s": dof / fspan}
+            res[f"load_{int(load * 100)}"] = entry
     # serial single-request FP64 launches of the same stream
     ctxs = {p: api.Context(3, p, "gll", "euler") for p in range(2, 9)}
     stream = torch.cuda.current_stream()
@@ -394,6 +482,27 @@ def timed_launches(fn, steps, warmup, stream, torch):
     return total, sum(per) / len(per)
 
 
+def timed_region(step, steps, warmup, dist, barrier_sync, timer, device=None):
+    """The timed region of the contract: `warmup` untimed steps, then exactly
+    `steps` steps bracketed by a barrier and a device synchronize on both
+    sides; the duration is the MAX over ranks.  `timer(step, steps)` returns
+    (total_ms, mean_launch_ms) of this rank (CUDA events on the launching
+    stream on the GPU); `barrier_sync()` synchronizes the device.  Returns
+    (max-over-ranks total_ms, this rank's mean launch ms)."""
+    from paper_2306_11665_gb300 import dist as D
+    for _ in range(warmup):
+        step()
+    barrier_sync()
+    if dist:
+        dist.barrier()
+    t_total, t_launch = timer(step, steps)
+    barrier_sync()
+    if dist:
+        dist.barrier()
+        t_total = D.max_over_ranks(t_total, dist, device)
+    return t_total, t_launch
+
+
 def entropy_defect_max(torch, ctx, tu64, tJ, r):
     """Largest per-element defect of the entropy identity of residual r, over
     the whole mesh (FP64, on the GPU: sfh_entropy_residual)."""
@@ -402,9 +511,9 @@ def entropy_defect_max(torch, ctx, tu64, tJ, r):
 
 def other_configs(torch, A, I, api, stream, hbm_peak):
     """The precision study (3D Euler, p = 7, Gauss, 16^3 warped) in the three
-    precision modes, and the adjoint configuration (p = 5, Gauss-Lobatto,
-    8^3 warped) with its forward residual: device-resident inputs, CUDA-event
-    mean launch times."""
+    precision modes, the 2D Burgers configuration (p = 3, 8 x 8 affine, FP64)
+    and the adjoint configuration (p = 5, Gauss-Lobatto, 8^3 warped) with its
+    forward residual: device-resident inputs, CUDA-event mean launch times."""
     out = {}
     sh = stream.cuda_stream
     dev = torch.device("cuda")
@@ -426,12 +535,28 @@ def other_configs(torch, A, I, api, stream, hbm_peak):
         res[name] = {"ms": ms, "element_dof_per_s": dof / (ms * 1e-3),
                      "entropy_identity_defect_max": entropy_defect_max(torch, ctx, t64, tJ, tr)}
     res["fp32k"]["hbm_frac_of_measured"] = b32 / (res["fp32k"]["ms"] * 1e-3) / 1e9 / hbm_peak
-    res["fp64"]["alu_frac_of_fp64_rate"] = fl / (res["fp64"]["ms"] * 1e-3) / 1.25e12
-    flm = pairs_per_element(3, 7) * MIX_PAIR_FP64_FLOPS * E
-    res["fp32mix"]["alu_frac_of_fp64_rate"] = flm / (res["fp32mix"]["ms"] * 1e-3) / 1.25e12
+    res["fp32k"]["roofline"] = fp32_roofline(3, 7, 1, E, res["fp32k"]["ms"], hbm_peak)
+    res["fp64"]["alu_frac_of_fp64_rate"] = fl / (res["fp64"]["ms"] * 1e-3) / (FP64_TFLOPS * 1e12)
+    flm, _ = mix_fp64_work(3, 7, 1)
+    res["fp32mix"]["alu_frac_of_fp64_rate"] = flm * E / (res["fp32mix"]["ms"] * 1e-3) / (FP64_TFLOPS * 1e12)
     assert ctx.check() == A.SFH_OK
     out["euler3d_p7_gauss_16cubed_warped"] = res
     ctx.close()
+
+    # 2D Burgers, p = 3 Gauss-Lobatto, 8 x 8 affine elements on [0, 1]^2, FP64:
+    # 64 elements, 1,024 nodes, 24 KB of inputs (L2-resident); one launch
+    # covers a fraction of one wave, so the time is the launch latency
+    ub, Jb = I.workload(2, 3, 0, 8, flux="burgers", amp=0.0)
+    cb = api.Context(2, 3, "gll", "burgers")
+    tub, tJb = torch.from_numpy(ub).to(dev), torch.from_numpy(Jb).to(dev)
+    trb = torch.empty_like(tub)
+    _, tb = timed_launches(lambda: A.sfh_volume_residual(cb.handle, ub.shape[0], tub.data_ptr(), tJb.data_ptr(),
+                                                         trb.data_ptr(), A.SFH_FP64, sh), 200, 10, stream, torch)
+    assert cb.check() == A.SFH_OK
+    out["burgers2d_p3_gll_8x8_affine"] = {
+        "fp64": {"ms": tb, "element_dof_per_s": ub.shape[0] * ub.shape[2] / (tb * 1e-3),
+                 "note": "64 elements (1,024 nodes), inputs L2-resident; launch-latency bound"}}
+    cb.close()
 
     u64, Ja = I.workload(3, 5, 0, 8)
     E, nn = u64.shape[0], u64.shape[2]
@@ -584,18 +709,11 @@ def main():
             A.sfh_vjp(ctx.handle, E, tu64.data_ptr(), tJ.data_ptr(), lam_main.data_ptr(), r64.data_ptr(), sh)
 
     # ---- headline: FP32-Kahan residual, K steps
-    for _ in range(args.warmup):
-        step32()
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    sampler.start()
-    time.sleep(0.2)
-    t_total, t_launch = timed_launches(step32, args.steps, 0, stream, torch)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-        t_total = D.max_over_ranks(t_total, dist, dev)
+    def gpu_timer(fn, k):
+        sampler.start()
+        time.sleep(0.2)
+        return timed_launches(fn, k, 0, stream, torch)
+    t_total, t_launch = timed_region(step32, args.steps, args.warmup, dist, torch.cuda.synchronize, gpu_timer, dev)
     assert ctx.check() == A.SFH_OK
     ms_step = t_total / args.steps
     value = D.aggregate_throughput(dof, world, ms_step * 1e-3)
@@ -604,24 +722,38 @@ def main():
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
     fl = flops_per_element(d, p, kind) * E
-    if args.prec == "fp32k":
+    if args.prec == "fp32k" and not modal and d == 3 and fp32_roofline(d, p, kind, E, t_launch, hbm_peak)["bound"] == "alu":
+        # high degree: the FP32 pipe binds before HBM (more pairs per node)
+        ops = fp32_pipe_ops_per_element(d, p, kind) * E
+        roofline = {"bound": "alu", "achieved": ops / (t_launch * 1e-3) / 1e12, "peak": FP32_LANE_OPS / 1e12,
+                    "unit": "Top/s (FP32 pipe operations)", "frac": ops / (t_launch * 1e-3) / FP32_LANE_OPS,
+                    "traffic": measured_traffic(args.prec, p, kind, N),
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (recipe unit counts and clock)",
+                    "kernel": fp32_kernel_name(d, p, modal), "binding": fp32_roofline(d, p, kind, E, t_launch, hbm_peak),
+                    "algorithmic_fp32_ops_per_launch": ops, "launch_ms": t_launch}
+    elif args.prec == "fp32k":
         b32 = bytes_per_node("fp32k", d) * dof
         roofline = {"bound": "hbm", "achieved": b32 / (t_launch * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                     "frac": b32 / (t_launch * 1e-3) / 1e9 / hbm_peak,
+                    "binding": None if modal else fp32_roofline(d, p, kind, E, t_launch, hbm_peak),
                     "traffic": None if modal else measured_traffic(args.prec, p, kind, N),
                     "peak_source": hbm_src,
-                    "kernel": ("volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, p + 1) if modal else
-                               "volume_fp32_row_kernel<%d>" % (p + 1) if d == 3 and p + 1 in (7, 8)
-                               else "volume_fp32_tma_kernel<%d,%d,euler>" % (d, p + 1)),
+                    "kernel": fp32_kernel_name(d, p, modal),
                     "ncu": None if modal else measured_counters(args.prec, p, kind, N),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     elif args.prec == "fp32mix":
-        # the FP64 log means bind the mixed mode: ALU roofline of the FP64 pipe
-        flm = pairs_per_element(d, p) * MIX_PAIR_FP64_FLOPS * E
-        roofline = {"bound": "alu", "achieved": flm / (t_launch * 1e-3) / 1e12, "peak": 1.25, "unit": "TFLOP/s",
-                    "frac": flm / (t_launch * 1e-3) / 1e12 / 1.25, "traffic": measured_traffic(args.prec, p, kind, N),
-                    "peak_source": "nominal FP64 rate of the recipe table", "kernel": "volume_kernel<mixed> (FP64 part)",
-                    "algorithmic_flops_per_launch": flm, "launch_ms": t_launch}
+        # the FP64 islands bind the mixed mode: ALU roofline of the FP64 pipe
+        # (flops against the nominal rate; instructions against its issue rate)
+        fle, ine = mix_fp64_work(d, p, kind)
+        flm, inm = fle * E, ine * E
+        roofline = {"bound": "alu", "achieved": flm / (t_launch * 1e-3) / 1e12, "peak": FP64_TFLOPS,
+                    "unit": "TFLOP/s", "frac": flm / (t_launch * 1e-3) / 1e12 / FP64_TFLOPS,
+                    "fp64_pipe_instr_frac": inm / (t_launch * 1e-3) / (FP64_TFLOPS * 1e12 / 2),
+                    "traffic": measured_traffic(args.prec, p, kind, N),
+                    "peak_source": "nominal FP64 rate of the recipe table (2 DFMA per clock per SM)",
+                    "kernel": ("volume_fp32_ws_kernel<%d,%d,euler,mixed> (FP64 islands)" % (d, p + 1)
+                               if d == 3 and 3 <= p + 1 <= 6 else "volume_kernel<mixed> (FP64 part)"),
+                    "algorithmic_flops_per_launch": flm, "fp64_instructions_per_launch": inm, "launch_ms": t_launch}
     else:
         # FP64 arithmetic binds: the ALU roofline against the nominal FP64 rate
         # (1.25 TFLOP/s; our FMA-chain microbenchmark measures the same)

@@ -111,9 +111,14 @@ sfh_status sfh_destroy(sfh_ctx *ctx);
  * u, r: device, [n_elem][nvar][n^d], double for SFH_FP64, float otherwise,
  *       8-byte (double) or 4-byte (float) aligned; r must not overlap u or Ja.
  * Ja:   device, [n_elem][d][d][n^d] double (FP64 in every mode), 8-byte aligned.
+ *       Accepted values: finite, and |Ja| < 2^126 in the FP32 modes (their
+ *       FP32 copies and pair sums then stay finite); metric terms are
+ *       O(h^{d-1}), far inside this range.
  * n_elem >= 0 (0 is a no-op).  Asynchronous on `stream`.
  * Errors: SFH_EINVAL before any launch; SFH_ECUDA if the launch fails;
- * domain errors are latched for sfh_check(). */
+ * device-detected errors are latched for sfh_check(): SFH_EDOMAIN for a
+ * density or pressure <= 0 (or NaN) and for a metric term outside the
+ * accepted range (the other elements' results are still computed). */
 sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, const double *Ja,
                                void *r, sfh_prec prec, sfh_stream_t stream);
 
@@ -205,7 +210,10 @@ sfh_status sfh_entropy_residual(sfh_ctx *ctx, int64_t n_elem, const double *u, c
 
 /* Synchronize `stream`, then read and clear the context's device error word.
  * Returns SFH_EDOMAIN if any kernel of this context saw rho <= 0 or p <= 0
- * (or a NaN) since the last check, SFH_ECUDA on a CUDA error, else SFH_OK. */
+ * (or a NaN) or a metric term outside the accepted range (see
+ * sfh_volume_residual) since the last check, SFH_ETIMEOUT if a bounded device
+ * wait gave up, SFH_ECUDA on a CUDA error, else SFH_OK; sfh_last_error()
+ * says which. */
 sfh_status sfh_check(sfh_ctx *ctx, sfh_stream_t stream);
 
 /* Host-buffer form of sfh_volume_residual: u_host, Ja_host, r_host are host
@@ -335,7 +343,12 @@ typedef struct {
 
 typedef struct {
     int status;          /* sfh_status of the request */
-    uint64_t t_submit_ns, t_admit_ns, t_done_ns;   /* host CLOCK_MONOTONIC timestamps */
+    /* host CLOCK_MONOTONIC timestamps: submitted, admitted (its tiles
+     * published), started (the first of its tiles began on the device: the
+     * device timer mapped to the host clock by a calibration at server
+     * creation, to within a few microseconds; 0 if no tile ran), done (the
+     * completion seen by the host) */
+    uint64_t t_submit_ns, t_admit_ns, t_start_ns, t_done_ns;
 } sfh_result;
 
 /* Create a server on the current device; starts its persistent kernel and
@@ -353,7 +366,10 @@ sfh_status sfh_serve_submit(sfh_server *srv, const sfh_request *req, uint64_t *t
 
 /* Non-blocking: SFH_OK and *out filled when the request is done (out->status
  * holds its own result), SFH_ENOTREADY while it is pending, SFH_EINVAL for an
- * unknown ticket.  A ticket can be polled done once. */
+ * unknown ticket.  A ticket can be polled done once.  A request still in
+ * flight timeout_ms after its admission is reported done with status
+ * SFH_ETIMEOUT; the device may still be running it, so its arrays must stay
+ * valid until sfh_server_destroy returns. */
 sfh_status sfh_serve_poll(sfh_server *srv, uint64_t ticket, sfh_result *out);
 
 /* Replay a request stream: request i is submitted at arrival_s[i] seconds
@@ -366,9 +382,41 @@ sfh_status sfh_serve_poll(sfh_server *srv, uint64_t ticket, sfh_result *out);
 sfh_status sfh_serve_replay(sfh_server *srv, int n, const sfh_request *reqs, const double *arrival_s,
                             sfh_result *results, int timeout_ms);
 
+/* Baseline of the serving benchmark (no paper counterpart): the same kind of
+ * request stream as sfh_serve_replay, run without a server -- each request
+ * as one plain launch of sfh_volume_residual (in its own precision) or
+ * sfh_vjp, in FIFO order on one stream of the current device, enqueued at
+ * its arrival time, so that waiting behind earlier requests is part of its
+ * latency.  Requests as for sfh_serve_submit (3D Euler, Ranocha flux);
+ * contexts are created per degree for the call.  results[i]: t_submit_ns =
+ * t_admit_ns = enqueue time; t_start_ns = max(enqueue time, previous
+ * request's done time), the start of a FIFO stream; t_done_ns = host time at
+ * which its completion was seen (polled every ~10 us).  Blocks until all are
+ * done (SFH_OK), or timeout_ms passes (SFH_ETIMEOUT).  A device-detected
+ * domain error of any request makes the call return SFH_EDOMAIN (not
+ * attributed to a request).  Errors: SFH_EINVAL, SFH_ECUDA. */
+sfh_status sfh_serial_replay(int n, const sfh_request *reqs, const double *arrival_s, sfh_result *results,
+                             int timeout_ms);
+
 /* Block until every submitted request is done or timeout_ms passes
  * (SFH_ETIMEOUT). */
 sfh_status sfh_serve_drain(sfh_server *srv, int timeout_ms);
+
+/* Host-side fault injection, for testing the server's failure detection (no
+ * paper counterpart; no device fault is involved):
+ *   SFH_FAULT_CREATE_ALLOC (srv may be NULL): the next sfh_server_create
+ *     fails at its arg-th allocation (1..4; 0 clears) and returns
+ *     SFH_ENOMEM after releasing what it had allocated;
+ *   SFH_FAULT_DROP_TILE: the next arg admitted requests publish all but
+ *     their last tile, so they never complete.  The server's watchdog reports
+ *     each SFH_ETIMEOUT timeout_ms after admission (its slot and budget stay
+ *     held), sfh_serve_drain returns SFH_ETIMEOUT, and sfh_server_destroy
+ *     stops the kernel, frees the server and returns SFH_ETIMEOUT;
+ *   SFH_FAULT_STALL_ADMISSION: the admission thread sleeps arg milliseconds
+ *     once (a stalled host thread); the caller's waits stay bounded.
+ * Errors: SFH_EINVAL for an unknown kind or argument. */
+typedef enum { SFH_FAULT_CREATE_ALLOC = 1, SFH_FAULT_DROP_TILE = 2, SFH_FAULT_STALL_ADMISSION = 3 } sfh_fault;
+sfh_status sfh_serve_inject_fault(sfh_server *srv, int kind, int arg);
 
 /* Serving-kernel counters since the server was created (tracing; no paper
  * counterpart), summed over the persistent CTAs from the device timer:

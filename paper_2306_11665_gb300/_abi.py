@@ -24,6 +24,7 @@ SFH_FLUX_BURGERS, SFH_FLUX_EULER_RANOCHA, SFH_FLUX_EULER_CHANDRASHEKAR = 0, 1, 2
 SFH_FP64, SFH_FP32_KAHAN, SFH_FP32_MIXED = 0, 1, 2
 SFH_BASIS_LEGENDRE, SFH_BASIS_LAGRANGE_GLL, SFH_BASIS_LAGRANGE_GAUSS = 0, 1, 2
 SFH_REQ_RESIDUAL, SFH_REQ_VJP = 0, 1
+SFH_FAULT_CREATE_ALLOC, SFH_FAULT_DROP_TILE, SFH_FAULT_STALL_ADMISSION = 1, 2, 3
 
 
 class SfhError(RuntimeError):
@@ -45,7 +46,7 @@ class Request(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("t_submit_ns", ctypes.c_uint64), ("t_admit_ns", ctypes.c_uint64),
-                ("t_done_ns", ctypes.c_uint64)]
+                ("t_start_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
 
 
 class ServeStats(ctypes.Structure):
@@ -82,6 +83,9 @@ _SIGS = {
     "sfh_serve_replay": [vp, ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
                          ctypes.POINTER(Result), ctypes.c_int],
     "sfh_server_destroy": [vp],
+    "sfh_serial_replay": [ctypes.c_int, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(Result), ctypes.c_int],
+    "sfh_serve_inject_fault": [vp, ctypes.c_int, ctypes.c_int],
 }
 
 
@@ -242,6 +246,22 @@ def sfh_serve_replay(srv: int, reqs, arrival_s, timeout_ms: int):
     out = (Result * n)()
     _call("sfh_serve_replay", srv, n, R, T, out, timeout_ms)
     return list(out)
+
+
+def sfh_serial_replay(reqs, arrival_s, timeout_ms: int):
+    """The serving baseline: the requests as plain FIFO launches on one stream,
+    each enqueued at its arrival time; returns the Results."""
+    n = len(reqs)
+    R = (Request * n)(*reqs)
+    T = (ctypes.c_double * n)(*arrival_s)
+    out = (Result * n)()
+    _call("sfh_serial_replay", n, R, T, out, timeout_ms)
+    return list(out)
+
+
+def sfh_serve_inject_fault(srv, kind: int, arg: int) -> None:
+    """Test hook: host-side fault injection into the server (header)."""
+    _call("sfh_serve_inject_fault", srv, kind, arg)
 
 
 def sfh_serve_drain(srv: int, timeout_ms: int) -> None:

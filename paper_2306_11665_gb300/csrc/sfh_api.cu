@@ -562,10 +562,22 @@ extern "C" sfh_status sfh_check(sfh_ctx *c, sfh_stream_t stream) {
     if ((e = cudaMemcpy(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(e, "read error word");
     if (h) {
         if ((e = cudaMemset(c->d_err, 0, sizeof(int))) != cudaSuccess) return cuda_fail(e, "clear error word");
-        return fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state");
+        return (sfh_status)sfh::err_word_status(h);
     }
     return SFH_OK;
 }
+
+namespace sfh {
+int err_word_status(int h) {
+    if (h & kErrTimeout) return fail(SFH_ETIMEOUT, "a bounded device wait gave up");
+    if ((h & kErrDomain) && (h & kErrMetric))
+        return fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state, and a metric term out of range "
+                                 "(Inf, NaN, or |Ja| >= 2^126 in an FP32 mode)");
+    if (h & kErrMetric)
+        return fail(SFH_EDOMAIN, "metric term out of range (Inf, NaN, or |Ja| >= 2^126 in an FP32 mode)");
+    return fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state");
+}
+}  // namespace sfh
 
 // ---------------------------------------------------------------------------
 // host-buffer pipeline: chunks alternate between two streams; on each stream

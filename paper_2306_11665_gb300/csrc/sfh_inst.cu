@@ -9,6 +9,7 @@
 #include "sfh_volume.cuh"
 #include "sfh_vjp.cuh"
 #include "sfh_volume_tma.cuh"
+#include "sfh_volume_ws.cuh"
 #include "sfh_volume_row.cuh"
 #include "sfh_volume_row64.cuh"
 
@@ -83,8 +84,24 @@ cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_ele
                          cudaStream_t stream) {
     if constexpr (use_row_kernel<D, N, FLUX>())
         return launch_volume_fp32_row<N>(u, Ja, r, n_elem, tab, err, stream);
+    else if constexpr (use_ws_kernel<D, N, FLUX>())
+        return launch_volume_fp32_ws<D, N, FLUX>(u, Ja, r, n_elem, tab, err, stream);
     else
         return launch_volume_fp32_tma<D, N, FLUX>(u, Ja, r, n_elem, tab, err, stream);
+}
+#endif
+
+#if defined(SFH_INST_MIXED) && !defined(SFH_INST_MODAL)
+// Mixed mode: the warp-specialized kernel for 3D Euler at n = 3..6 (FP64
+// metric pair sums and log-mean islands in its sweep), the thread-per-line
+// kernel otherwise.
+template <int D, int N, int FLUX>
+cudaError_t launch_mixed(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab, int *err,
+                         cudaStream_t stream) {
+    if constexpr (use_ws_kernel<D, N, FLUX>())
+        return launch_volume_fp32_ws<D, N, FLUX, true>(u, Ja, r, n_elem, tab, err, stream);
+    else
+        return launch_volume<D, N, FLUX, ModeMixed>(u, Ja, r, n_elem, tab, err, stream);
 }
 #endif
 
@@ -159,13 +176,14 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
                    const OpTab<typename Mode::T> &tab, int *err, cudaStream_t stream) {
     constexpr int D = SFH_INST_D;
 #if defined(SFH_INST_FP32K)
-    // FP32-Kahan: the persistent TMA-staged kernels (a thread per line, or a
-    // thread per line and node for 3D Euler at high degree)
+    // FP32-Kahan: the persistent TMA-staged kernels (warp-specialized for 3D
+    // Euler at n = 3..6, a thread per line and node for 3D Euler at n = 7, 8,
+    // a thread per line otherwise)
 #define SFH_VCALL(N, F) launch_fp32k<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
 #elif defined(SFH_INST_FP64)
 #define SFH_VCALL(N, F) launch_fp64<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
 #else
-#define SFH_VCALL(N, F) launch_volume<D, N, F, Mode>(u, Ja, r, n_elem, tab, err, stream)
+#define SFH_VCALL(N, F) launch_mixed<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
 #endif
 #define SFH_CASE(N)                                                                                    \
     case N:                                                                                            \

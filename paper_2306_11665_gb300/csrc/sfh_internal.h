@@ -140,6 +140,11 @@ inline cudaError_t (*vjp_fn(int d, int flux))(int, int, const double *, const do
 // compute with the same FP32 and FP64 values.
 bool op_tables(int p, int nodes, OpTab<double> &tab_d, OpTab<float> &tab_f);
 
+// Status of a nonzero device error word (kErr* bits), with the calling
+// thread's message set: a timeout gives SFH_ETIMEOUT, a bad state or an
+// out-of-range metric term SFH_EDOMAIN.  Returns an sfh_status value.
+int err_word_status(int h);
+
 // Set the calling thread's message returned by sfh_last_error().
 void set_error_message(const char *msg);
 

@@ -133,7 +133,6 @@ extern "C" sfh_status sfh_volume_residual_host_noalloc(int d, int p, sfh_nodes n
         (e = cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return na_fail(SFH_ECUDA, "result copy: %s", cudaGetErrorString(e));
-    if (h_err & 2) return na_fail(SFH_ETIMEOUT, "a bounded device wait gave up");
-    if (h_err) return na_fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state");
+    if (h_err) return (sfh_status)sfh::err_word_status(h_err);
     return SFH_OK;
 }

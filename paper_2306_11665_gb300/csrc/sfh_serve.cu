@@ -69,6 +69,7 @@ static_assert(sizeof(Req) == 64, "descriptor read as four 16-byte words");
 struct Done {  // written by the device
     uint32_t seq;
     int32_t status;
+    unsigned long long t_start;   // device timer at the start of the request's first tile
 };
 
 struct DevCtrl {   // device memory
@@ -77,6 +78,7 @@ struct DevCtrl {   // device memory
     int quit;          // set once every CTA is idle: the whole kernel leaves
     int done_tiles[kMaxSlots];
     int err[kMaxSlots];
+    unsigned long long t_start[kMaxSlots];   // earliest tile start of the slot's request (~0: none yet)
     unsigned long long tiles[4], busy_ns[4], claim_ns;   // counters (sfh_serve_stats)
 };
 
@@ -199,7 +201,7 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         for (int s = threadIdx.x; s < nb * S::J_EL; s += kThreads) cp_async8(rawJ + s, J + s);
         cp_async_commit();
     };
-    bool bad = false;
+    int bad = 0;
     fetch(0);
     for (int b0 = 0; b0 < ne; b0 += S::EPB) {
         const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
@@ -213,7 +215,7 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         fp32_block_store<S, 3>(sR, static_cast<float *>(q.out) + (e0 + b0) * S::U_EL, nb, threadIdx.x, kThreads);
         __syncthreads();
     }
-    if (bad) atomicOr(err, kErrDomain);
+    if (bad) atomicOr(err, bad);
 }
 template <int N>
 __device__ __noinline__ void run_mix(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
@@ -313,6 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
         if (threadIdx.x == 0) {
             t_run = global_timer_ns();
             atomicAdd(&a.ctrl->claim_ns, (unsigned long long)(t_run - t_claim));
+            atomicMin(&a.ctrl->t_start[s_slot], (unsigned long long)t_run);
         }
         const int64_t e0 = (int64_t)s_tile * q.epb;
         const int ne = (int)((q.n_elem - e0) < q.epb ? (q.n_elem - e0) : q.epb);
@@ -337,15 +340,25 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
             if (done == q.ntiles) {
                 __threadfence();
                 const int st = atomicExch(&a.ctrl->err[slot], 0);
+                const unsigned long long ts = atomicExch(&a.ctrl->t_start[slot], ~0ull);
                 a.ctrl->done_tiles[slot] = 0;
                 __threadfence_system();
                 volatile Done *dn = a.done + slot;
                 dn->status = st ? (st & kErrTimeout ? SFH_ETIMEOUT : SFH_EDOMAIN) : SFH_OK;
+                dn->t_start = ts;
                 __threadfence_system();
                 dn->seq = q.seq;
             }
         }
         __syncthreads();
+    }
+}
+
+// Device timer read into mapped host memory (clock calibration).
+__global__ void read_timer_kernel(volatile unsigned long long *out) {
+    if (threadIdx.x == 0) {
+        *out = global_timer_ns();
+        __threadfence_system();
     }
 }
 
@@ -378,7 +391,11 @@ struct Inflight {
     int ntiles;
     uint32_t seq;
     uint64_t t_submit, t_admit;
+    bool abandoned;   // reported SFH_ETIMEOUT to the caller; slot and budget held until the device finishes
 };
+
+// Test-only fault injection (sfh_serve_inject_fault): host-side faults only.
+std::atomic<int> g_fail_alloc{0};   // the next server creation fails at this allocation (1-based; 0 off)
 
 size_t req_bytes(const sfh_request &r) {
     const size_t nn = (size_t)(r.p + 1) * (r.p + 1) * (r.p + 1);
@@ -413,6 +430,7 @@ struct sfh_server {
     bool slot_busy[kMaxSlots];
     uint32_t slot_seq[kMaxSlots];
     int inflight = 0;
+    int abandoned = 0;   // in flight but already reported SFH_ETIMEOUT
     size_t used_bytes = 0;
     uint64_t tiles_live = 0;
     uint64_t tail = 0;
@@ -422,6 +440,10 @@ struct sfh_server {
     bool quit = false;
     bool kernel_error = false;
     std::thread worker;
+    int64_t clk_offset = 0;       // host steady clock - device timer (ns)
+    int inject_drop_tile = 0;     // test hook: publish all but the last tile of the next N admitted requests
+    int inject_stall_ms = 0;      // test hook: the admission thread sleeps this long once
+    bool give_up = false;         // destroy after a failed drain: stop relaunching, leave the loop
 };
 
 namespace {
@@ -439,18 +461,46 @@ void admission_loop(sfh_server *s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         // completions
+        if (s->inject_stall_ms > 0) {   // test hook: a stalled admission thread
+            const int ms = s->inject_stall_ms;
+            s->inject_stall_ms = 0;
+            lk.unlock();
+            std::this_thread::sleep_for(std::chrono::milliseconds(ms));
+            lk.lock();
+        }
+        const uint64_t t_now = now_ns();
         for (int k = 0; k < s->opts.max_inflight; ++k) {
             if (!s->slot_busy[k]) continue;
             const volatile Done *dn = s->done_h + k;
-            if (dn->seq != s->slots[k].seq) continue;
+            if (dn->seq != s->slots[k].seq) {
+                // watchdog: a request in flight for longer than timeout_ms is
+                // reported SFH_ETIMEOUT; its slot and budget stay held until
+                // the device finishes it (it may still read its arrays)
+                if (!s->slots[k].abandoned &&
+                    t_now - s->slots[k].t_admit > (uint64_t)s->opts.timeout_ms * 1000000ull) {
+                    s->slots[k].abandoned = true;
+                    sfh_result r = {SFH_ETIMEOUT, s->slots[k].t_submit, s->slots[k].t_admit, 0, t_now};
+                    s->results[s->slots[k].ticket] = r;
+                    s->where[s->slots[k].ticket] = 2;
+                    ++s->abandoned;
+                    s->cv.notify_all();
+                }
+                continue;
+            }
             std::atomic_thread_fence(std::memory_order_acquire);
-            sfh_result r;
-            r.status = dn->status;
-            r.t_submit_ns = s->slots[k].t_submit;
-            r.t_admit_ns = s->slots[k].t_admit;
-            r.t_done_ns = now_ns();
-            s->results[s->slots[k].ticket] = r;
-            s->where[s->slots[k].ticket] = 2;
+            if (s->slots[k].abandoned) {
+                --s->abandoned;   // already reported; only the resources come back
+            } else {
+                sfh_result r;
+                r.status = dn->status;
+                r.t_submit_ns = s->slots[k].t_submit;
+                r.t_admit_ns = s->slots[k].t_admit;
+                const unsigned long long ts = dn->t_start;
+                r.t_start_ns = ts == ~0ull ? 0 : (uint64_t)((int64_t)ts + s->clk_offset);
+                r.t_done_ns = now_ns();
+                s->results[s->slots[k].ticket] = r;
+                s->where[s->slots[k].ticket] = 2;
+            }
             s->slot_busy[k] = false;
             s->used_bytes -= s->slots[k].bytes;
             s->tiles_live -= (uint64_t)s->slots[k].ntiles;
@@ -478,13 +528,18 @@ void admission_loop(sfh_server *s) {
             q.epb = pq.epb;
             q.ntiles = pq.ntiles;
             q.seq = seq;
-            for (int t = 0; t < pq.ntiles; ++t) {
+            int publish = pq.ntiles;
+            if (s->inject_drop_tile > 0 && pq.ntiles > 0) {   // test hook: a tile that is never published
+                --s->inject_drop_tile;
+                --publish;
+            }
+            for (int t = 0; t < publish; ++t) {
                 Tile &te = s->ring_h[(s->tail + t) % kRing];
                 te.slot = k;
                 te.tile = t;
             }
             std::atomic_thread_fence(std::memory_order_release);
-            s->tail += (uint64_t)pq.ntiles;
+            s->tail += (uint64_t)publish;
             *s->tail_h = s->tail;
             Inflight &f = s->slots[k];
             f.ticket = pq.ticket;
@@ -493,6 +548,7 @@ void admission_loop(sfh_server *s) {
             f.seq = seq;
             f.t_submit = pq.t_submit;
             f.t_admit = now_ns();
+            f.abandoned = false;
             s->slot_busy[k] = true;
             s->where[pq.ticket] = 1;
             s->used_bytes += pq.bytes;
@@ -500,8 +556,10 @@ void admission_loop(sfh_server *s) {
             ++s->inflight;
             s->pending.pop_front();
         }
-        // keep the persistent kernel alive while work is in flight
-        if (s->inflight > 0 && !s->kernel_error) {
+        // keep the persistent kernel alive while work is in flight (a
+        // request whose tiles will never all arrive keeps it relaunching at
+        // the idle interval until the server is destroyed)
+        if (s->inflight > 0 && !s->kernel_error && !s->give_up) {
             const cudaError_t q = cudaStreamQuery(s->stream);
             if (q == cudaSuccess) {
                 if (launch(s) != SFH_OK) s->kernel_error = true;
@@ -513,9 +571,13 @@ void admission_loop(sfh_server *s) {
             // fail everything in flight: the device cannot be trusted to finish it
             for (int k = 0; k < s->opts.max_inflight; ++k) {
                 if (!s->slot_busy[k]) continue;
-                sfh_result r = {SFH_ECUDA, s->slots[k].t_submit, s->slots[k].t_admit, now_ns()};
-                s->results[s->slots[k].ticket] = r;
-                s->where[s->slots[k].ticket] = 2;
+                if (!s->slots[k].abandoned) {
+                    sfh_result r = {SFH_ECUDA, s->slots[k].t_submit, s->slots[k].t_admit, 0, now_ns()};
+                    s->results[s->slots[k].ticket] = r;
+                    s->where[s->slots[k].ticket] = 2;
+                } else {
+                    --s->abandoned;
+                }
                 s->slot_busy[k] = false;
                 s->used_bytes -= s->slots[k].bytes;
                 s->tiles_live -= (uint64_t)s->slots[k].ntiles;
@@ -523,7 +585,7 @@ void admission_loop(sfh_server *s) {
             }
             s->cv.notify_all();
         }
-        if (s->quit && s->pending.empty() && s->inflight == 0) break;
+        if (s->quit && ((s->pending.empty() && s->inflight == 0) || s->give_up)) break;
         if (s->inflight == 0 && s->pending.empty()) {
             s->cv.wait_for(lk, std::chrono::milliseconds(2));
         } else {
@@ -532,6 +594,39 @@ void admission_loop(sfh_server *s) {
             lk.lock();
         }
     }
+}
+
+}  // namespace
+
+namespace {
+
+// Allocation step k (1-based) of a server creation: fails with `e` when the
+// test hook asked for it, else performs `op`.
+template <class Op>
+cudaError_t alloc_step(int k, Op op) {
+    int want = g_fail_alloc.load();
+    if (want == k && g_fail_alloc.compare_exchange_strong(want, 0)) return cudaErrorMemoryAllocation;
+    return op();
+}
+
+// Host steady clock minus device timer, from the tightest of a few
+// launch-and-wait brackets around one read of the device timer.
+cudaError_t calibrate_clock(cudaStream_t st, volatile unsigned long long *h, unsigned long long *d, int64_t *out) {
+    int64_t best_w = INT64_MAX, best = 0;
+    for (int it = 0; it < 5; ++it) {
+        *h = 0;
+        const uint64_t t0 = now_ns();
+        read_timer_kernel<<<1, 32, 0, st>>>(d);
+        cudaError_t e = cudaStreamSynchronize(st);
+        const uint64_t t1 = now_ns();
+        if (e != cudaSuccess) return e;
+        if ((int64_t)(t1 - t0) < best_w) {
+            best_w = (int64_t)(t1 - t0);
+            best = (int64_t)((t0 + t1) / 2) - (int64_t)*h;
+        }
+    }
+    *out = best;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -552,51 +647,49 @@ extern "C" sfh_status sfh_server_create(const sfh_server_opts *opts, sfh_server 
     s->n_workers = opts->n_workers > 0 ? opts->n_workers : sms;
     memset(s->slot_busy, 0, sizeof s->slot_busy);
     memset(s->slot_seq, 0, sizeof s->slot_seq);
-    // mapped host memory for the ring, descriptors, completions and control words
-    const size_t hbytes = sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots + sizeof(Done) * kMaxSlots + 64;
+    // mapped host memory for the ring, descriptors, completions, control words
+    // and the clock-calibration word
+    const size_t hbytes = sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots + sizeof(Done) * kMaxSlots + 128;
     void *h = nullptr;
-    if ((e = cudaHostAlloc(&h, hbytes, cudaHostAllocMapped)) != cudaSuccess) { delete s; return SFH_ENOMEM; }
+    if ((e = alloc_step(1, [&] { return cudaHostAlloc(&h, hbytes, cudaHostAllocMapped); })) != cudaSuccess) {
+        delete s;
+        return SFH_ENOMEM;
+    }
     memset(h, 0, hbytes);
     char *hc = static_cast<char *>(h);
     s->ring_h = reinterpret_cast<Tile *>(hc);
     s->reqs_h = reinterpret_cast<Req *>(hc + sizeof(Tile) * kRing);
     s->done_h = reinterpret_cast<Done *>(hc + sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots);
-    s->tail_h = reinterpret_cast<volatile unsigned long long *>(hc + hbytes - 64);
-    s->stop_h = reinterpret_cast<volatile int *>(hc + hbytes - 32);
+    s->tail_h = reinterpret_cast<volatile unsigned long long *>(hc + hbytes - 128);
+    s->stop_h = reinterpret_cast<volatile int *>(hc + hbytes - 96);
+    volatile unsigned long long *clk_h = reinterpret_cast<volatile unsigned long long *>(hc + hbytes - 64);
     void *dh = nullptr;
     if ((e = cudaHostGetDevicePointer(&dh, h, 0)) != cudaSuccess) { cudaFreeHost(h); delete s; return SFH_ECUDA; }
     char *dc = static_cast<char *>(dh);
     s->args.ring = reinterpret_cast<const Tile *>(dc);
     s->args.reqs = reinterpret_cast<const Req *>(dc + sizeof(Tile) * kRing);
     s->args.done = reinterpret_cast<Done *>(dc + sizeof(Tile) * kRing + sizeof(Req) * kMaxSlots);
-    s->args.tail = reinterpret_cast<const volatile unsigned long long *>(dc + hbytes - 64);
-    s->args.stop = reinterpret_cast<const volatile int *>(dc + hbytes - 32);
+    s->args.tail = reinterpret_cast<const volatile unsigned long long *>(dc + hbytes - 128);
+    s->args.stop = reinterpret_cast<const volatile int *>(dc + hbytes - 96);
+    unsigned long long *clk_d = reinterpret_cast<unsigned long long *>(dc + hbytes - 64);
     s->args.idle_ns = 2000000ull;   // 2 ms without work: CTAs leave, the host relaunches on demand
     // device: control block and operator tables for every (node set, n)
-    if ((e = cudaMalloc(&s->ctrl_d, sizeof(DevCtrl))) != cudaSuccess ||
-        (e = cudaMalloc(&s->tabd_d, sizeof(sfh::OpTab<double>) * 20)) != cudaSuccess ||
-        (e = cudaMalloc(&s->tabf_d, sizeof(sfh::OpTab<float>) * 20)) != cudaSuccess) {
+    s->ctrl_d = nullptr;
+    s->tabd_d = nullptr;
+    s->tabf_d = nullptr;
+    if ((e = alloc_step(2, [&] { return cudaMalloc(&s->ctrl_d, sizeof(DevCtrl)); })) != cudaSuccess ||
+        (e = alloc_step(3, [&] { return cudaMalloc(&s->tabd_d, sizeof(sfh::OpTab<double>) * 20); })) != cudaSuccess ||
+        (e = alloc_step(4, [&] { return cudaMalloc(&s->tabf_d, sizeof(sfh::OpTab<float>) * 20); })) != cudaSuccess) {
         cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFreeHost(h); delete s; return SFH_ENOMEM;
     }
     cudaMemset(s->ctrl_d, 0, sizeof(DevCtrl));
+    cudaMemset(&s->ctrl_d->t_start, 0xff, sizeof(DevCtrl::t_start));   // no tile started yet
     std::vector<sfh::OpTab<double>> td(20);
     std::vector<sfh::OpTab<float>> tf(20);
     memset(td.data(), 0, sizeof(sfh::OpTab<double>) * 20);
     memset(tf.data(), 0, sizeof(sfh::OpTab<float>) * 20);
     for (int nodes = 0; nodes < 2; ++nodes)
-        for (int p = kPMin; p <= kPMax; ++p) {
-            double xi[sfh::NMAX], w[sfh::NMAX], D[sfh::NMAX * sfh::NMAX], Q1[sfh::NMAX * sfh::NMAX];
-            sfh_operator_tables(p, (sfh_nodes)nodes, xi, w, D, Q1);
-            const int n = p + 1, k = nodes * 10 + n;
-            for (int a = 0; a < n; ++a) {
-                td[k].w[a] = w[a];
-                tf[k].w[a] = (float)w[a];
-                for (int b = 0; b < n; ++b) {
-                    td[k].Q1[a * n + b] = Q1[a * n + b];
-                    tf[k].Q1[a * n + b] = (float)Q1[a * n + b];
-                }
-            }
-        }
+        for (int p = kPMin; p <= kPMax; ++p) sfh::op_tables(p, nodes, td[nodes * 10 + p + 1], tf[nodes * 10 + p + 1]);
     cudaMemcpy(s->tabd_d, td.data(), sizeof(sfh::OpTab<double>) * 20, cudaMemcpyHostToDevice);
     cudaMemcpy(s->tabf_d, tf.data(), sizeof(sfh::OpTab<float>) * 20, cudaMemcpyHostToDevice);
     s->args.ctrl = s->ctrl_d;
@@ -606,12 +699,28 @@ extern "C" sfh_status sfh_server_create(const sfh_server_opts *opts, sfh_server 
         (e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking)) != cudaSuccess) {
         cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFree(s->tabf_d); cudaFreeHost(h); delete s; return SFH_ECUDA;
     }
-    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess ||
+        (e = calibrate_clock(s->stream, clk_h, clk_d, &s->clk_offset)) != cudaSuccess) {
         cudaStreamDestroy(s->stream); cudaFree(s->ctrl_d); cudaFree(s->tabd_d); cudaFree(s->tabf_d);
         cudaFreeHost(h); delete s; return SFH_ECUDA;
     }
     s->worker = std::thread(admission_loop, s);
     *out = s;
+    return SFH_OK;
+}
+
+extern "C" sfh_status sfh_serve_inject_fault(sfh_server *s, int kind, int arg) {
+    if (kind == SFH_FAULT_CREATE_ALLOC) {
+        if (arg < 0 || arg > 4) return SFH_EINVAL;
+        g_fail_alloc.store(arg);
+        return SFH_OK;
+    }
+    if (!s || arg < 0) return SFH_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (kind == SFH_FAULT_DROP_TILE) s->inject_drop_tile = arg;
+    else if (kind == SFH_FAULT_STALL_ADMISSION) s->inject_stall_ms = arg;
+    else return SFH_EINVAL;
+    s->cv.notify_all();
     return SFH_OK;
 }
 
@@ -686,32 +795,24 @@ extern "C" sfh_status sfh_server_destroy(sfh_server *s) {
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->quit = true;
-        if (st != SFH_OK) {   // give up on what is left: nothing more is admitted
+        if (st != SFH_OK) {
+            // give up on what is left: nothing more is admitted or relaunched;
+            // requests still in flight (never completed) stay unreported
             s->pending.clear();
+            s->give_up = true;
         }
         s->cv.notify_all();
     }
     *s->stop_h = 1;
-    // the admission thread ends once nothing is in flight (bounded by the drain above)
-    const uint64_t t0 = now_ns();
-    while (true) {
-        {
-            std::lock_guard<std::mutex> lk(s->mu);
-            if (s->inflight == 0) break;
-        }
-        if (now_ns() - t0 > (uint64_t)s->opts.timeout_ms * 1000000ull) { st = SFH_ETIMEOUT; break; }
-        std::this_thread::sleep_for(std::chrono::milliseconds(1));
-    }
-    if (st == SFH_OK) {
-        s->worker.join();
-    } else {
-        s->worker.detach();   // the runtime cannot be reclaimed safely; report it
-        return SFH_ETIMEOUT;
-    }
-    // the persistent kernel leaves on the stop word; wait for it, bounded
+    // the admission thread leaves once nothing is in flight, or at once after
+    // a failed drain; every wait of its loop is short, so the join is bounded
+    s->worker.join();
+    // the persistent kernel leaves on the stop word (a CTA finishes the tile it
+    // runs first); wait for it, bounded.  Only then can nothing on the device
+    // touch the server's memory.
     const uint64_t t1 = now_ns();
     while (cudaStreamQuery(s->stream) == cudaErrorNotReady) {
-        if (now_ns() - t1 > (uint64_t)s->opts.timeout_ms * 1000000ull) return SFH_ETIMEOUT;
+        if (now_ns() - t1 > (uint64_t)s->opts.timeout_ms * 1000000ull) return SFH_ETIMEOUT;   // cannot free safely
         std::this_thread::sleep_for(std::chrono::microseconds(100));
     }
     cudaStreamDestroy(s->stream);
@@ -738,7 +839,7 @@ extern "C" sfh_status sfh_serve_replay(sfh_server *s, int n, const sfh_request *
         while (next < n && now >= t0 + (uint64_t)(arrival_s[next] * 1e9)) {
             const sfh_status st = sfh_serve_submit(s, &reqs[next], &tickets[next]);
             if (st != SFH_OK) {
-                results[next] = sfh_result{st, now, now, now};
+                results[next] = sfh_result{st, now, now, 0, now};
                 ++n_done;
             } else {
                 open.push_back(next);
@@ -769,4 +870,93 @@ extern "C" sfh_status sfh_serve_replay(sfh_server *s, int n, const sfh_request *
         if (due > t + 30000) std::this_thread::sleep_for(std::chrono::microseconds(10));
     }
     return SFH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// serving baseline: the same stream as plain single-request launches, FIFO on
+// one stream, each enqueued at its arrival time (queueing included)
+// ---------------------------------------------------------------------------
+extern "C" sfh_status sfh_serial_replay(int n, const sfh_request *reqs, const double *arrival_s,
+                                        sfh_result *results, int timeout_ms) {
+    if (n < 0 || (n > 0 && (!reqs || !arrival_s || !results)) || timeout_ms < 1) return SFH_EINVAL;
+    for (int i = 0; i < n; ++i) {
+        const sfh_request &r = reqs[i];
+        if ((r.kind != SFH_REQ_RESIDUAL && r.kind != SFH_REQ_VJP) || r.p < kPMin || r.p > kPMax ||
+            (r.nodes != SFH_NODES_GLL && r.nodes != SFH_NODES_GAUSS) || r.n_elem < 1 || (i > 0 && arrival_s[i] < arrival_s[i - 1]))
+            return SFH_EINVAL;
+        results[i] = sfh_result{SFH_ENOTREADY, 0, 0, 0, 0};
+    }
+    sfh_ctx *ctx[2][kPMax + 1] = {};
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)n, nullptr);
+    std::vector<char> launched((size_t)n, 0);
+    sfh_status ret = SFH_OK;
+    auto cleanup = [&]() {
+        if (st) cudaStreamSynchronize(st);   // every launch is a bounded kernel
+        for (int nd = 0; nd < 2; ++nd)
+            for (int p = 0; p <= kPMax; ++p)
+                if (ctx[nd][p]) {
+                    if (ret == SFH_OK && sfh_check(ctx[nd][p], st) != SFH_OK) ret = SFH_EDOMAIN;
+                    sfh_destroy(ctx[nd][p]);
+                }
+        for (auto &x : ev)
+            if (x) cudaEventDestroy(x);
+        if (st) cudaStreamDestroy(st);
+    };
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return SFH_ECUDA;
+    for (int i = 0; i < n; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) {
+            ret = SFH_ECUDA;
+            cleanup();
+            return ret;
+        }
+    int next = 0, head = 0, n_done = 0;
+    uint64_t prev_done = 0;
+    const uint64_t t0 = now_ns();
+    while (n_done < n) {
+        // enqueue every request whose arrival time has come
+        while (next < n && now_ns() >= t0 + (uint64_t)(arrival_s[next] * 1e9)) {
+            const sfh_request &r = reqs[next];
+            sfh_ctx *&c = ctx[r.nodes][r.p];
+            sfh_status s1 = SFH_OK;
+            if (!c) s1 = sfh_create(3, r.p, (sfh_nodes)r.nodes, 5, SFH_FLUX_EULER_RANOCHA, &c);
+            const uint64_t t = now_ns();
+            if (s1 == SFH_OK)
+                s1 = r.kind == SFH_REQ_VJP
+                         ? sfh_vjp(c, r.n_elem, static_cast<const double *>(r.u), r.Ja, r.lambda,
+                                   static_cast<double *>(r.out), st)
+                         : sfh_volume_residual(c, r.n_elem, r.u, r.Ja, r.out, (sfh_prec)r.prec, st);
+            results[next] = sfh_result{s1, t, t, 0, t};
+            if (s1 == SFH_OK && cudaEventRecord(ev[next], st) == cudaSuccess) {
+                launched[next] = 1;
+                results[next].status = SFH_ENOTREADY;
+            } else {
+                if (s1 == SFH_OK) results[next].status = SFH_ECUDA;
+                ++n_done;
+            }
+            ++next;
+        }
+        // completions, in FIFO order
+        while (head < next) {
+            if (!launched[head]) { ++head; continue; }
+            const cudaError_t q = cudaEventQuery(ev[head]);
+            if (q == cudaErrorNotReady) break;
+            const uint64_t t = now_ns();
+            sfh_result &r = results[head];
+            r.t_start_ns = r.t_admit_ns > prev_done ? r.t_admit_ns : prev_done;
+            r.t_done_ns = t;
+            r.status = q == cudaSuccess ? SFH_OK : SFH_ECUDA;
+            prev_done = t;
+            ++n_done;
+            ++head;
+        }
+        if (now_ns() - t0 > (uint64_t)timeout_ms * 1000000ull) {
+            ret = SFH_ETIMEOUT;
+            break;
+        }
+        const uint64_t due = next < n ? t0 + (uint64_t)(arrival_s[next] * 1e9) : UINT64_MAX;
+        if (due > now_ns() + 30000) std::this_thread::sleep_for(std::chrono::microseconds(10));
+    }
+    cleanup();
+    return ret;
 }

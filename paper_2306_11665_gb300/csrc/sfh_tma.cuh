@@ -16,6 +16,17 @@ namespace sfh {
 constexpr int kMaxDevices = 64;  // launch facts are cached per device index below this
 constexpr int kErrDomain = 1;    // density or pressure <= 0 (or NaN)
 constexpr int kErrTimeout = 2;   // a bounded wait gave up
+constexpr int kErrMetric = 4;    // a metric term outside the accepted range (see below)
+
+// Accepted metric terms, compared on the high word of |Ja| (sign cleared):
+// FP32 modes take |Ja| < 2^126, so that its FP32 value and the sum of two of
+// them stay finite; FP64 takes any finite value.  Inf and NaN are refused
+// everywhere.
+constexpr uint32_t kMetricHiFp32 = 0x47d00000u;   // high word of 2^126
+constexpr uint32_t kMetricHiFp64 = 0x7ff00000u;   // Inf / NaN exponent
+__device__ __forceinline__ uint32_t abs_hi(double x) {
+    return static_cast<uint32_t>(static_cast<unsigned long long>(__double_as_longlong(x)) >> 32) & 0x7fffffffu;
+}
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -49,6 +60,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
         : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// try_wait with a suspend-time hint: a thread whose phase is not complete
+// sleeps until it completes or about hint_ns pass, instead of spinning (a
+// spinning warp takes issue slots from the warps doing the work).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return ok != 0;
 }
@@ -149,6 +175,18 @@ __device__ __forceinline__ float d2f_int(double x) {
     return __uint_as_float(f | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
 }
 
+// d2f_int that also keeps the largest high word of the rounded magnitude
+// seen (hmax), for the range check against kMetricHiFp32.
+__device__ __forceinline__ float d2f_int_track(double x, uint32_t &hmax) {
+    const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+    const unsigned long long mag = (b & 0x7fffffffffffffffull) + (1ull << 28);
+    const uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
+    hmax = max(hmax, hi);
+    uint32_t f = __funnelshift_l(lo, hi, 3) - 0xc0000000u;
+    f = hi < 0x38100000u ? 0u : f;
+    return __uint_as_float(f | (static_cast<uint32_t>(b >> 32) & 0x80000000u));
+}
+
 // FP32 -> FP64 by integer operations (exact for normal x; zero and
 // subnormal x are not handled), so that the widening does not occupy the
 // FP64 pipe: the exponent field moves from bit 23 to bit 52 (of the high
@@ -157,6 +195,23 @@ __device__ __forceinline__ double f2d_int(float x) {
     const uint32_t b = __float_as_uint(x);
     const uint32_t hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20));
     return __hiloint2double(static_cast<int>(hi), static_cast<int>(b << 29));
+}
+
+// Exact FP32 -> FP64 of a positive normal x by integer operations (three:
+// the exponent moves from bit 23 to bit 52 and is re-biased by 896).
+__device__ __forceinline__ double f2d_pos(float x) {
+    const uint32_t b = __float_as_uint(x);
+    return __hiloint2double(static_cast<int>((b >> 3) + (896u << 20)), static_cast<int>(b << 29));
+}
+
+// FP64 -> FP32 of a positive value inside the FP32 normal range, rounded half
+// away from zero, by integer operations (four: the rounding add with carry,
+// the funnel shift and the re-bias of d2f_int, without its sign and
+// underflow handling).
+__device__ __forceinline__ float d2f_pos(double x) {
+    const unsigned long long mag = static_cast<unsigned long long>(__double_as_longlong(x)) + (1ull << 28);
+    const uint32_t hi = static_cast<uint32_t>(mag >> 32), lo = static_cast<uint32_t>(mag);
+    return __uint_as_float(__funnelshift_l(lo, hi, 3) - 0xc0000000u);
 }
 
 // Hardware reciprocal approximation (PTX rcp.approx.ftz.f32: at most 1 ulp

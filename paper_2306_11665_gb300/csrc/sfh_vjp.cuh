@@ -188,13 +188,17 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
     }
 
     const double *Jb = Ja + e0 * D * D * NN;
+    uint32_t hmax = 0;   // largest |Ja| high word: Inf and NaN are refused
 #pragma unroll 1
     for (int m = 0; m < D; ++m) {
         __syncthreads();
         for (int s = threadIdx.x; s < ne * D * NN; s += blockDim.x) {
             const int el = s / (D * NN), rem = s - el * D * NN;
-            sJ[s] = Jb[((int64_t)el * D * D + m * D) * NN + rem];
+            const double j = Jb[((int64_t)el * D * D + m * D) * NN + rem];
+            hmax = max(hmax, abs_hi(j));
+            sJ[s] = j;
         }
+        if (m == D - 1 && hmax >= kMetricHiFp64) atomicOr(err, kErrMetric);
         __syncthreads();
         const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
         for (int L = threadIdx.x; L < ne * NLINE; L += blockDim.x) {

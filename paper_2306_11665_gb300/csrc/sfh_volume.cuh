@@ -287,14 +287,18 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     if (bad) atomicOr(err, 1);
 
     const double *Jb = Ja + e0 * D * D * NN;
+    uint32_t hmax = 0;   // largest |Ja| high word (range check: FP32 modes 2^126, FP64 finite)
 #pragma unroll 1
     for (int m = 0; m < D; ++m) {
         // ---- 2a. stage the metric row of direction m: Ja[e][m][k][i] -> sJ[el][k][i]
         __syncthreads();
         for (int s = threadIdx.x; s < ne * D * NN; s += blockDim.x) {
             const int el = s / (D * NN), rem = s - el * D * NN;
-            sJ[s] = (TJ)Jb[((int64_t)el * D * D + m * D) * NN + rem];
+            const double j = Jb[((int64_t)el * D * D + m * D) * NN + rem];
+            hmax = max(hmax, abs_hi(j));
+            sJ[s] = (TJ)j;
         }
+        if (m == D - 1 && hmax >= (sizeof(T) == 4 ? kMetricHiFp32 : kMetricHiFp64)) atomicOr(err, kErrMetric);
         __syncthreads();
 
         // ---- 2b. line sweeps

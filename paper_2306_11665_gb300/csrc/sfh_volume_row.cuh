@@ -284,6 +284,7 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
         const float *U = rawU + cur.offU;
         const double *J = rawJ + cur.offJ;
         bool bad = false;
+        uint32_t hmax = 0;   // largest |Ja| high word (range check)
         for (int s = tid; s < ne * NN; s += blockDim.x) {
             const int el = s / NN, i = s - el * NN;
             const float *ue = U + el * U_EL + i;
@@ -311,10 +312,12 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
             const double *je = J + el * J_EL + i;
 #pragma unroll
             for (int m = 0; m < 3; ++m)
-                sJ[(el * 3 + m) * S::NNP + S::slot(i)] = make_float4(d2f_int(je[(3 * m) * NN]), d2f_int(je[(3 * m + 1) * NN]),
-                                                        d2f_int(je[(3 * m + 2) * NN]), 0.0f);
+                sJ[(el * 3 + m) * S::NNP + S::slot(i)] =
+                    make_float4(d2f_int_track(je[(3 * m) * NN], hmax), d2f_int_track(je[(3 * m + 1) * NN], hmax),
+                                d2f_int_track(je[(3 * m + 2) * NN], hmax), 0.0f);
         }
         if (bad) atomicOr(err, kErrDomain);
+        if (hmax >= kMetricHiFp32) atomicOr(err, kErrMetric);
         __syncthreads();
 
         // ---- 3. prefetch the next block into the raw buffers

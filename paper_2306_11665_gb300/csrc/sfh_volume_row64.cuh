@@ -156,6 +156,7 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
         const double *U = rawU + cur.offU;
         const double *J = rawJ + cur.offJ;
         bool bad = false;
+        uint32_t hmax = 0;   // largest |Ja| high word (range check)
         for (int s = tid; s < ne * NN; s += blockDim.x) {
             const int el = s / NN, i = s - el * NN;
             const double *ue = U + el * U_EL + i;
@@ -188,11 +189,14 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
                 double2 *mm = sM + ((el * 3 + m) * 2) * NNP + S::slot(i);
-                mm[0] = make_double2(je[(3 * m) * NN], je[(3 * m + 1) * NN]);
-                mm[NNP] = make_double2(je[(3 * m + 2) * NN], rbd);
+                const double j0 = je[(3 * m) * NN], j1 = je[(3 * m + 1) * NN], j2 = je[(3 * m + 2) * NN];
+                hmax = max(hmax, max(abs_hi(j0), max(abs_hi(j1), abs_hi(j2))));
+                mm[0] = make_double2(j0, j1);
+                mm[NNP] = make_double2(j2, rbd);
             }
         }
         if (bad) atomicOr(err, kErrDomain);
+        if (hmax >= kMetricHiFp64) atomicOr(err, kErrMetric);
         __syncthreads();
 
         // ---- 3. prefetch the next block

@@ -203,13 +203,15 @@ __device__ __noinline__ void euler_line_general(const float *pe, const float *jl
 // ---------------------------------------------------------------------------
 
 // Primitives and FP32 metric rows of ne elements from U ([el][var][i] floats)
-// and J ([el][m][k][i] doubles), in shared or global memory; returns whether
-// this thread saw rho <= 0 or p <= 0 (or NaN).
+// and J ([el][m][k][i] doubles), in shared or global memory; returns the
+// error bits this thread found: kErrDomain (rho <= 0 or p <= 0, or NaN),
+// kErrMetric (a metric term outside the FP32 modes' range).
 template <class S, int D, int N, int FLUX>
-__device__ __forceinline__ bool fp32_block_convert(const float *U, const double *J, int ne, float *sP, float *sJF,
-                                                   int tid, int nthreads) {
+__device__ __forceinline__ int fp32_block_convert(const float *U, const double *J, int ne, float *sP, float *sJF,
+                                                  int tid, int nthreads) {
     constexpr int NN = S::NN, NLINE = S::NLINE, NP = S::NP, U_EL = S::U_EL, J_EL = S::J_EL;
     bool bad = false;
+    uint32_t hmax = 0;
     for (int s = tid; s < ne * NN; s += nthreads) {
         const int el = s / NN, i = s - el * NN;
         const float *ue = U + el * U_EL + i;
@@ -260,7 +262,7 @@ __device__ __forceinline__ bool fp32_block_convert(const float *U, const double 
                 }
                 float *dst = jl + (m * NLINE + line) * S::LJ + pos * D;
 #pragma unroll
-                for (int k = 0; k < D; ++k) dst[k] = d2f_int(je[(m * D + k) * NN]);
+                for (int k = 0; k < D; ++k) dst[k] = d2f_int_track(je[(m * D + k) * NN], hmax);
             }
         } else {
             pe[0] = ue[0];
@@ -271,13 +273,13 @@ __device__ __forceinline__ bool fp32_block_convert(const float *U, const double 
             const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
             const double *jm = J + ((el * D + m) * D) * NN + i;
             static_assert(is_euler(FLUX) || S::JF_EL == D * NN, "Burgers metric sums are node-major");
-            float acc = d2f_int(jm[0]);
+            float acc = d2f_int_track(jm[0], hmax);
 #pragma unroll
-            for (int k = 1; k < D; ++k) acc += d2f_int(jm[k * NN]);
+            for (int k = 1; k < D; ++k) acc += d2f_int_track(jm[k * NN], hmax);
             sJF[s] = acc;
         }
     }
-    return bad;
+    return (bad ? kErrDomain : 0) | (hmax >= kMetricHiFp32 ? kErrMetric : 0);
 }
 
 // Line sweeps of all directions at once: thread tid < D * EPB * NLINE owns one
@@ -588,8 +590,8 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
             __syncthreads();
             uin = D == 3 ? s2 : s1;
         }
-        const bool bad = fp32_block_convert<S, D, N, FLUX>(uin, rawJ + cur.offJ, ne, sP, sJF, tid, S::THREADS);
-        if (bad) atomicOr(err, kErrDomain);
+        const int bad = fp32_block_convert<S, D, N, FLUX>(uin, rawJ + cur.offJ, ne, sP, sJF, tid, S::THREADS);
+        if (bad) atomicOr(err, bad);
         __syncthreads();
 
         // ---- 3. prefetch the next block into the raw buffers

@@ -65,3 +65,28 @@ def test_surface_fluxes_match_interpolation_nonzeros(d, p, kind):
         for x in (-1.0, 1.0):
             nnz += abs(np.polynomial.polynomial.polyval(x, c)) > 1e-10
     assert bench.surface_fluxes_per_element(d, p, kind) == d * n ** (d - 1) * nnz
+
+
+@pytest.mark.parametrize("p, kind", [(4, 0), (4, 1), (7, 1), (2, 0)])
+def test_fp32_pipe_count_and_binding_roofline(p, kind):
+    """The FP32-pipe count: pairs x 86 + nonzero diagonal terms x 50 + nodes
+    x 45 (3D Euler), diagonal terms counted from the nonzeros of diag(Q1);
+    the binding roofline takes the larger of the two floors."""
+    import oracle as O
+    _, _, _, Q1 = O.op1d(p, kind)
+    n = p + 1
+    ndiag = int(np.count_nonzero(np.abs(np.diag(Q1)) > 1e-12))
+    want = bench.pairs_per_element(3, p) * 86 + 3 * n * n * ndiag * 50 + n ** 3 * 45
+    assert bench.fp32_pipe_ops_per_element(3, p, kind) == want
+    r = bench.fp32_roofline(3, p, kind, 1000, 1.0, 6800.0)
+    assert r["frac"] == pytest.approx(max(r["hbm_frac"], r["fp32_pipe_frac"]))
+    assert r["bound"] == ("hbm" if r["t_hbm_ms"] >= r["t_fp32_pipe_ms"] else "alu")
+
+
+def test_mixed_fp64_work_per_kernel():
+    """The mixed mode's FP64 count follows the kernel: 9 instructions and 11
+    flops per pair plus 3 / 5 per node on the warp-specialized kernel (3D,
+    n = 3..6), 35 flops per pair on the thread-per-line kernel."""
+    fl, ins = bench.mix_fp64_work(3, 4, 0)
+    assert (fl, ins) == (750 * 11 + 125 * 5, 750 * 9 + 125 * 3)
+    assert bench.mix_fp64_work(3, 7, 1)[0] == bench.pairs_per_element(3, 7) * 35

@@ -63,3 +63,53 @@ def test_gloo_world2_sharded_equals_whole(tmp_path):
     assert np.array_equal(parts, whole)
     for r in range(world):
         assert np.load(tmp_path / f"t{r}.npy")[0] == world   # max over ranks of 1, 2
+
+
+def _bench_worker(rank, world, port, out_dir):
+    """bench.py's timed region and throughput aggregation on a gloo world,
+    with a CPU stand-in for the device step (rank r sleeps (r + 1) ms per
+    step) and a host timer."""
+    import sys
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    r, w, _ = D.rank_world()
+    assert (r, w) == (rank, world)
+    calls = []
+
+    def step():
+        calls.append(1)
+        time.sleep(0.001 * (rank + 1))
+
+    def host_timer(fn, k):
+        t0 = time.perf_counter()
+        for _ in range(k):
+            fn()
+        dt = (time.perf_counter() - t0) * 1e3
+        return dt, dt / k
+
+    steps, warmup = 20, 3
+    t_total, t_launch = bench.timed_region(step, steps, warmup, dist, lambda: None, host_timer)
+    value = D.aggregate_throughput(1000.0, world, t_total / steps * 1e-3)
+    np.save(os.path.join(out_dir, f"b{rank}.npy"), np.array([t_total, t_launch, value, len(calls)]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_gloo_world2_bench_timed_region_takes_max_over_ranks(tmp_path):
+    world = 2
+    mp.start_processes(_bench_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True,
+                       start_method="spawn")
+    res = [np.load(tmp_path / f"b{r}.npy") for r in range(world)]
+    # every rank reports the same (maximum) duration: the slower rank's
+    assert res[0][0] == res[1][0]
+    assert res[0][0] >= 20 * 2.0 * 0.9          # rank 1 sleeps 2 ms per step
+    assert res[1][1] > res[0][1]                # per-rank launch means differ
+    # whole-job throughput: all ranks' units over the slowest rank's time
+    assert res[0][2] == pytest.approx(1000.0 * world / (res[0][0] / 20 * 1e-3))
+    # exactly warmup + steps calls of the step on each rank
+    assert res[0][3] == res[1][3] == 23

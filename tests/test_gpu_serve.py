@@ -116,9 +116,9 @@ def test_alone_equals_in_the_mix_and_parity():
             assert rel_err_per_var(got, ref) <= 1e-12
         else:
             ref = O.volume_sf(3, p, kind, O.FLUX_EULER, r["u"], r["Ja"])
-            ref_w = O.volume_sf(3, p, kind, O.FLUX_EULER, I.to_fp32(r["u"]).astype(np.float64), r["Ja"])
-            from tests.test_gpu_volume import kappa
-            fp32_check(got, ref, ref_w, lambda: kappa(3, p, kind, "euler", r["u"], r["Ja"], ref))
+            u32 = I.to_fp32(r["u"]).astype(np.float64)
+            ref_w = O.volume_sf(3, p, kind, O.FLUX_EULER, u32, r["Ja"])
+            fp32_check(got, ref, ref_w, terms=O.volume_absterms(3, p, kind, O.FLUX_EULER, u32, r["Ja"]))
 
 
 def test_admission_budget_oversize_and_tickets():

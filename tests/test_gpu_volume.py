@@ -16,7 +16,7 @@ import oracle as O
 from paper_2306_11665_gb300 import _abi as A
 from paper_2306_11665_gb300 import api
 from paper_2306_11665_gb300 import inputs as I
-from tests._entropy import identity_residual, kron_q
+from tests._entropy import identity_residual
 from tests._helpers import fp32_check, rel_err_per_var
 
 pytestmark = pytest.mark.gpu
@@ -63,20 +63,6 @@ def test_fp64_parity_small(d, flux, kind, p):
     assert rel_err_per_var(got, ref) <= 1e-12
 
 
-def kappa(d, p, kind, flux, u, Ja, r, n_el=3):
-    """kappa_v = max_i sum_{m,j} |Q_m,ij||F_m,ij,v| / max_i |r_i,v| on the first elements."""
-    E = min(u.shape[0], n_el)
-    S = np.zeros((E,) + u.shape[1:])
-    for e in range(E):
-        for m in range(d):
-            Q = kron_q(d, p, kind, m)
-            rows, cols = np.nonzero(Q)
-            for i, j in zip(rows, cols):
-                F = O.ec_flux(d, FLUXES[flux], u[e, :, i], u[e, :, j], Ja[e, m, :, i] + Ja[e, m, :, j])
-                S[e, :, i] += abs(Q[i, j]) * np.abs(F)
-    return [S[:, v].max() / np.abs(r[:E, v]).max() for v in range(u.shape[1])]
-
-
 @pytest.mark.parametrize("d, flux", CASES)
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("p", range(1, 9))
@@ -89,7 +75,8 @@ def test_fp32_parity_small(d, flux, kind, p, prec):
     ctx = api.Context(d, p, kind, flux)
     got, st = run_gpu(ctx, u32, Ja, prec)
     assert st == A.SFH_OK
-    fp32_check(got, ref, ref_w, lambda: kappa(d, p, kind, flux, u, Ja, ref))
+    S = O.volume_absterms(d, p, kind, FLUXES[flux], u32.astype(np.float64), Ja)
+    fp32_check(got, ref, ref_w, terms=S)
 
 
 def test_burgers_2d_full_config_fp64():
@@ -112,6 +99,7 @@ def _sampled(d, p, kind, N, precs, n_sample, seed):
     idx = np.unique(np.concatenate([[0, E - 1], rng.choice(E, size=n_sample, replace=False)]))
     ref = O.volume_sf(d, p, kind, O.FLUX_EULER, u[idx], Ja[idx])
     ref_w = O.volume_sf(d, p, kind, O.FLUX_EULER, I.to_fp32(u[idx]).astype(np.float64), Ja[idx])
+    S = O.volume_absterms(d, p, kind, O.FLUX_EULER, I.to_fp32(u[idx]).astype(np.float64), Ja[idx])
     ctx = api.Context(d, p, kind, "euler")
     out = {}
     for prec in precs:
@@ -122,8 +110,7 @@ def _sampled(d, p, kind, N, precs, n_sample, seed):
             out[prec] = {"per_variable_worst": float(rel_err_per_var(got[idx], ref))}
             assert out[prec]["per_variable_worst"] <= 1e-12
         else:
-            out[prec] = fp32_check(got[idx], ref, ref_w,
-                                   lambda: kappa(d, p, kind, "euler", u[idx], Ja[idx], ref))
+            out[prec] = fp32_check(got[idx], ref, ref_w, terms=S)
     return out, u, Ja, idx, ctx
 
 
@@ -188,8 +175,9 @@ def test_large_mesh_64bit_offsets(prec):
     if prec == "fp64":
         assert rel_err_per_var(got, ref) <= 1e-12
     else:
-        ref_w = O.volume_sf(3, 4, 0, O.FLUX_EULER, I.to_fp32(u[base]).astype(np.float64), Ja[base])
-        fp32_check(got, ref, ref_w, lambda: kappa(3, 4, 0, "euler", u[base], Ja[base], ref))
+        u32 = I.to_fp32(u[base]).astype(np.float64)
+        ref_w = O.volume_sf(3, 4, 0, O.FLUX_EULER, u32, Ja[base])
+        fp32_check(got, ref, ref_w, terms=O.volume_absterms(3, 4, 0, O.FLUX_EULER, u32, Ja[base]))
 
 
 @pytest.mark.parametrize("d, p, kind, flux", [(3, 4, 0, "euler"), (3, 7, 1, "euler"), (3, 3, 1, "euler"),
@@ -318,7 +306,8 @@ def test_rough_states_take_the_logarithm_path(d, p, kind):
     assert rel_err_per_var(got, ref) <= 1e-12
     u32 = I.to_fp32(u)
     ref_w = O.volume_sf(d, p, kind, O.FLUX_EULER, u32.astype(np.float64), Ja)
+    S = O.volume_absterms(d, p, kind, O.FLUX_EULER, u32.astype(np.float64), Ja)
     for prec in ("fp32k", "fp32mix"):
         got, st = run_gpu(ctx, u32, Ja, prec)
         assert st == A.SFH_OK
-        fp32_check(got, ref, ref_w, lambda: kappa(d, p, kind, "euler", u, Ja, ref))
+        fp32_check(got, ref, ref_w, terms=S)
