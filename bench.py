@@ -172,7 +172,7 @@ def fp32_kernel_name(d: int, p: int, modal: bool = False) -> str:
         return "volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, n)
     if d == 3 and n in (7, 8):
         return "volume_fp32_row_kernel<%d>" % n
-    if d == 3 and 3 <= n <= 6:
+    if d == 3 and 3 <= n <= 5:
         return "volume_fp32_ws_kernel<%d,%d,euler>" % (d, n)
     return "volume_fp32_tma_kernel<%d,%d,euler>" % (d, n)
 

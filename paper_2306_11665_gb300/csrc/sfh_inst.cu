@@ -98,7 +98,7 @@ cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_ele
 template <int D, int N, int FLUX>
 cudaError_t launch_mixed(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab, int *err,
                          cudaStream_t stream) {
-    if constexpr (use_ws_kernel<D, N, FLUX>())
+    if constexpr (use_ws_mixed<D, N, FLUX>())
         return launch_volume_fp32_ws<D, N, FLUX, true>(u, Ja, r, n_elem, tab, err, stream);
     else
         return launch_volume<D, N, FLUX, ModeMixed>(u, Ja, r, n_elem, tab, err, stream);

@@ -1,5 +1,5 @@
-// sfh_volume_ws.cuh -- warp-specialized persistent FP32 (Kahan) volume
-// residual of the 3D Euler fluxes at n = 3..6.
+// sfh_volume_ws.cuh -- warp-specialized persistent FP32 volume residual of
+// the 3D Euler fluxes: FP32-Kahan at n = 3..5, the mixed mode at n = 3..6.
 //
 // The arithmetic is that of the persistent line kernel (Eq. 3 with the Eq. 5
 // operators: one unordered line pair per flux evaluation, scattered to both
@@ -31,8 +31,15 @@
 
 namespace sfh {
 
+// FP32-Kahan: n = 3..5 (at n = 6 the line body spills under the 128
+// registers of twelve sweep warps and the thread-per-line kernel is faster);
+// mixed mode: n = 3..6
 template <int D, int N, int FLUX>
 constexpr bool use_ws_kernel() {
+    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 5;
+}
+template <int D, int N, int FLUX>
+constexpr bool use_ws_mixed() {
     return D == 3 && is_euler(FLUX) && N >= 3 && N <= 6;
 }
 
@@ -46,9 +53,10 @@ struct WsShape {
     // primitives as three float2 per node: (rho, beta), (v0/2, v1/2), (v2/2, p)
     static constexpr int P2_EL = 3 * NN;
     static constexpr int TASKS_EL = D * NLINE;
-    // the mixed mode's line body needs more registers: eight sweep warps
-    // (twelve warps in all, three per sub-partition: 168 registers each)
-    static constexpr int SVC_WARPS = 4, MAX_SWEEP_WARPS = MIX ? 8 : 12;
+    // twelve sweep warps (three per sub-partition) also in the mixed mode:
+    // its FP64 chains are latency-bound, and more warps beat more registers
+    // per warp (653 against 763 us at p = 4 with eight warps of 168 registers)
+    static constexpr int SVC_WARPS = 4, MAX_SWEEP_WARPS = 12;
     static constexpr int SVC_THREADS = 32 * SVC_WARPS;
     static constexpr int RAW_EL = 4 * U_EL + 8 * J_EL;
     // double-buffered raw staging, primitives and residual slices (the mixed
@@ -635,6 +643,8 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
             const BlockPlan pl = plan(k);
             const float *R0 = R(k & 1);
             float *gR = r + pl.e0 * U_EL;
+            // unrolled: independent loads of several outputs in flight per thread
+#pragma unroll 8
             for (int s = st; s < pl.ne * U_EL; s += S::SVC_THREADS) {
                 float t = R0[s] + R0[S::R_SLICE + s];
                 t += R0[2 * S::R_SLICE + s];
