@@ -136,7 +136,8 @@ TRAFFIC = {
 # The sources that define the timed kernels' code: the persistent FP32 kernel
 # and its building blocks, and the instantiation unit; with the compiler flags.
 # (Other files of the library hold only other kernels and host code.)
-KERNEL_SOURCES = ("sfh_volume_ws.cuh", "sfh_volume_tma.cuh", "sfh_tma.cuh", "sfh_device.cuh", "sfh_inst.cu")
+KERNEL_SOURCES = ("sfh_volume_ws.cuh", "sfh_volume_tma.cuh", "sfh_tma.cuh", "sfh_debug.cuh", "sfh_device.cuh",
+                  "sfh_inst.cu")
 
 
 def _kernel_sources_sha1():
@@ -172,7 +173,7 @@ def fp32_kernel_name(d: int, p: int, modal: bool = False) -> str:
         return "volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, n)
     if d == 3 and n in (7, 8):
         return "volume_fp32_row_kernel<%d>" % n
-    if d == 3 and 3 <= n <= 5:
+    if d == 3 and 3 <= n <= 6:
         return "volume_fp32_ws_kernel<%d,%d,euler>" % (d, n)
     return "volume_fp32_tma_kernel<%d,%d,euler>" % (d, n)
 

@@ -57,7 +57,8 @@ typedef enum {
     SFH_EBUSY = 5,         /* the server cannot take the request now */
     SFH_ENOTREADY = 6,     /* a polled request has not completed yet */
     SFH_ETIMEOUT = 7,      /* a bounded wait gave up */
-    SFH_EUNSUPPORTED = 8   /* valid but not provided (e.g. no CUDA device) */
+    SFH_EUNSUPPORTED = 8,  /* valid but not provided (e.g. no CUDA device) */
+    SFH_EBOUNDS = 9        /* debug build only: a kernel index left its buffer (the access was not made) */
 } sfh_status;
 
 typedef enum { SFH_NODES_GLL = 0, SFH_NODES_GAUSS = 1 } sfh_nodes;
@@ -309,6 +310,35 @@ sfh_status sfh_peak_fma(sfh_prec prec, double *tflops, double *ms);
  * CUDA error.  *elapsed_us (optional) receives the device-measured wait.
  * ------------------------------------------------------------------------- */
 sfh_status sfh_selftest_bounded_wait(int64_t limit_us, sfh_stream_t stream, double *elapsed_us);
+
+/* ---------------------------------------------------------------------------
+ * Build variant (no paper counterpart).  Returns a bit set: SFH_BUILD_DEBUG
+ * when this library is the bounds-checked debug build (libsfhad_debug.so,
+ * compiled with -DSFH_DEBUG).  In that build every kernel addresses global and
+ * shared memory through checked pointers that know their buffer: an index
+ * outside it latches a bit in the call's device error word, the access is
+ * not made (a load reads a scratch word, a store is dropped, a bulk copy is
+ * not issued and its mbarrier bytes are released), no thread leaves early and
+ * no barrier is skipped; the next sfh_check (or the synchronous call) returns
+ * SFH_EBOUNDS.  The release library (libsfhad.so) has no checks; its kernels
+ * are the same code as without the checked pointers.
+ * ------------------------------------------------------------------------- */
+#define SFH_BUILD_DEBUG 1
+int sfh_build_flags(void);
+
+/* ---------------------------------------------------------------------------
+ * Self-test of the debug build's bounds checks (no paper counterpart).
+ * Launches one thread on the current device with a checked pointer over the
+ * first 64 words of a 128-word device buffer (so even an unchecked access
+ * would stay inside the allocation): it reads word 64 and writes word 65,
+ * both outside the pointer's extent, and writes word 0, inside it.
+ * Synchronous on `stream`.
+ * Returns SFH_OK when the checks latched the bounds bit, skipped the write
+ * outside the extent and made the one inside it; SFH_EBOUNDS if they did not
+ * (a defect); SFH_EUNSUPPORTED in the release build (nothing is launched);
+ * SFH_ECUDA for a CUDA error.
+ * ------------------------------------------------------------------------- */
+sfh_status sfh_selftest_bounds(sfh_stream_t stream);
 
 /* ---------------------------------------------------------------------------
  * Serving: batched residual and VJP requests of mixed degree p, element

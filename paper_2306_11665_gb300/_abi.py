@@ -12,13 +12,19 @@ import ctypes
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsfhad.so")
+# SFH_LIB_VARIANT=debug loads the bounds-checked debug build instead
+LIB_VARIANT = os.environ.get("SFH_LIB_VARIANT", "")
+if LIB_VARIANT not in ("", "release", "debug"):
+    raise RuntimeError(f"SFH_LIB_VARIANT must be 'release' or 'debug', got {LIB_VARIANT!r}")
+LIB_PATH = os.path.join(HERE, "libsfhad_debug.so" if LIB_VARIANT == "debug" else "libsfhad.so")
 
 # enums (mirror include/sfhad.h)
 SFH_OK, SFH_EINVAL, SFH_ENOMEM, SFH_ECUDA, SFH_EDOMAIN = 0, 1, 2, 3, 4
-SFH_EBUSY, SFH_ENOTREADY, SFH_ETIMEOUT, SFH_EUNSUPPORTED = 5, 6, 7, 8
+SFH_EBUSY, SFH_ENOTREADY, SFH_ETIMEOUT, SFH_EUNSUPPORTED, SFH_EBOUNDS = 5, 6, 7, 8, 9
 STATUS_NAMES = {0: "SFH_OK", 1: "SFH_EINVAL", 2: "SFH_ENOMEM", 3: "SFH_ECUDA", 4: "SFH_EDOMAIN",
-                5: "SFH_EBUSY", 6: "SFH_ENOTREADY", 7: "SFH_ETIMEOUT", 8: "SFH_EUNSUPPORTED"}
+                5: "SFH_EBUSY", 6: "SFH_ENOTREADY", 7: "SFH_ETIMEOUT", 8: "SFH_EUNSUPPORTED",
+                9: "SFH_EBOUNDS"}
+SFH_BUILD_DEBUG = 1
 SFH_NODES_GLL, SFH_NODES_GAUSS = 0, 1
 SFH_FLUX_BURGERS, SFH_FLUX_EULER_RANOCHA, SFH_FLUX_EULER_CHANDRASHEKAR = 0, 1, 2
 SFH_FP64, SFH_FP32_KAHAN, SFH_FP32_MIXED = 0, 1, 2
@@ -75,6 +81,8 @@ _SIGS = {
     "sfh_entropy_residual": [vp, i64, vp, vp, vp, ctypes.c_int, vp, vp],
     "sfh_fig1_hadamard": [ctypes.c_int, i64, vp, vp, ctypes.c_int, vp],
     "sfh_selftest_bounded_wait": [ctypes.c_int64, ctypes.c_void_p, dp],
+    "sfh_selftest_bounds": [ctypes.c_void_p],
+    "sfh_build_flags": [],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
     "sfh_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(Result)],
@@ -208,6 +216,16 @@ def sfh_peak_fma(prec: int):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _call("sfh_peak_fma", prec, ctypes.byref(tf), ctypes.byref(ms))
     return tf.value, ms.value
+
+
+def sfh_build_flags() -> int:
+    return lib().sfh_build_flags()
+
+
+def sfh_selftest_bounds(stream: int = 0) -> int:
+    """Status of the debug build's bounds self-test (SFH_OK or, in the release
+    library, SFH_EUNSUPPORTED)."""
+    return _call("sfh_selftest_bounds", stream, ok=(SFH_OK, SFH_EUNSUPPORTED))
 
 
 def sfh_selftest_bounded_wait(limit_us: int, stream: int = 0):

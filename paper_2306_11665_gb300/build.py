@@ -5,6 +5,13 @@ mode and dimension) that compile in parallel; the host API, the serving
 runtime and the peak benchmarks are separate objects.  Objects are rebuilt
 when their source or any header is newer.  Output:
 ``paper_2306_11665_gb300/libsfhad.so`` (objects under ``_build/``).
+
+``build(debug=True)`` (or ``python -m paper_2306_11665_gb300.build --debug``)
+builds the bounds-checked debug library ``libsfhad_debug.so`` from the same
+sources with ``-DSFH_DEBUG`` (objects under ``_build_debug/``): every kernel
+index into global and shared memory is checked against its buffer, and an
+index outside it is reported as SFH_EBOUNDS instead of being used.  The
+binding loads it when ``SFH_LIB_VARIANT=debug``.
 """
 from __future__ import annotations
 
@@ -19,6 +26,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsfhad.so")
+OUT_DEBUG = os.path.join(HERE, "_build_debug")
+LIB_DEBUG = os.path.join(HERE, "libsfhad_debug.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -49,12 +58,12 @@ def nvcc() -> str:
     return exe
 
 
-def _units():
+def _units(out=OUT, defs0=()):
     units = []
     for name, defs in INST:
-        units.append((os.path.join(CSRC, "sfh_inst.cu"), os.path.join(OUT, f"inst_{name}.o"), defs))
+        units.append((os.path.join(CSRC, "sfh_inst.cu"), os.path.join(out, f"inst_{name}.o"), list(defs0) + defs))
     for src in ("sfh_api.cu", "sfh_serve.cu", "sfh_noalloc.cu", "sfh_entropy.cu", "sfh_fig1.cu", "sfh_surface.cu"):
-        units.append((os.path.join(CSRC, src), os.path.join(OUT, src.replace(".cu", ".o")), []))
+        units.append((os.path.join(CSRC, src), os.path.join(out, src.replace(".cu", ".o")), list(defs0)))
     return units
 
 
@@ -76,10 +85,12 @@ def _compile(src, obj, defs, extra, verbose):
     return res.stdout + res.stderr if verbose else ""
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=()) -> str:
-    """Compile every CUDA unit for sm_103a and link libsfhad.so; returns its path."""
-    os.makedirs(OUT, exist_ok=True)
-    units = _units()
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile every CUDA unit for sm_103a and link libsfhad.so (debug: the
+    bounds-checked libsfhad_debug.so); returns its path."""
+    out, lib_path = (OUT_DEBUG, LIB_DEBUG) if debug else (OUT, LIB)
+    os.makedirs(out, exist_ok=True)
+    units = _units(out, ["-DSFH_DEBUG"] if debug else [])
     todo = [u for u in units if force or _stale(u[0], u[1])]
     jobs = jobs or max(1, min(len(todo) or 1, os.cpu_count() or 1))
     logs = []
@@ -89,20 +100,20 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
             for f in futs:
                 logs.append(f.result())
     objs = [u[1] for u in units]
-    if todo or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib_path) or any(os.path.getmtime(o) > os.path.getmtime(lib_path) for o in objs):
+        tmp = lib_path + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{' '.join(cmd)}\n{res.stdout}\n{res.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib_path)
     if verbose:
         sys.stdout.write("".join(logs))
-    return LIB
+    return lib_path
 
 
 if __name__ == "__main__":
     v = "-v" in sys.argv
     f = "-f" in sys.argv
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(force=f or bool(extra), verbose=v or bool(extra), extra=extra))
+    print(build(force=f or bool(extra), verbose=v or bool(extra), extra=extra, debug="--debug" in sys.argv))

@@ -569,6 +569,8 @@ extern "C" sfh_status sfh_check(sfh_ctx *c, sfh_stream_t stream) {
 
 namespace sfh {
 int err_word_status(int h) {
+    if (h & kErrBounds)
+        return fail(SFH_EBOUNDS, "debug build: a kernel index left its buffer (the access was not made)");
     if (h & kErrTimeout) return fail(SFH_ETIMEOUT, "a bounded device wait gave up");
     if ((h & kErrDomain) && (h & kErrMetric))
         return fail(SFH_EDOMAIN, "density or pressure <= 0 (or NaN) in the state, and a metric term out of range "
@@ -677,6 +679,51 @@ extern "C" sfh_status sfh_selftest_bounded_wait(int64_t limit_us, sfh_stream_t s
     if (elapsed_us) *elapsed_us = (double)h[1];
     if (h[0] == sfh::kErrTimeout) return fail(SFH_ETIMEOUT, "bounded wait gave up after %d us (expected)", h[1]);
     return SFH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// build variant and the debug build's bounds self-test
+// ---------------------------------------------------------------------------
+extern "C" int sfh_build_flags(void) { return sfh::kDebugBuild ? SFH_BUILD_DEBUG : 0; }
+
+#ifdef SFH_DEBUG
+// a checked pointer over buf[0, n) of a 2n-word buffer: word n is read and
+// word n + 1 written (both refused: outside the extent, inside the
+// allocation), word 0 written (made)
+__global__ void bounds_selftest_kernel(int *buf, int n, int *err, int *out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const auto p = sfh::bp(buf, n, err);
+    out[0] = p[n];
+    p[n + 1] = 12345;
+    p[0] = 777;
+}
+#endif
+
+extern "C" sfh_status sfh_selftest_bounds(sfh_stream_t stream) {
+    clear_err();
+#ifdef SFH_DEBUG
+    constexpr int n = 64;
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, (2 * n + 2) * sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc");
+    cudaStream_t s = (cudaStream_t)stream;
+    int h[2 * n + 2];
+    int *err = d + 2 * n, *out = d + 2 * n + 1;
+    if ((e = cudaMemsetAsync(d, 0, sizeof h, s)) == cudaSuccess) {
+        bounds_selftest_kernel<<<1, 32, 0, s>>>(d, n, err, out);
+        if ((e = cudaGetLastError()) == cudaSuccess && (e = cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, s)) == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+    }
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "bounds self-test kernel");
+    const int herr = h[2 * n];
+    if ((herr & sfh::kErrBounds) && h[n + 1] == 0 && h[0] == 777) return SFH_OK;
+    return fail(SFH_EBOUNDS, "bounds checks did not act as designed (error word %d, word n+1 = %d, word 0 = %d)", herr,
+                h[n + 1], h[0]);
+#else
+    (void)stream;
+    return fail(SFH_EUNSUPPORTED, "the release library has no bounds checks (build with debug=True)");
+#endif
 }
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "sfh_debug.cuh"
 #include "sfh_tma.cuh"
 
 namespace sfh {
@@ -55,10 +56,11 @@ constexpr int kPassPlain = 0, kPassFirst = 1, kPassLast = 2;
 // compile-time constants.  ROLE (forward, const_mode): kPassFirst drops the
 // constant coefficient u_hat_0 (read from `coef`, the pass-0 input), kPassLast
 // adds c = u_hat_0 c0 to every output.
-template <typename T, int D, int N, bool TRANSPOSE, int ROLE = kPassPlain, typename TI, typename TO,
-          typename TC = TI>
-__device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq, const BasisTab<T> &bt, int tid,
-                                           int nthreads, const TC *coef = nullptr) {
+// in, out and coef are pointers or checked pointers (BPtr) to the elements.
+template <typename T, int D, int N, bool TRANSPOSE, int ROLE = kPassPlain, typename PI, typename PO,
+          typename PC = const T *>
+__device__ __forceinline__ void basis_pass(PI in, PO out, int m, int nq, const BasisTab<T> &bt, int tid,
+                                           int nthreads, PC coef = nullptr) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
     for (int t = tid; t < nq * NLINE; t += nthreads) {
@@ -66,8 +68,8 @@ __device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq,
         int base;
         if constexpr (D == 3) base = m == 0 ? N * l : (m == 1 ? l % N + N * N * (l / N) : l);
         else base = m == 0 ? N * l : l;
-        const TI *src = in + (size_t)q * NN + base;
-        TO *dst = out + (size_t)q * NN + base;
+        const auto src = in + (size_t)q * NN + base;
+        const auto dst = out + (size_t)q * NN + base;
         T x[N];
 #pragma unroll
         for (int b = 0; b < N; ++b) x[b] = (T)src[b * stride];
@@ -84,7 +86,7 @@ __device__ __forceinline__ void basis_pass(const TI *in, TO *out, int m, int nq,
 #pragma unroll
             for (int b = 0; b < N; ++b) s = fma(TRANSPOSE ? bt.V[b * N + a] : bt.V[a * N + b], x[b], s);
             if constexpr (ROLE == kPassLast) s += c;
-            dst[a * stride] = (TO)s;
+            dst[a * stride] = s;
         }
     }
 }

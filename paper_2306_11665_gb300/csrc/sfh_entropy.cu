@@ -47,16 +47,16 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
     using S = EntShape<D, N, FLUX>;
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NS = S::NS;
     extern __shared__ __align__(16) double sm[];
-    double *sS = sm;                      // [NS][NN]
-    double *sW = sS + NS * NN;            // [NVAR][NN]
-    double *sPsi = sW + NVAR * NN;        // [D][NN]
+    const auto sS = SFH_BP(sm, NS * NN, err);                             // [NS][NN]
+    const auto sW = SFH_BP(sm + NS * NN, NVAR * NN, err);                 // [NVAR][NN]
+    const auto sPsi = SFH_BP(sm + (NS + NVAR) * NN, D * NN, err);         // [D][NN]
     __shared__ double red[3][kEntThreads];
 
     const int64_t e = blockIdx.x;
     const int tid = threadIdx.x;
-    const double *ue = u + e * NVAR * NN;
-    const TR *re = r + e * NVAR * NN;
-    const double *Je = Ja + e * D * D * NN;
+    const auto ue = SFH_BP(u, n_elem * NVAR * NN, err) + e * NVAR * NN;
+    const auto re = SFH_BP(r, n_elem * NVAR * NN, err) + e * NVAR * NN;
+    const auto Je = SFH_BP(Ja, n_elem * D * D * NN, err) + e * D * D * NN;
 
     // ---- node pass: states, entropy variables, potentials; w^T r
     double lhs = 0.0, rhs = 0.0, scale = 0.0;
@@ -116,7 +116,7 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
             omega = tab.w[l];
         }
         const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
-        const double *Jm = Je + m * D * NN;   // Ja^m_k(i) = Jm[k * NN + i]
+        const auto Jm = Je + m * D * NN;   // Ja^m_k(i) = Jm[k * NN + i]
         double t1 = 0.0;
         // the psi terms: -1/2 sum_a (E 1)_a psi_a.J_a - 1/2 sum_ab E_ab psi_a.J_b + sum_ab Q_ab psi_a.J_b
         double tpsi = 0.0;
@@ -212,7 +212,7 @@ entropy_identity_kernel(const double *__restrict__ u, const double *__restrict__
         }
         __syncthreads();
     }
-    if (tid == 0) out[e] = fabs(red[0][0] - red[1][0]) / red[2][0];
+    if (tid == 0) SFH_BP(out, n_elem, err)[e] = fabs(red[0][0] - red[1][0]) / red[2][0];
 }
 
 template <int D, int N, int FLUX, typename TR>

@@ -173,32 +173,37 @@ __host__ __device__ inline int tile_epb(int kind, int prec, int n) {
 template <int N>
 __device__ __noinline__ void run_vjp(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
                                      unsigned char *smem) {
-    vjp_tile<3, N, kFluxEuler, typename Cls<N>::VJP>(static_cast<const double *>(q.u), q.Ja, q.lam,
-                                                     static_cast<double *>(q.out), e0, ne, td, err, smem);
+    const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
+    vjp_tile<3, N, kFluxEuler, typename Cls<N>::VJP>(SFH_BP(static_cast<const double *>(q.u), nu, err), SFH_BP(q.Ja, nj, err),
+                                                     SFH_BP(q.lam, nu, err), SFH_BP(static_cast<double *>(q.out), nu, err), e0,
+                                                     ne, td, err, smem);
 }
 template <int N>
 __device__ __noinline__ void run_f64(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
                                      unsigned char *smem) {
-    volume_tile<3, N, kFluxEuler, ModeFP64, typename Cls<N>::F64>(static_cast<const double *>(q.u), q.Ja,
-                                                                  static_cast<double *>(q.out), e0, ne, td, err, smem);
+    const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
+    volume_tile<3, N, kFluxEuler, ModeFP64, typename Cls<N>::F64>(SFH_BP(static_cast<const double *>(q.u), nu, err),
+                                                                  SFH_BP(q.Ja, nj, err),
+                                                                  SFH_BP(static_cast<double *>(q.out), nu, err), e0, ne,
+                                                                  td, err, smem);
 }
 template <int N>
 __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
                                      unsigned char *smem) {
     using S = ServeF32<N>;
-    float *sP = reinterpret_cast<float *>(smem);
-    float *sJF = reinterpret_cast<float *>(smem + S::OFF_JF);
-    float *sR = reinterpret_cast<float *>(smem + S::OFF_R);
-    float *rawU = reinterpret_cast<float *>(smem + S::OFF_RU);
-    double *rawJ = reinterpret_cast<double *>(smem + S::OFF_RJ);
+    const auto sP = SFH_BP(reinterpret_cast<float *>(smem), S::EPB * S::NP * S::NN, err);
+    const auto sJF = SFH_BP(reinterpret_cast<float *>(smem + S::OFF_JF), S::EPB * S::JF_EL, err);
+    const auto sR = SFH_BP(reinterpret_cast<float *>(smem + S::OFF_R), S::D * S::EPB * S::U_EL, err);
+    const auto rawU = SFH_BP(reinterpret_cast<float *>(smem + S::OFF_RU), S::EPB * S::U_EL, err);
+    const auto rawJ = SFH_BP(reinterpret_cast<double *>(smem + S::OFF_RJ), S::EPB * S::J_EL, err);
     // the raw u and Ja of a sub-block arrive by per-thread asynchronous copies,
     // issued while the previous sub-block is swept
     auto fetch = [&](int b0) {
         const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
-        const float *U = static_cast<const float *>(q.u) + (e0 + b0) * S::U_EL;
-        const double *J = q.Ja + (e0 + b0) * S::J_EL;
-        for (int s = threadIdx.x; s < nb * S::U_EL; s += kThreads) cp_async4(rawU + s, U + s);
-        for (int s = threadIdx.x; s < nb * S::J_EL; s += kThreads) cp_async8(rawJ + s, J + s);
+        const auto U = SFH_BP(static_cast<const float *>(q.u), (int64_t)q.n_elem * S::U_EL, err) + (e0 + b0) * S::U_EL;
+        const auto J = SFH_BP(q.Ja, (int64_t)q.n_elem * S::J_EL, err) + (e0 + b0) * S::J_EL;
+        for (int s = threadIdx.x; s < nb * S::U_EL; s += kThreads) cp_async4_ck(rawU + s, U + s);
+        for (int s = threadIdx.x; s < nb * S::J_EL; s += kThreads) cp_async8_ck(rawJ + s, J + s);
         cp_async_commit();
     };
     int bad = 0;
@@ -212,7 +217,8 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         if (b0 + S::EPB < ne) fetch(b0 + S::EPB);
         fp32_block_sweep<S, 3, N, kFluxEuler>(threadIdx.x, nb, sP, sJF, sR, tf);
         __syncthreads();
-        fp32_block_store<S, 3>(sR, static_cast<float *>(q.out) + (e0 + b0) * S::U_EL, nb, threadIdx.x, kThreads);
+        fp32_block_store<S, 3>(sR, SFH_BP(static_cast<float *>(q.out), (int64_t)q.n_elem * S::U_EL, err) + (e0 + b0) * S::U_EL,
+                               nb, threadIdx.x, kThreads);
         __syncthreads();
     }
     if (bad) atomicOr(err, bad);
@@ -220,8 +226,11 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
 template <int N>
 __device__ __noinline__ void run_mix(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
                                      unsigned char *smem) {
-    volume_tile<3, N, kFluxEuler, ModeMixed, typename Cls<N>::MIX>(static_cast<const float *>(q.u), q.Ja,
-                                                                   static_cast<float *>(q.out), e0, ne, tf, err, smem);
+    const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
+    volume_tile<3, N, kFluxEuler, ModeMixed, typename Cls<N>::MIX>(SFH_BP(static_cast<const float *>(q.u), nu, err),
+                                                                   SFH_BP(q.Ja, nj, err),
+                                                                   SFH_BP(static_cast<float *>(q.out), nu, err), e0, ne,
+                                                                   tf, err, smem);
 }
 
 template <int N>
@@ -306,6 +315,13 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
         const Req &q = s_req;
         const int slot = s_slot;
         const int tabi = q.nodes * 10 + q.n;
+        // debug build: a descriptor whose slot or operator-table index leaves
+        // its array is skipped, with kErrBounds latched in slot 0's error word
+        // (the skipped request never completes and times out on the host)
+        if (kDebugBuild && !dbg_require((unsigned)slot < (unsigned)kMaxSlots && (unsigned)tabi < 20u, &a.ctrl->err[0])) {
+            __syncthreads();
+            continue;
+        }
         for (int i = threadIdx.x; i < (int)(sizeof(OpTab<double>) / 8); i += blockDim.x)
             reinterpret_cast<double *>(&s_td)[i] = reinterpret_cast<const double *>(a.tabd + tabi)[i];
         for (int i = threadIdx.x; i < (int)(sizeof(OpTab<float>) / 4); i += blockDim.x)
@@ -344,7 +360,9 @@ __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constan
                 a.ctrl->done_tiles[slot] = 0;
                 __threadfence_system();
                 volatile Done *dn = a.done + slot;
-                dn->status = st ? (st & kErrTimeout ? SFH_ETIMEOUT : SFH_EDOMAIN) : SFH_OK;
+                dn->status = st ? ((kDebugBuild && (st & kErrBounds)) ? SFH_EBOUNDS
+                                                                      : (st & kErrTimeout ? SFH_ETIMEOUT : SFH_EDOMAIN))
+                                : SFH_OK;
                 dn->t_start = ts;
                 __threadfence_system();
                 dn->seq = q.seq;

@@ -37,7 +37,7 @@ struct SurfShape {
 };
 
 template <int D>
-__device__ __forceinline__ EulerNodeD<D> euler_node_from_u(const double *u, int stride, bool &bad) {
+__device__ __forceinline__ EulerNodeD<D> euler_node_from_u(BPtr<const double> u, int stride, bool &bad) {
     EulerNodeD<D> nd;
     const double rho = u[0], E = u[(D + 1) * stride], irho = rcp_nr(rho);
     double ke = 0.0;
@@ -67,8 +67,14 @@ surface_kernel(const double *__restrict__ u, const double *__restrict__ u_face, 
     using S = SurfShape<D, N, FLUX>;
     constexpr int NN = S::NN, NF = S::NF, NVAR = S::NVAR, NS = S::NS, EPB = S::EPB;
     extern __shared__ __align__(16) double sm[];
-    double *sS = sm;                       // [EPB][NS][NN]
-    double *sR = sS + EPB * NS * NN;       // [EPB][NVAR][NN]
+    const auto sS = SFH_BP(sm, EPB * NS * NN, err);                    // [EPB][NS][NN]
+    const auto sR = SFH_BP(sm + EPB * NS * NN, EPB * NVAR * NN, err);  // [EPB][NVAR][NN]
+    // the inputs and outputs over their whole extents
+    const auto gu = SFH_BP(u, n_elem * NVAR * NN, err);
+    const auto guf = SFH_BP(u_face, n_elem * 2 * D * NVAR * NF, err);
+    const auto gnJ = SFH_BP(nJ, n_elem * 2 * D * D * NF, err);
+    const auto grv = SFH_BP(r_vol, n_elem * NVAR * NN, err);
+    const auto grf = SFH_BP(r_face, n_elem * 2 * D * NVAR * NF, err);
     const int64_t e0 = (int64_t)blockIdx.x * EPB;
     const int ne = (int)((n_elem - e0) < EPB ? (n_elem - e0) : EPB);
     const int tid = threadIdx.x;
@@ -77,8 +83,8 @@ surface_kernel(const double *__restrict__ u, const double *__restrict__ u_face, 
     // ---- volume primitives, zero the volume sums
     for (int s = tid; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
-        const double *ue = u + (e0 + el) * NVAR * NN + i;
-        double *se = sS + el * NS * NN + i;
+        const auto ue = gu + (e0 + el) * NVAR * NN + i;
+        const auto se = sS + el * NS * NN + i;
         if constexpr (is_euler(FLUX)) {
             const EulerNodeD<D> nd = euler_node_from_u<D>(ue, NN, bad);
             se[0] = nd.rho;
@@ -115,13 +121,13 @@ surface_kernel(const double *__restrict__ u, const double *__restrict__ u_face, 
                 wf = tab.w[b0];
             }
             const int64_t fo = ((e0 + el) * 2 * D + face);
-            const double *uf = u_face + fo * NVAR * NF + f;
-            const double *nf = nJ + fo * D * NF + f;
+            const auto uf = guf + fo * NVAR * NF + f;
+            const auto nf = gnJ + fo * D * NF + f;
             double acc[NVAR];
 #pragma unroll
             for (int v = 0; v < NVAR; ++v) acc[v] = 0.0;
-            const double *se = sS + el * NS * NN;
-            double *re = sR + el * NVAR * NN;
+            BPtr<const double> se = sS + el * NS * NN;
+            const auto re = sR + el * NVAR * NN;
             if constexpr (is_euler(FLUX)) {
                 EulerNodeD<D> A = euler_node_from_u<D>(uf, NF, bad);
 #pragma unroll
@@ -166,7 +172,7 @@ surface_kernel(const double *__restrict__ u, const double *__restrict__ u_face, 
                     re[j] += h;
                 }
             }
-            double *rf = r_face + fo * NVAR * NF + f;
+            const auto rf = grf + fo * NVAR * NF + f;
 #pragma unroll
             for (int v = 0; v < NVAR; ++v) rf[v * NF] = acc[v];
         }
@@ -175,7 +181,7 @@ surface_kernel(const double *__restrict__ u, const double *__restrict__ u_face, 
     if (bad) atomicOr(err, kErrDomain);
 
     // ---- write the volume sums
-    double *rb = r_vol + e0 * NVAR * NN;
+    const auto rb = grv + e0 * NVAR * NN;
     for (int s = tid; s < ne * NVAR * NN; s += blockDim.x) rb[s] = sR[s];
 }
 

@@ -17,6 +17,7 @@ constexpr int kMaxDevices = 64;  // launch facts are cached per device index bel
 constexpr int kErrDomain = 1;    // density or pressure <= 0 (or NaN)
 constexpr int kErrTimeout = 2;   // a bounded wait gave up
 constexpr int kErrMetric = 4;    // a metric term outside the accepted range (see below)
+constexpr int kErrBounds = 8;    // debug build: an index outside its buffer (access not made)
 
 // Accepted metric terms, compared on the high word of |Ja| (sign cleared):
 // FP32 modes take |Ja| < 2^126, so that its FP32 value and the sum of two of

@@ -107,18 +107,19 @@ __device__ __forceinline__ void euler_pair_vjp(const double *PA, const double *P
 // V^T r_v(V u_hat): the transforms run in shared memory (the primitive,
 // adjoint and lambda buffers serve as scratch).
 template <int D, int N, int FLUX, class S = VjpShape<D, N, FLUX>, bool MODAL = false>
-__device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const double *__restrict__ Ja,
-                                         const double *__restrict__ lam, double *__restrict__ g, int64_t e0, int ne,
+__device__ __forceinline__ void vjp_tile(BPtr<const double> SFH_RESTRICT u, BPtr<const double> SFH_RESTRICT Ja,
+                                         BPtr<const double> SFH_RESTRICT lam, BPtr<double> SFH_RESTRICT g, int64_t e0, int ne,
                                          const OpTab<double> &tab, int *__restrict__ err, unsigned char *smem_raw,
                                          const BasisTab<double> *bt = nullptr) {
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB;
-    double *sP = reinterpret_cast<double *>(smem_raw);   // [EPB][NP][NN]
-    double *sA = sP + EPB * NP * NN;                       // [EPB][NP][NN] adjoints of primitives
-    double *sL = sA + EPB * NP * NN;                       // [EPB][NVAR][NN] lambda
-    double *sJ = sL + EPB * NVAR * NN;                     // [EPB][D][NN]
+    double *const s0 = reinterpret_cast<double *>(smem_raw);
+    const auto sP = SFH_BP(s0, EPB * NP * NN, err);                                    // [EPB][NP][NN]
+    const auto sA = SFH_BP(s0 + EPB * NP * NN, EPB * NP * NN, err);                    // adjoints of primitives
+    const auto sL = SFH_BP(s0 + 2 * EPB * NP * NN, EPB * NVAR * NN, err);              // [EPB][NVAR][NN] lambda
+    const auto sJ = SFH_BP(s0 + 2 * EPB * NP * NN + EPB * NVAR * NN, EPB * D * NN, err);   // [EPB][D][NN]
 
-    const double *ub = u + e0 * NVAR * NN;
-    const double *lb = lam + e0 * NVAR * NN;
+    BPtr<const double> ub = u + e0 * NVAR * NN;
+    const auto lb = lam + e0 * NVAR * NN;
     if constexpr (MODAL) {
         // lambda_v = V lambda_hat into sL, then u_v = V u_hat into sA ([el][var][i])
         const int nq = ne * NVAR, t = threadIdx.x, nt = blockDim.x;
@@ -150,8 +151,8 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
     bool bad = false;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
-        const double *ue = ub + (int64_t)el * NVAR * NN + i;
-        double *pe = sP + el * NP * NN + i;
+        const auto ue = ub + (int64_t)el * NVAR * NN + i;
+        const auto pe = sP + el * NP * NN + i;
         if constexpr (is_euler(FLUX)) {
             const double rho = ue[0], E = ue[(D + 1) * NN], irho = rcp_nr(rho);
             double ke = 0.0;
@@ -187,7 +188,7 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
         for (int s2 = threadIdx.x; s2 < ne * NP * NN; s2 += blockDim.x) sA[s2] = 0.0;
     }
 
-    const double *Jb = Ja + e0 * D * D * NN;
+    const auto Jb = Ja + e0 * D * D * NN;
     uint32_t hmax = 0;   // largest |Ja| high word: Inf and NaN are refused
 #pragma unroll 1
     for (int m = 0; m < D; ++m) {
@@ -263,13 +264,13 @@ __device__ __forceinline__ void vjp_tile(const double *__restrict__ u, const dou
 
     // ---- 3. primitive adjoints -> conservative adjoints; write g (modal:
     //      g_v into sL, then g_hat = V^T g_v)
-    double *gbp = g + e0 * NVAR * NN;
-    double *gdst = MODAL ? sL : gbp;
+    const auto gbp = g + e0 * NVAR * NN;
+    const auto gdst = MODAL ? sL : gbp;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
-        const double *pe = sP + el * NP * NN + i;
-        const double *ae = sA + el * NP * NN + i;
-        double *ge = gdst + (int64_t)el * NVAR * NN + i;
+        const auto pe = sP + el * NP * NN + i;
+        const auto ae = sA + el * NP * NN + i;
+        const auto ge = gdst + (int64_t)el * NVAR * NN + i;
         if constexpr (is_euler(FLUX)) {
             const double rho = pe[0], p = pe[(D + 1) * NN], beta = pe[(D + 2) * NN];
             const double irho = rcp_nr(rho), ip = rcp_nr(p);
@@ -316,7 +317,9 @@ vjp_modal_kernel(const double *__restrict__ u, const double *__restrict__ Ja, co
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    vjp_tile<D, N, FLUX, S, true>(u, Ja, lam, g, e0, ne, tab, err, smem_raw, &bt);
+    const int64_t nu = n_elem * S::NVAR * S::NN;
+    vjp_tile<D, N, FLUX, S, true>(SFH_BP(u, nu, err), SFH_BP(Ja, n_elem * D * D * S::NN, err), SFH_BP(lam, nu, err), SFH_BP(g, nu, err),
+                                  e0, ne, tab, err, smem_raw, &bt);
 }
 
 template <int D, int N, int FLUX>
@@ -342,7 +345,9 @@ vjp_kernel(const double *__restrict__ u, const double *__restrict__ Ja, const do
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    vjp_tile<D, N, FLUX, S>(u, Ja, lam, g, e0, ne, tab, err, smem_raw);
+    const int64_t nu = n_elem * S::NVAR * S::NN;
+    vjp_tile<D, N, FLUX, S>(SFH_BP(u, nu, err), SFH_BP(Ja, n_elem * D * D * S::NN, err), SFH_BP(lam, nu, err), SFH_BP(g, nu, err), e0,
+                            ne, tab, err, smem_raw);
 }
 
 template <int D, int N, int FLUX, class S>

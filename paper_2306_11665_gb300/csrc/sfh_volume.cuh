@@ -185,8 +185,8 @@ __device__ __forceinline__ void euler_diag_flux(const EulerNode<typename M::T, t
 // nodal values V u_hat are formed in shared memory before the node pass and
 // r receives V^T r_v (the residual and primitive buffers serve as scratch).
 template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>, bool MODAL = false>
-__device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u, const double *__restrict__ Ja,
-                                            typename M::T *__restrict__ r, int64_t e0, int ne,
+__device__ __forceinline__ void volume_tile(BPtr<const typename M::T> SFH_RESTRICT u, BPtr<const double> SFH_RESTRICT Ja,
+                                            BPtr<typename M::T> SFH_RESTRICT r, int64_t e0, int ne,
                                             const OpTab<typename M::T> &tab, int *__restrict__ err,
                                             unsigned char *smem_raw,
                                             const BasisTab<typename M::T> *bt = nullptr) {
@@ -198,14 +198,17 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     // layout: [beta_d (mixed)] [J: EPB][D][NN] TJ  [P: EPB][NP][NN] T  [R: EPB][NVAR][NN] T
     //         (FP64 Euler: [rho_f: EPB][NN] [beta_f: EPB][NN] float in place of beta_d)
     constexpr bool F64E = S::F64E;
-    double *sBd = reinterpret_cast<double *>(smem_raw);
-    float *sRF = reinterpret_cast<float *>(smem_raw);
     constexpr int BD_COUNT = ((M::mixed || F64E) && is_euler(FLUX)) ? EPB * NN : 0;
-    TJ *sJ = reinterpret_cast<TJ *>(smem_raw + sizeof(double) * BD_COUNT);
-    T *sP = reinterpret_cast<T *>(reinterpret_cast<unsigned char *>(sJ) + sizeof(TJ) * EPB * D * NN);
-    T *sR = sP + EPB * NP * NN;
+    const auto sBd = SFH_BP(reinterpret_cast<double *>(smem_raw), BD_COUNT, err);
+    const auto sRF = SFH_BP(reinterpret_cast<float *>(smem_raw), 2 * BD_COUNT, err);
+    const auto sJ = SFH_BP(reinterpret_cast<TJ *>(smem_raw + sizeof(double) * BD_COUNT), EPB * D * NN, err);
+    const auto sP = SFH_BP(reinterpret_cast<T *>(smem_raw + sizeof(double) * BD_COUNT + sizeof(TJ) * EPB * D * NN),
+                       EPB * NP * NN, err);
+    const auto sR = SFH_BP(reinterpret_cast<T *>(smem_raw + sizeof(double) * BD_COUNT + sizeof(TJ) * EPB * D * NN) +
+                           EPB * NP * NN,
+                       EPB * NVAR * NN, err);
 
-    const T *ub = u + e0 * NVAR * NN;
+    BPtr<const T> ub = u + e0 * NVAR * NN;
     if constexpr (MODAL) {
         // nodal values u_v = V u_hat, ending in sR ([el][var][i])
         if constexpr (D == 3) {
@@ -228,8 +231,8 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     bool bad = false;
     for (int s = threadIdx.x; s < ne * NN; s += blockDim.x) {
         const int el = s / NN, i = s - el * NN;
-        const T *ue = ub + (int64_t)el * NVAR * NN + i;
-        T *pe = sP + el * NP * NN + i;
+        const auto ue = ub + (int64_t)el * NVAR * NN + i;
+        const auto pe = sP + el * NP * NN + i;
         if constexpr (is_euler(FLUX)) {
             // reciprocals refined by Newton steps instead of IEEE divisions
             // (FP64: rcp_nr; FP32: hardware seed + one step); beta = rho / p
@@ -286,7 +289,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
     }
     if (bad) atomicOr(err, 1);
 
-    const double *Jb = Ja + e0 * D * D * NN;
+    const auto Jb = Ja + e0 * D * D * NN;
     uint32_t hmax = 0;   // largest |Ja| high word (range check: FP32 modes 2^126, FP64 finite)
 #pragma unroll 1
     for (int m = 0; m < D; ++m) {
@@ -328,7 +331,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
                     const int i = nb + a * stride;
-                    const T *pe = sP + el * NP * NN + (base + a * stride);
+                    const auto pe = sP + el * NP * NN + (base + a * stride);
                     nd[a].rho = pe[0];
 #pragma unroll
                     for (int k = 0; k < D; ++k) nd[a].hv[k] = pe[(1 + k) * NN];
@@ -362,7 +365,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 #pragma unroll
                 for (int a = 0; a < N; ++a) {
                     const int i = nb + a * stride;
-                    const T *pe = sP + el * NP * NN + (base + a * stride);
+                    const auto pe = sP + el * NP * NN + (base + a * stride);
                     nd[a].rho = pe[0];
 #pragma unroll
                     for (int k = 0; k < D; ++k) nd[a].v[k] = pe[(1 + k) * NN];
@@ -427,7 +430,7 @@ __device__ __forceinline__ void volume_tile(const typename M::T *__restrict__ u,
 
     // ---- 3. write r (layout [el][v][i] matches the global layout); modal:
     //      r_hat = V^T r_v
-    T *rb = r + e0 * NVAR * NN;
+    const auto rb = r + e0 * NVAR * NN;
     if constexpr (MODAL) {
         if constexpr (D == 3) {
             basis_pass<T, D, N, true>(sR, sP, 0, ne * NVAR, *bt, threadIdx.x, blockDim.x);
@@ -453,7 +456,8 @@ volume_kernel(const typename M::T *__restrict__ u, const double *__restrict__ Ja
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    volume_tile<D, N, FLUX, M, S>(u, Ja, r, e0, ne, tab, err, smem_raw);
+    volume_tile<D, N, FLUX, M, S>(SFH_BP(u, n_elem * S::NVAR * S::NN, err), SFH_BP(Ja, n_elem * D * D * S::NN, err),
+                                  SFH_BP(r, n_elem * S::NVAR * S::NN, err), e0, ne, tab, err, smem_raw);
 }
 
 template <int D, int N, int FLUX, class M, class S>
@@ -465,7 +469,8 @@ volume_modal_kernel(const typename M::T *__restrict__ u, const double *__restric
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
     const int ne = (int)((n_elem - e0) < S::EPB ? (n_elem - e0) : S::EPB);
-    volume_tile<D, N, FLUX, M, S, true>(u, Ja, r, e0, ne, tab, err, smem_raw, &bt);
+    volume_tile<D, N, FLUX, M, S, true>(SFH_BP(u, n_elem * S::NVAR * S::NN, err), SFH_BP(Ja, n_elem * D * D * S::NN, err),
+                                        SFH_BP(r, n_elem * S::NVAR * S::NN, err), e0, ne, tab, err, smem_raw, &bt);
 }
 
 template <int D, int N, int FLUX, class M, class S = Shape<D, N, FLUX, M>>

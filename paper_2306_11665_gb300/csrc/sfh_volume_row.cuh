@@ -162,8 +162,8 @@ struct RowAcc {
 // A, B, Jm, base and stride address node slots; re points at the node's
 // residual (unpadded layout).
 template <int N>
-__device__ __noinline__ void row_general(const float4 *A, const float2 *B, const float4 *Jm, int base, int stride, int a,
-                                         float omega, const OpTab<float> &tab, float *re) {
+__device__ __noinline__ void row_general(BPtr<const float4> A, BPtr<const float2> B, BPtr<const float4> Jm, int base,
+                                         int stride, int a, float omega, const OpTab<float> &tab, BPtr<float> re) {
     constexpr int NN = N * N * N;
     const int ia = base + a * stride;
     const RowNode o = row_node(A[ia], B[ia], Jm[ia]);
@@ -210,12 +210,18 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
     constexpr int NN = S::NN, NLINE = S::NLINE, EPB = S::EPB, U_EL = S::U_EL, J_EL = S::J_EL, G = S::G;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-    float *rawU = reinterpret_cast<float *>(sm + S::OFF_U);
-    double *rawJ = reinterpret_cast<double *>(sm + S::OFF_J);
-    float4 *sA = reinterpret_cast<float4 *>(sm + S::OFF_A);
-    float2 *sB = reinterpret_cast<float2 *>(sm + S::OFF_B);
-    float4 *sJ = reinterpret_cast<float4 *>(sm + S::OFF_JF);
-    float *sR = reinterpret_cast<float *>(sm + S::OFF_R);
+    const auto rawU = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_U), S::RAWU_BYTES / 4, err);
+    const auto rawJ = SFH_BP(reinterpret_cast<double *>(sm + S::OFF_J), S::RAWJ_BYTES / 8, err);
+    const auto sA = SFH_BP(reinterpret_cast<float4 *>(sm + S::OFF_A), EPB * S::NNP, err);
+    const auto sB = SFH_BP(reinterpret_cast<float2 *>(sm + S::OFF_B), EPB * S::NNP, err);
+    const auto sJ = SFH_BP(reinterpret_cast<float4 *>(sm + S::OFF_JF), EPB * 3 * S::NNP, err);
+    const auto sR = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_R), 3 * EPB * U_EL, err);
+    // u, Ja and r over their whole extents (bytes of u and Ja for the bulk copies)
+    const auto gu = SFH_BP(u, n_elem * U_EL, err);
+    const auto gJ = SFH_BP(Ja, n_elem * J_EL, err);
+    const auto gr = SFH_BP(r, n_elem * U_EL, err);
+    const auto gUb = SFH_BP(reinterpret_cast<const char *>(u), n_elem * U_EL * 4, err);
+    const auto gJb = SFH_BP(reinterpret_cast<const char *>(Ja), n_elem * J_EL * 8, err);
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -254,8 +260,8 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
     BlockPlan cur = plan_block<S>(blk, n_elem, u, Ja, aligned_bases != 0);
     if (tid == 0 && cur.tma) {
         mbar_arrive_expect_tx(bar, cur.bytesU + cur.bytesJ);
-        bulk_load(rawU, cur.srcU, cur.bytesU, bar);
-        bulk_load(rawJ, cur.srcJ, cur.bytesJ, bar);
+        bulk_load_ck(rawU, bp_at(gUb, cur.srcU), cur.bytesU, bar);
+        bulk_load_ck(rawJ, bp_at(gJb, cur.srcJ), cur.bytesJ, bar);
     }
 
     for (; blk < nblk; blk += gridDim.x) {
@@ -265,10 +271,10 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
             if (!mbar_wait_bounded(bar, phase, 2000000000ull)) s_abort = 1;
             phase ^= 1u;
         } else {
-            const float *gU = u + cur.e0 * U_EL;
-            const double *gJ = Ja + cur.e0 * J_EL;
+            const auto gU = gu + cur.e0 * U_EL;
+            const auto gJe = gJ + cur.e0 * J_EL;
             for (int s = tid; s < ne * U_EL; s += blockDim.x) rawU[s] = gU[s];
-            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJ[s];
+            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJe[s];
         }
         __syncthreads();
         if (s_abort) {
@@ -281,13 +287,13 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
         }
 
         // ---- 2. primitives and FP32 metrics, node by node
-        const float *U = rawU + cur.offU;
-        const double *J = rawJ + cur.offJ;
+        const auto U = rawU + cur.offU;
+        const auto J = rawJ + cur.offJ;
         bool bad = false;
         uint32_t hmax = 0;   // largest |Ja| high word (range check)
         for (int s = tid; s < ne * NN; s += blockDim.x) {
             const int el = s / NN, i = s - el * NN;
-            const float *ue = U + el * U_EL + i;
+            const auto ue = U + el * U_EL + i;
             const float rho = ue[0], E = ue[4 * NN];
             float ir = rcp_approx(rho);
             ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
@@ -309,7 +315,7 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
             sA[sl] = make_float4(rho, bt, hv[0], hv[1]);
             sB[sl] = make_float2(hv[2], p);
             bad |= !(rho > 0.0f && p > 0.0f);
-            const double *je = J + el * J_EL + i;
+            const auto je = J + el * J_EL + i;
 #pragma unroll
             for (int m = 0; m < 3; ++m)
                 sJ[(el * 3 + m) * S::NNP + S::slot(i)] =
@@ -327,8 +333,8 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
         if (tid == 0 && nxt < nblk && nx.tma) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, nx.bytesU + nx.bytesJ);
-            bulk_load(rawU, nx.srcU, nx.bytesU, bar);
-            bulk_load(rawJ, nx.srcJ, nx.bytesJ, bar);
+            bulk_load_ck(rawU, bp_at(gUb, nx.srcU), nx.bytesU, bar);
+            bulk_load_ck(rawJ, bp_at(gJb, nx.srcJ), nx.bytesJ, bar);
         }
 
         // ---- 4. rows, a pass of SLOTS lines at a time
@@ -347,9 +353,9 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
             const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
             const int pbase = S::slot(base), pstride = S::slot_stride(m);
             const float omega = tab.w[o0] * tab.w[o1];
-            const float4 *A = sA + el * S::NNP;
-            const float2 *B = sB + el * S::NNP;
-            const float4 *Jm = sJ + (el * 3 + m) * S::NNP;
+            BPtr<const float4> A = sA + el * S::NNP;
+            BPtr<const float2> B = sB + el * S::NNP;
+            BPtr<const float4> Jm = sJ + (el * 3 + m) * S::NNP;
             const int ia = base + a * stride, pa = pbase + a * pstride;
             const RowNode o = row_node(A[pa], B[pa], Jm[pa]);
 
@@ -383,7 +389,7 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
             // a pair outside the band anywhere in the line group sends the
             // whole group to the general routine (also for a NaN maximum)
             const unsigned out = __ballot_sync(0xffffffffu, !(umax < 1e-2f));
-            float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + ia;
+            const auto re = sR + (size_t)m * EPB * U_EL + el * U_EL + ia;
             if (__builtin_expect((out & gmask) != 0u, 0)) {
                 if (ok) row_general<N>(A, B, Jm, pbase, pstride, a, omega, tab, re);
             } else if (ok) {
@@ -398,7 +404,7 @@ volume_fp32_row_kernel(const float *__restrict__ u, const double *__restrict__ J
         __syncthreads();
 
         // ---- 5. sum the directions in a fixed order and store r
-        float *gR = r + cur.e0 * U_EL;
+        const auto gR = gr + cur.e0 * U_EL;
         for (int s2 = tid; s2 < ne * U_EL; s2 += blockDim.x)
             gR[s2] = (sR[s2] + sR[EPB * U_EL + s2]) + sR[2 * EPB * U_EL + s2];
         cur = nx;

@@ -87,11 +87,17 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
     constexpr int NNP = S::NNP;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-    double *rawU = reinterpret_cast<double *>(sm + S::OFF_U);
-    double *rawJ = reinterpret_cast<double *>(sm + S::OFF_J);
-    double2 *sN = reinterpret_cast<double2 *>(sm + S::OFF_N);   // [3][EPB * NNP]
-    double2 *sM = reinterpret_cast<double2 *>(sm + S::OFF_M);   // [EPB][3 m][2][NNP]
-    double *sR = reinterpret_cast<double *>(sm + S::OFF_R);
+    const auto rawU = SFH_BP(reinterpret_cast<double *>(sm + S::OFF_U), S::RAWU_BYTES / 8, err);
+    const auto rawJ = SFH_BP(reinterpret_cast<double *>(sm + S::OFF_J), S::RAWJ_BYTES / 8, err);
+    const auto sN = SFH_BP(reinterpret_cast<double2 *>(sm + S::OFF_N), 3 * EPB * NNP, err);   // [3][EPB * NNP]
+    const auto sM = SFH_BP(reinterpret_cast<double2 *>(sm + S::OFF_M), 6 * EPB * NNP, err);   // [EPB][3 m][2][NNP]
+    const auto sR = SFH_BP(reinterpret_cast<double *>(sm + S::OFF_R), 3 * EPB * U_EL, err);
+    // u, Ja and r over their whole extents (bytes of u and Ja for the bulk copies)
+    const auto gu = SFH_BP(u, n_elem * U_EL, err);
+    const auto gJ = SFH_BP(Ja, n_elem * J_EL, err);
+    const auto gr = SFH_BP(r, n_elem * U_EL, err);
+    const auto gUb = SFH_BP(reinterpret_cast<const char *>(u), n_elem * U_EL * 8, err);
+    const auto gJb = SFH_BP(reinterpret_cast<const char *>(Ja), n_elem * J_EL * 8, err);
     __shared__ int s_abort;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -126,8 +132,8 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
     BlockPlan cur = plan_block<S>(blk, n_elem, u, Ja, aligned_bases != 0);
     if (tid == 0 && cur.tma) {
         mbar_arrive_expect_tx(bar, cur.bytesU + cur.bytesJ);
-        bulk_load(rawU, cur.srcU, cur.bytesU, bar);
-        bulk_load(rawJ, cur.srcJ, cur.bytesJ, bar);
+        bulk_load_ck(rawU, bp_at(gUb, cur.srcU), cur.bytesU, bar);
+        bulk_load_ck(rawJ, bp_at(gJb, cur.srcJ), cur.bytesJ, bar);
     }
 
     for (; blk < nblk; blk += gridDim.x) {
@@ -137,10 +143,10 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
             if (!mbar_wait_bounded(bar, phase, 2000000000ull)) s_abort = 1;
             phase ^= 1u;
         } else {
-            const double *gU = u + cur.e0 * U_EL;
-            const double *gJ = Ja + cur.e0 * J_EL;
+            const auto gU = gu + cur.e0 * U_EL;
+            const auto gJe = gJ + cur.e0 * J_EL;
             for (int s = tid; s < ne * U_EL; s += blockDim.x) rawU[s] = gU[s];
-            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJ[s];
+            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJe[s];
         }
         __syncthreads();
         if (s_abort) {
@@ -153,13 +159,13 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
         }
 
         // ---- 2. primitives (v/2, p, beta) and metric rows, node by node
-        const double *U = rawU + cur.offU;
-        const double *J = rawJ + cur.offJ;
+        BPtr<const double> U = rawU + cur.offU;
+        BPtr<const double> J = rawJ + cur.offJ;
         bool bad = false;
         uint32_t hmax = 0;   // largest |Ja| high word (range check)
         for (int s = tid; s < ne * NN; s += blockDim.x) {
             const int el = s / NN, i = s - el * NN;
-            const double *ue = U + el * U_EL + i;
+            const auto ue = U + el * U_EL + i;
             const double rho = ue[0], E = ue[4 * NN];
             const double ir = rcp_nr(rho);
             double hv[3], ke = 0.0;
@@ -185,10 +191,10 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
             // of the (J2, .) unit
             const float2 rbf = make_float2(d2f_int(rho), d2f_int(bt));
             const double rbd = __longlong_as_double(*reinterpret_cast<const long long *>(&rbf));
-            const double *je = J + el * J_EL + i;
+            const auto je = J + el * J_EL + i;
 #pragma unroll
             for (int m = 0; m < 3; ++m) {
-                double2 *mm = sM + ((el * 3 + m) * 2) * NNP + S::slot(i);
+                const auto mm = sM + ((el * 3 + m) * 2) * NNP + S::slot(i);
                 const double j0 = je[(3 * m) * NN], j1 = je[(3 * m + 1) * NN], j2 = je[(3 * m + 2) * NN];
                 hmax = max(hmax, max(abs_hi(j0), max(abs_hi(j1), abs_hi(j2))));
                 mm[0] = make_double2(j0, j1);
@@ -206,8 +212,8 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
         if (tid == 0 && nxt < nblk && nx.tma) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, nx.bytesU + nx.bytesJ);
-            bulk_load(rawU, nx.srcU, nx.bytesU, bar);
-            bulk_load(rawJ, nx.srcJ, nx.bytesJ, bar);
+            bulk_load_ck(rawU, bp_at(gUb, nx.srcU), nx.bytesU, bar);
+            bulk_load_ck(rawJ, bp_at(gJb, nx.srcJ), nx.bytesJ, bar);
         }
 
         // ---- 4. rows
@@ -226,8 +232,8 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
             const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
             const int pbase = S::slot(base), pstride = S::slot_stride(m);
             const double omega = tab.w[o0] * tab.w[o1];
-            const double2 *N0 = sN + el * NNP, *N1 = N0 + EPB * NNP, *N2 = N1 + EPB * NNP;
-            const double2 *M0 = sM + ((el * 3 + m) * 2) * NNP, *M1 = M0 + NNP;
+            BPtr<const double2> N0 = sN + el * NNP, N1 = N0 + EPB * NNP, N2 = N1 + EPB * NNP;
+            BPtr<const double2> M0 = sM + ((el * 3 + m) * 2) * NNP, M1 = M0 + NNP;
             auto node = [&](int sl) {
                 EulerNodeD<3> nd;
                 const double2 x0 = N0[sl], x1 = N1[sl], x2 = N2[sl], y0 = M0[sl], y1 = M1[sl];
@@ -269,7 +275,7 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
                 for (int v = 0; v < 5; ++v) acc[v] = fma(qd, F[v], acc[v]);
             }
             if (ok) {
-                double *re = sR + (size_t)m * EPB * U_EL + el * U_EL + ia;
+                const auto re = sR + (size_t)m * EPB * U_EL + el * U_EL + ia;
 #pragma unroll
                 for (int v = 0; v < 5; ++v) re[v * NN] = omega * acc[v];
             }
@@ -277,7 +283,7 @@ volume_fp64_row_kernel(const double *__restrict__ u, const double *__restrict__ 
         __syncthreads();
 
         // ---- 5. sum the directions in a fixed order and store r
-        double *gR = r + cur.e0 * U_EL;
+        const auto gR = gr + cur.e0 * U_EL;
         for (int s2 = tid; s2 < ne * U_EL; s2 += blockDim.x)
             gR[s2] = (sR[s2] + sR[EPB * U_EL + s2]) + sR[2 * EPB * U_EL + s2];
         cur = nx;

@@ -152,8 +152,8 @@ __device__ __forceinline__ void line_geometry(int m, int l, const OpTab<float> &
 // for states with large jumps along a line; the arithmetic is that of the
 // fast path otherwise.
 template <int D, int N, int NN, int NP, int FLUX>
-__device__ __noinline__ void euler_line_general(const float *pe, const float *jl, float *re, int stride, float omega,
-                                                const OpTab<float> &tab) {
+__device__ __noinline__ void euler_line_general(BPtr<const float> pe, BPtr<const float> jl, BPtr<float> re, int stride,
+                                                float omega, const OpTab<float> &tab) {
     constexpr int NVAR = D + 2;
 #pragma unroll 1
     for (int a = 0; a < N; ++a) {
@@ -207,15 +207,15 @@ __device__ __noinline__ void euler_line_general(const float *pe, const float *jl
 // error bits this thread found: kErrDomain (rho <= 0 or p <= 0, or NaN),
 // kErrMetric (a metric term outside the FP32 modes' range).
 template <class S, int D, int N, int FLUX>
-__device__ __forceinline__ int fp32_block_convert(const float *U, const double *J, int ne, float *sP, float *sJF,
-                                                  int tid, int nthreads) {
+__device__ __forceinline__ int fp32_block_convert(BPtr<const float> U, BPtr<const double> J, int ne, BPtr<float> sP,
+                                                  BPtr<float> sJF, int tid, int nthreads) {
     constexpr int NN = S::NN, NLINE = S::NLINE, NP = S::NP, U_EL = S::U_EL, J_EL = S::J_EL;
     bool bad = false;
     uint32_t hmax = 0;
     for (int s = tid; s < ne * NN; s += nthreads) {
         const int el = s / NN, i = s - el * NN;
-        const float *ue = U + el * U_EL + i;
-        float *pe = sP + el * NP * NN + i;
+        const auto ue = U + el * U_EL + i;
+        const auto pe = sP + el * NP * NN + i;
         if constexpr (is_euler(FLUX)) {
             // per-node divisions to within about half an ulp: with the
             // residual's cancellation, per-node errors act like
@@ -246,8 +246,8 @@ __device__ __forceinline__ int fp32_block_convert(const float *U, const double *
             // the node's d*d metric values, FP64 -> FP32, into the line of
             // each direction through it: (line, position) = (i / N, i0),
             // (i0 + N i2, i1), (i0 + N i1, i2) in 3D; (i1, i0), (i0, i1) in 2D
-            const double *je = J + el * J_EL + i;
-            float *jl = sJF + el * S::JF_EL;
+            const auto je = J + el * J_EL + i;
+            const auto jl = sJF + el * S::JF_EL;
             const int i0 = i % N;
 #pragma unroll
             for (int m = 0; m < D; ++m) {
@@ -260,7 +260,7 @@ __device__ __forceinline__ int fp32_block_convert(const float *U, const double *
                     line = m == 0 ? i / N : i0;
                     pos = m == 0 ? i0 : i / N;
                 }
-                float *dst = jl + (m * NLINE + line) * S::LJ + pos * D;
+                const auto dst = jl + (m * NLINE + line) * S::LJ + pos * D;
 #pragma unroll
                 for (int k = 0; k < D; ++k) dst[k] = d2f_int_track(je[(m * D + k) * NN], hmax);
             }
@@ -271,7 +271,7 @@ __device__ __forceinline__ int fp32_block_convert(const float *U, const double *
     if constexpr (!is_euler(FLUX)) {
         for (int s = tid; s < ne * D * NN; s += nthreads) {
             const int el = s / (D * NN), rem = s - el * D * NN, m = rem / NN, i = rem - m * NN;
-            const double *jm = J + ((el * D + m) * D) * NN + i;
+            const auto jm = J + ((el * D + m) * D) * NN + i;
             static_assert(is_euler(FLUX) || S::JF_EL == D * NN, "Burgers metric sums are node-major");
             float acc = d2f_int_track(jm[0], hmax);
 #pragma unroll
@@ -286,8 +286,8 @@ __device__ __forceinline__ int fp32_block_convert(const float *U, const double *
 // (direction, element, line) and writes its direction's residual slice of sR
 // ([m][el][var][i]).
 template <class S, int D, int N, int FLUX>
-__device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *sP, const float *sJF, float *sR,
-                                                 const OpTab<float> &tab) {
+__device__ __forceinline__ void fp32_block_sweep(int tid, int ne, BPtr<const float> sP, BPtr<const float> sJF,
+                                                 BPtr<float> sR, const OpTab<float> &tab) {
     constexpr int NN = S::NN, NLINE = S::NLINE, NVAR = S::NVAR, NP = S::NP, EPB = S::EPB, U_EL = S::U_EL;
     if (tid < D * EPB * NLINE) {
         const int m = tid / (EPB * NLINE);
@@ -305,7 +305,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                 base = m == 0 ? N * l : l;
                 omega = tab.w[l];
             }
-            const float *pe = sP + el * NP * NN + base;
+            const auto pe = sP + el * NP * NN + base;
             float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
             if constexpr (is_euler(FLUX)) {
                 // Euler: variables accumulate in packed pairs (0,1), (2,3) [, 4]
@@ -318,7 +318,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                     for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
                     acc4[a].zero();
                 }
-                const float *jl = sJF + el * S::JF_EL + (m * NLINE + l) * S::LJ;   // this line's metric rows
+                const auto jl = sJF + el * S::JF_EL + (m * NLINE + l) * S::LJ;   // this line's metric rows
                 float2 rb[N];          // (rho, beta)
                 float hv[N][D], p[N];
 #pragma unroll
@@ -414,7 +414,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                         if constexpr (D == 3) acc4[a].add_prod(qaa, F[4]);
                     }
                 }
-                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+                const auto re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
                 // also false for a NaN maximum (fmaxf drops NaN operands; the
                 // domain flag of the node pass reports the state)
                 if (__builtin_expect(!(umax < 1e-2f), 0)) {
@@ -435,7 +435,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                 KahanF acc[N][NVAR];
 #pragma unroll
                 for (int a = 0; a < N; ++a) acc[a][0].zero();
-                const float *je = sJF + (el * D + m) * NN + base;
+                const auto je = sJF + (el * D + m) * NN + base;
                 float uu[N], Sm[N];
 #pragma unroll
                 for (int a = 0; a < N; ++a) { uu[a] = pe[a * stride]; Sm[a] = je[a * stride]; }
@@ -450,7 +450,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
                     const float qaa = tab.Q1[a * N + a];
                     if (qaa != 0.0f) acc[a][0].add_prod(qaa, uu[a] * uu[a] * Sm[a]);
                 }
-                float *re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
+                const auto re = sR + (size_t)m * EPB * U_EL + el * U_EL + base;
 #pragma unroll
                 for (int a = 0; a < N; ++a) re[a * stride] = omega * acc[a][0].value();
             }
@@ -460,7 +460,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, const float *s
 
 // The directions' slices summed in a fixed order into r (coalesced).
 template <class S, int D>
-__device__ __forceinline__ void fp32_block_store(const float *sR, float *gR, int ne, int tid, int nthreads) {
+__device__ __forceinline__ void fp32_block_store(BPtr<const float> sR, BPtr<float> gR, int ne, int tid, int nthreads) {
     constexpr int EPB = S::EPB, U_EL = S::U_EL;
     for (int s2 = tid; s2 < ne * U_EL; s2 += nthreads) {
         float t = sR[s2] + sR[EPB * U_EL + s2];
@@ -475,8 +475,9 @@ __device__ __forceinline__ void fp32_block_store(const float *sR, float *gR, int
 // nodal store).  (Packing two element-variables into FP32x2 lanes measured
 // 6 % slower at p = 4.)
 template <int D, int N, bool TRANSPOSE, int ROLE = kPassPlain, int NSUM = 1>
-__device__ __forceinline__ void basis_pass_f(const float *in, float *out, int m, int nq, const BasisTab<float> &bt,
-                                             int tid, int nthreads, const float *coef = nullptr, int slice = 0) {
+__device__ __forceinline__ void basis_pass_f(BPtr<const float> in, BPtr<float> out, int m, int nq,
+                                             const BasisTab<float> &bt, int tid, int nthreads,
+                                             BPtr<const float> coef = nullptr, int slice = 0) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1);
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
     for (int t = tid; t < nq * NLINE; t += nthreads) {
@@ -484,7 +485,7 @@ __device__ __forceinline__ void basis_pass_f(const float *in, float *out, int m,
         int base;
         if constexpr (D == 3) base = m == 0 ? N * l : (m == 1 ? l % N + N * N * (l / N) : l);
         else base = m == 0 ? N * l : l;
-        const float *src = in + q * NN + base;
+        const auto src = in + q * NN + base;
         float x[N];
 #pragma unroll
         for (int b = 0; b < N; ++b) {
@@ -500,7 +501,7 @@ __device__ __forceinline__ void basis_pass_f(const float *in, float *out, int m,
         if constexpr (ROLE == kPassLast) {
             if (bt.const_mode) c = coef[q * NN] * bt.c0;
         }
-        float *dst = out + q * NN + base;
+        const auto dst = out + q * NN + base;
 #pragma unroll
         for (int a = 0; a < N; ++a) {
             float acc = 0.0f;
@@ -525,11 +526,17 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
     constexpr int U_EL = S::U_EL, J_EL = S::J_EL;
     extern __shared__ __align__(128) unsigned char sm[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(sm);
-    float *rawU = reinterpret_cast<float *>(sm + S::OFF_U);
-    double *rawJ = reinterpret_cast<double *>(sm + S::OFF_J);
-    float *sP = reinterpret_cast<float *>(sm + S::OFF_P);
-    float *sJF = reinterpret_cast<float *>(sm + S::OFF_JF);
-    float *sR = reinterpret_cast<float *>(sm + S::OFF_R);
+    const auto rawU = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_U), S::RAWU_BYTES / 4, err);
+    const auto rawJ = SFH_BP(reinterpret_cast<double *>(sm + S::OFF_J), S::RAWJ_BYTES / 8, err);
+    const auto sP = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_P), EPB * NP * NN, err);
+    const auto sJF = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_JF), EPB * S::JF_EL, err);
+    const auto sR = SFH_BP(reinterpret_cast<float *>(sm + S::OFF_R), D * EPB * U_EL, err);
+    // u, Ja and r over their whole extents (bytes of u and Ja for the bulk copies)
+    const auto gu = SFH_BP(u, n_elem * U_EL, err);
+    const auto gJ = SFH_BP(Ja, n_elem * J_EL, err);
+    const auto gr = SFH_BP(r, n_elem * U_EL, err);
+    const auto gUb = SFH_BP(reinterpret_cast<const char *>(u), n_elem * U_EL * 4, err);
+    const auto gJb = SFH_BP(reinterpret_cast<const char *>(Ja), n_elem * J_EL * 8, err);
     __shared__ int s_abort;
 
     const int tid = threadIdx.x;
@@ -547,8 +554,8 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
     BlockPlan cur = plan_block<S>(blk, n_elem, u, Ja, aligned_bases != 0);
     if (tid == 0 && cur.tma) {
         mbar_arrive_expect_tx(bar, cur.bytesU + cur.bytesJ);
-        bulk_load(rawU, cur.srcU, cur.bytesU, bar);
-        bulk_load(rawJ, cur.srcJ, cur.bytesJ, bar);
+        bulk_load_ck(rawU, bp_at(gUb, cur.srcU), cur.bytesU, bar);
+        bulk_load_ck(rawJ, bp_at(gJb, cur.srcJ), cur.bytesJ, bar);
     }
 
     for (; blk < nblk; blk += gridDim.x) {
@@ -558,10 +565,10 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
             if (!mbar_wait_bounded(bar, phase, 2000000000ull)) s_abort = 1;
             phase ^= 1u;
         } else {
-            const float *gU = u + cur.e0 * U_EL;
-            const double *gJ = Ja + cur.e0 * J_EL;
+            const auto gU = gu + cur.e0 * U_EL;
+            const auto gJe = gJ + cur.e0 * J_EL;
             for (int s = tid; s < ne * U_EL; s += blockDim.x) rawU[s] = gU[s];
-            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJ[s];
+            for (int s = tid; s < ne * J_EL; s += blockDim.x) rawJ[s] = gJe[s];
         }
         __syncthreads();
         if (s_abort) {
@@ -575,9 +582,9 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
 
         // ---- 2. (modal: nodal values u_v = V u_hat into the last residual
         //      slice) primitives and FP32 metrics
-        const float *uin = rawU + cur.offU;
+        BPtr<const float> uin = rawU + cur.offU;
         if constexpr (MODAL) {
-            float *s0 = sR, *s1 = sR + EPB * U_EL, *s2 = sR + 2 * EPB * U_EL;
+            const auto s0 = sR, s1 = sR + EPB * U_EL, s2 = sR + 2 * EPB * U_EL;
             basis_pass_f<D, N, false, kPassFirst>(uin, s0, 0, ne * NVAR, *bt, tid, S::THREADS);
             __syncthreads();
             if constexpr (D == 3) {
@@ -601,8 +608,8 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
         if (tid == 0 && nxt < nblk && nx.tma) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, nx.bytesU + nx.bytesJ);
-            bulk_load(rawU, nx.srcU, nx.bytesU, bar);
-            bulk_load(rawJ, nx.srcJ, nx.bytesJ, bar);
+            bulk_load_ck(rawU, bp_at(gUb, nx.srcU), nx.bytesU, bar);
+            bulk_load_ck(rawJ, bp_at(gJb, nx.srcJ), nx.bytesJ, bar);
         }
 
         // ---- 4. line sweeps, all directions at once
@@ -614,8 +621,8 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
         if constexpr (MODAL) {
             // pass 0 sums the directions' slices (same order as the nodal
             // store) into the free primitive buffer
-            float *s0 = sR;
-            float *gR = r + cur.e0 * U_EL;
+            const auto s0 = sR;
+            const auto gR = gr + cur.e0 * U_EL;
             basis_pass_f<D, N, true, kPassPlain, D>(sR, sP, 0, ne * NVAR, *bt, tid, S::THREADS, nullptr,
                                                      EPB * U_EL);
             __syncthreads();
@@ -627,7 +634,7 @@ __device__ __forceinline__ void fp32_tma_body(const float *__restrict__ u, const
                 basis_pass_f<D, N, true>(sP, gR, 1, ne * NVAR, *bt, tid, S::THREADS);
             }
         } else {
-            fp32_block_store<S, D>(sR, r + cur.e0 * U_EL, ne, tid, S::THREADS);
+            fp32_block_store<S, D>(sR, gr + cur.e0 * U_EL, ne, tid, S::THREADS);
         }
         cur = nx;
     }

@@ -31,12 +31,12 @@
 
 namespace sfh {
 
-// FP32-Kahan: n = 3..5 (at n = 6 the line body spills under the 128
-// registers of twelve sweep warps and the thread-per-line kernel is faster);
-// mixed mode: n = 3..6
+// FP32-Kahan and mixed mode: n = 3..6 (at n = 6 the FP32 line body spills a
+// few registers under the 128 of sixteen warps and is still faster than the
+// thread-per-line kernel: 311 against 330 us on 32^3 elements)
 template <int D, int N, int FLUX>
 constexpr bool use_ws_kernel() {
-    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 5;
+    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 6;
 }
 template <int D, int N, int FLUX>
 constexpr bool use_ws_mixed() {
@@ -134,8 +134,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 // staged FP64 values).  Out of line: it runs only for states with large
 // jumps along a line.
 template <int D, int N, int NN, int FLUX>
-__device__ __noinline__ void ws_euler_line_general(const float2 *pe, const double *je, float *re, int stride,
-                                                   float omega, const OpTab<float> &tab) {
+__device__ __noinline__ void ws_euler_line_general(BPtr<const float2> pe, BPtr<const double> je, BPtr<float> re,
+                                                   int stride, float omega, const OpTab<float> &tab) {
     constexpr int NVAR = D + 2;
     static_assert(D == 3, "3D only");
     uint32_t hmax = 0;
@@ -185,17 +185,17 @@ __device__ __noinline__ void ws_euler_line_general(const float2 *pe, const doubl
 // [3][NN]); je: the element's staged FP64 metric, [m][k][NN].  Returns the
 // largest high word of the metric magnitudes met (range check).
 template <int D, int N, int FLUX>
-__device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, const float2 *pe0, const double *je0, float *re0,
-                                                  const OpTab<float> &tab) {
+__device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float2> pe0, BPtr<const double> je0,
+                                                  BPtr<float> re0, const OpTab<float> &tab) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1), NVAR = D + 2;
     static_assert(D == 3 && NLINE == N * N, "3D only");
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
     const int o0 = l % N, o1 = l / N;
     const int base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
     const float omega = tab.w[o0] * tab.w[o1];
-    const float2 *pe = pe0 + base;
-    const double *je = je0 + m * D * NN + base;
-    float *re = re0 + base;
+    const auto pe = pe0 + base;
+    const auto je = je0 + m * D * NN + base;
+    const auto re = re0 + base;
 
     uint32_t hmax = 0;
     // node data in FP32x2 lanes where the pair arithmetic pairs them:
@@ -315,8 +315,8 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, const float2 *pe
 // for pairs outside the series band: metric pair sums in FP64 as in the fast
 // path; inside the band the means of ws_mix_means.  Out of line (rare).
 template <int D, int N, int NN, int FLUX>
-__device__ __noinline__ void ws_mix_line_general(const float2 *pe, const double *je, const double *be, float *re,
-                                                 int stride, float omega, const OpTab<float> &tab);
+__device__ __noinline__ void ws_mix_line_general(BPtr<const float2> pe, BPtr<const double> je, BPtr<const double> be,
+                                                 BPtr<float> re, int stride, float omega, const OpTab<float> &tab);
 
 // The two logarithmic means of a pair in the mixed mode (inside the series
 // band): FP64 where FP32 would lose accuracy, FP32 where it cannot.
@@ -345,18 +345,19 @@ __device__ __forceinline__ float2 ws_mix_means(float rho_a, float rho_b, double 
 // formed in FP64 (then rounded to FP32) and the logarithmic means of
 // ws_mix_means.  be0: the element's FP64 betas [NN].
 template <int D, int N, int FLUX>
-__device__ __forceinline__ uint32_t ws_line_sweep_mix(int m, int l, const float2 *pe0, const double *je0,
-                                                      const double *be0, float *re0, const OpTab<float> &tab) {
+__device__ __forceinline__ uint32_t ws_line_sweep_mix(int m, int l, BPtr<const float2> pe0, BPtr<const double> je0,
+                                                      BPtr<const double> be0, BPtr<float> re0,
+                                                      const OpTab<float> &tab) {
     constexpr int NN = ipow(N, D), NLINE = ipow(N, D - 1), NVAR = D + 2;
     static_assert(D == 3 && NLINE == N * N, "3D only");
     const int stride = m == 0 ? 1 : (m == 1 ? N : N * N);
     const int o0 = l % N, o1 = l / N;
     const int base = m == 0 ? N * l : (m == 1 ? o0 + N * N * o1 : l);
     const float omega = tab.w[o0] * tab.w[o1];
-    const float2 *pe = pe0 + base;
-    const double *je = je0 + m * D * NN + base;
-    const double *be = be0 + base;
-    float *re = re0 + base;
+    const auto pe = pe0 + base;
+    const auto je = je0 + m * D * NN + base;
+    const auto be = be0 + base;
+    const auto re = re0 + base;
 
     uint32_t hmax = 0;
     float2 rb[N], h01[N];
@@ -478,8 +479,8 @@ __device__ __forceinline__ uint32_t ws_line_sweep_mix(int m, int l, const float2
 }
 
 template <int D, int N, int NN, int FLUX>
-__device__ __noinline__ void ws_mix_line_general(const float2 *pe, const double *je, const double *be, float *re,
-                                                 int stride, float omega, const OpTab<float> &tab) {
+__device__ __noinline__ void ws_mix_line_general(BPtr<const float2> pe, BPtr<const double> je, BPtr<const double> be,
+                                                 BPtr<float> re, int stride, float omega, const OpTab<float> &tab) {
     constexpr int NVAR = D + 2;
     static_assert(D == 3, "3D only");
     const float cg = (float)(2.0 / (kGamma - 1.0));
@@ -540,13 +541,13 @@ __device__ __noinline__ void ws_mix_line_general(const float2 *pe, const double 
 // [el][var][i]) into float2 triples [el][3][i]; returns whether any node had
 // rho <= 0 or p <= 0 (or NaN).  Same arithmetic as fp32_block_convert.
 template <class S, int D>
-__device__ __forceinline__ bool ws_primitives(const float *U, float2 *P2, int ne, int s0, int step,
-                                              double *B64 = nullptr) {
+__device__ __forceinline__ bool ws_primitives(BPtr<const float> U, BPtr<float2> P2, int ne, int s0, int step,
+                                              BPtr<double> B64 = nullptr) {
     constexpr int NN = S::NN, U_EL = S::U_EL;
     bool bad = false;
     for (int s = s0; s < ne * NN; s += step) {
         const int el = s / NN, i = s - el * NN;
-        const float *ue = U + el * U_EL + i;
+        const auto ue = U + el * U_EL + i;
         const float rho = ue[0], E = ue[(D + 1) * NN];
         float ir = rcp_approx(rho);
         ir = fmaf(ir, fmaf(-rho, ir, 1.0f), ir);
@@ -564,11 +565,11 @@ __device__ __forceinline__ bool ws_primitives(const float *U, float2 *P2, int ne
         ip = fmaf(ip, fmaf(-p, ip, 1.0f), ip);
         float bt = rho * ip;
         bt = fmaf(ip, fmaf(-p, bt, rho), bt);
-        float2 *pe = P2 + el * 3 * NN + i;
+        const auto pe = P2 + el * 3 * NN + i;
         pe[0] = f2(rho, bt);
         pe[NN] = f2(hv[0], hv[1]);
         pe[2 * NN] = f2(hv[2], p);
-        if (B64) {
+        if (raw(B64)) {
             // mixed mode: beta = rho / p in FP64 (exact FP32 rho and p, the
             // FP32 reciprocal seed refined by one FP64 Newton step: ~2^-46)
             const double pd = f2d_pos(p), r0 = f2d_pos(ip);
@@ -612,11 +613,29 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
     }
     __syncthreads();
     const bool al = aligned_bases != 0;
-    auto rawU = [&](int b) { return reinterpret_cast<float *>(sm + S::OFF_RAW + b * S::RAW_BYTES); };
-    auto rawJ = [&](int b) { return reinterpret_cast<double *>(sm + S::OFF_RAW + b * S::RAW_BYTES + S::RAWU_BYTES); };
-    auto P2 = [&](int b) { return reinterpret_cast<float2 *>(sm + S::OFF_P2 + b * S::P2_BYTES); };
-    auto R = [&](int b) { return reinterpret_cast<float *>(sm + S::OFF_R + b * S::R_BYTES); };
-    auto B64 = [&](int b) { return reinterpret_cast<double *>(sm + S::OFF_B64 + b * S::B64_BYTES); };
+    // the carve-outs of buffer b, each checked against its own extent
+    auto rawU = [&](int b) {
+        return SFH_BP(reinterpret_cast<float *>(sm + S::OFF_RAW + b * S::RAW_BYTES), S::RAWU_BYTES / 4, err);
+    };
+    auto rawJ = [&](int b) {
+        return SFH_BP(reinterpret_cast<double *>(sm + S::OFF_RAW + b * S::RAW_BYTES + S::RAWU_BYTES),
+                      (S::RAW_BYTES - S::RAWU_BYTES) / 8, err);
+    };
+    auto P2 = [&](int b) {
+        return SFH_BP(reinterpret_cast<float2 *>(sm + S::OFF_P2 + b * S::P2_BYTES), S::P2_BYTES / 8, err);
+    };
+    auto R = [&](int b) {
+        return SFH_BP(reinterpret_cast<float *>(sm + S::OFF_R + b * S::R_BYTES), S::R_BYTES / 4, err);
+    };
+    auto B64 = [&](int b) {
+        return SFH_BP(reinterpret_cast<double *>(sm + S::OFF_B64 + b * S::B64_BYTES), S::B64_BYTES / 8, err);
+    };
+    // u, Ja and r over their whole extents (bytes of u and Ja for the bulk copies)
+    const auto gu = SFH_BP(u, n_elem * U_EL, err);
+    const auto gJ = SFH_BP(Ja, n_elem * J_EL, err);
+    const auto gr = SFH_BP(r, n_elem * U_EL, err);
+    const auto gUb = SFH_BP(reinterpret_cast<const char *>(u), n_elem * U_EL * 4, err);
+    const auto gJb = SFH_BP(reinterpret_cast<const char *>(Ja), n_elem * J_EL * 8, err);
     auto plan = [&](int k) {
         return plan_block<S>((int64_t)blockIdx.x + (int64_t)k * gridDim.x, n_elem, u, Ja, al);
     };
@@ -634,15 +653,15 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
             const int b = k & 1;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(full + b, pl.bytesU + pl.bytesJ);
-            bulk_load(rawU(b), pl.srcU, pl.bytesU, full + b);
-            bulk_load(rawJ(b), pl.srcJ, pl.bytesJ, full + b);
+            bulk_load_ck(rawU(b), bp_at(gUb, pl.srcU), pl.bytesU, full + b);
+            bulk_load_ck(rawJ(b), bp_at(gJb, pl.srcJ), pl.bytesJ, full + b);
             issued = k + 1;
         };
         auto store = [&](int k) {
             // the directions' slices summed in a fixed order, (m0 + m1) + m2
             const BlockPlan pl = plan(k);
-            const float *R0 = R(k & 1);
-            float *gR = r + pl.e0 * U_EL;
+            const auto R0 = R(k & 1);
+            const auto gR = gr + pl.e0 * U_EL;
             // unrolled: independent loads of several outputs in flight per thread
 #pragma unroll 8
             for (int s = st; s < pl.ne * U_EL; s += S::SVC_THREADS) {
@@ -668,18 +687,18 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
             } else {
                 // a block whose aligned window would leave the arrays (or
                 // unaligned bases): plain loads, published on copied[b]
-                const float *gU = u + cur.e0 * U_EL;
-                const double *gJ = Ja + cur.e0 * J_EL;
-                float *dU = rawU(b);
-                double *dJ = rawJ(b);
+                const auto gU = gu + cur.e0 * U_EL;
+                const auto gJe = gJ + cur.e0 * J_EL;
+                const auto dU = rawU(b);
+                const auto dJ = rawJ(b);
                 for (int s = st; s < cur.ne * U_EL; s += S::SVC_THREADS) dU[s] = gU[s];
-                for (int s = st; s < cur.ne * J_EL; s += S::SVC_THREADS) dJ[s] = gJ[s];
+                for (int s = st; s < cur.ne * J_EL; s += S::SVC_THREADS) dJ[s] = gJe[s];
                 mbar_arrive(copied + b);
                 if (!ws_wait(copied + b, ph.next(b, true), abort)) { give_up(); ok = false; break; }
             }
             // 2. primitives of block k, handed to the sweep warps
             bad |= ws_primitives<S, D>(rawU(b) + cur.offU, P2(b), cur.ne, st, S::SVC_THREADS,
-                                       MIX ? B64(b) : nullptr);
+                                       MIX ? B64(b) : BPtr<double>(nullptr));
             mbar_arrive(ready + b);
             // 3. block k - 1: once swept, its raw buffer takes block k + 1 and
             //    its residual is stored
@@ -723,8 +742,8 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
                 const int L = tid - m * (EPB * NLINE);
                 const int el = L / NLINE, l = L - el * NLINE;
                 if (el < cur.ne) {
-                    float *re0 = R(b) + m * S::R_SLICE + el * U_EL;
-                    const double *je0 = rawJ(b) + cur.offJ + el * J_EL;
+                    const auto re0 = R(b) + m * S::R_SLICE + el * U_EL;
+                    const auto je0 = rawJ(b) + cur.offJ + el * J_EL;
                     if constexpr (MIX)
                         hmax = max(hmax, ws_line_sweep_mix<D, N, FLUX>(m, l, P2(b) + el * S::P2_EL, je0,
                                                                         B64(b) + el * S::NN, re0, tab));
