@@ -125,13 +125,12 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
 # the figure).
 TRAFFIC = {
     # (prec, p, nodes, N): ncu capture of the timed kernel, launch 2 of
-    # `bench.py --steps 3 --warmup 1 --no-variants --no-cpu --no-e2e --no-serve`
-    ("fp32k", 4, 0, 32): {"bytes": 377_451_520 + 67_561_984, "sha1": "419dd4f048fa8ff245d1531a58cc8db94222cf41",
-                          "counters": {"issue_active_pct": 63.1, "dram_throughput_pct": 33.6, "fma_pipe_pct": 48.6,
-                                       "alu_pipe_pct": 25.2, "warps_active_pct": 23.4,
+    # `bench.py --steps 3 --warmup 3 --no-serve --no-variants --no-cpu --no-e2e`
+    ("fp32k", 4, 0, 32): {"bytes": 376_972_288 + 65_356_288, "sha1": "eaf542a1ba6c9298d0fcc839fd7c5bf7fcd5c05f",
+                          "counters": {"issue_active_pct": 66.8, "dram_throughput_pct": 39.9, "fma_pipe_pct": 53.4,
+                                       "alu_pipe_pct": 34.2, "warps_active_pct": 24.9,
                                        "binding": "instruction issue (FP32 pair arithmetic), not DRAM"}},
 }
-
 
 # The sources that define the timed kernels' code: the persistent FP32 kernel
 # and its building blocks, and the instantiation unit; with the compiler flags.
