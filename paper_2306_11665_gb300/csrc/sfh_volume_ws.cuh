@@ -51,6 +51,7 @@ struct WsShape {
     static constexpr int U_EL = NVAR * NN;   // floats of u (and r) per element
     static constexpr int J_EL = D * D * NN;  // doubles of Ja per element
     // primitives as three float2 per node: (rho, beta), (v0/2, v1/2), (v2/2, p)
+    // (FP32-Kahan with Ranocha's flux: (v2/2, p/2), see ws_line_sweep)
     static constexpr int P2_EL = 3 * NN;
     static constexpr int TASKS_EL = D * NLINE;
     // twelve sweep warps (three per sub-partition) also in the mixed mode:
@@ -130,7 +131,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // One Euler line from scratch, with the logarithm for pairs outside the
-// series band (primitives as float2 triples, metric rows re-read from the
+// series band (primitives as float2 triples, p halved as in ws_line_sweep for
+// Ranocha's flux; metric rows re-read from the
 // staged FP64 values).  Out of line: it runs only for states with large
 // jumps along a line.
 template <int D, int N, int NN, int FLUX>
@@ -161,7 +163,8 @@ __device__ __noinline__ void ws_euler_line_general(BPtr<const float2> pe, BPtr<c
             float hna = 0.0f, hnb = 0.0f, hvv = 0.0f;
 #pragma unroll
             for (int k = 0; k < 3; ++k) { hna = fmaf(hva[k], n[k], hna); hnb = fmaf(hvb[k], n[k], hnb); hvv = fmaf(hva[k], hvb[k], hvv); }
-            const float ra = rba.x, rb = rbb.x, pa = h2pa.y, pb = h2pb.y;
+            const float ra = rba.x, rb = rbb.x;
+            const float pa = FLUX == kFluxEuler ? 2.0f * h2pa.y : h2pa.y, pb = FLUX == kFluxEuler ? 2.0f * h2pb.y : h2pb.y;
             const float Lr = ln_mean(ra, rb), iLb = inv_ln_mean(rba.y, rbb.y);
             float F[NVAR];
             const float frho = Lr * (hna + hnb);
@@ -213,6 +216,8 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float
         j01[a].y = d2f_int_track(je[1 * NN + a * stride], hmax);
         j2[a] = d2f_int_track(je[2 * NN + a * stride], hmax);
     }
+    // compensated sums per node: (m0, m1) and (m2, E) flux pairs packed,
+    // the density flux alone
     constexpr int NPAIR = NVAR / 2;
     KahanF2 accp[N][NPAIR];
     KahanF acc4[N];
@@ -222,9 +227,18 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float
         for (int v = 0; v < NPAIR; ++v) accp[a][v].zero();
         acc4[a].zero();
     }
+    // Ranocha's flux: the node pass stores p/2, so that the mean {p} is one
+    // addition.  The energy flux is then formed at half scale: the pressure
+    // work with p/2 in place of p, the inverse beta mean from the series
+    // with halved coefficients, and v_a.v_b / 2 in place of 2 (v_a/2).(v_b/2).
+    // Each step is an exact power-of-two scaling of the full-scale
+    // arithmetic, so the energy sum is exactly half of the full-scale one;
+    // the store scales it by 2 omega.
+    constexpr bool PH = FLUX == kFluxEuler;
     float umax = 0.0f;   // largest u_rho + u_beta of the line's pairs
-    // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean) as one packed Horner chain
-    const float cg = (float)(2.0 / (kGamma - 1.0));
+    // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean; PH: half of
+    // it) as one packed Horner chain
+    const float cg = (float)((PH ? 1.0 : 2.0) / (kGamma - 1.0));
     const float2 c0 = f2(0.5f, cg), c1 = f2(0.5f * (-1.0f / 3.0f), cg * (1.0f / 3.0f));
     const float2 c2 = f2(0.5f * (-4.0f / 45.0f), cg * (1.0f / 5.0f));
     const float2 c3 = f2(0.5f * (-44.0f / 945.0f), cg * (1.0f / 7.0f));
@@ -255,23 +269,21 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float
             umax = fmaxf(umax, u2.x + u2.y);
             const float2 m2 = mul2(f2(s2.x, r2.y), h);   // ({rho}_ln, 1/((g-1){beta}_ln))
             const float frho = m2.x * (hna + hnb);
-            const float pavg = FLUX == kFluxEulerCh ? s2.x * r2.y : 0.5f * (p[a] + p[b]);
+            const float pavg = FLUX == kFluxEulerCh ? s2.x * r2.y : (PH ? p[a] + p[b] : 0.5f * (p[a] + p[b]));
             const float work = FLUX == kFluxEulerCh ? pavg * (hna + hnb) : fmaf(p[a], hnb, p[b] * hna);
-            float2 F01, F23;
-            F01.x = frho;
-            F01.y = fmaf(frho, hs01.x, pavg * n01.x);
-            F23.x = fmaf(frho, hs01.y, pavg * n01.y);
-            F23.y = fmaf(frho, h2[a] + h2[b], pavg * n2);
-            const float K = fmaf(2.0f, hvv, m2.y);
+            const float2 F12 = fma2(f2s(frho), hs01, mul2(f2s(pavg), n01));
+            const float F3 = fmaf(frho, h2[a] + h2[b], pavg * n2);
+            const float K = PH ? hvv + m2.y : fmaf(2.0f, hvv, m2.y);
             const float FE = fmaf(frho, K, work);
+            const float2 F34 = f2(F3, FE);
             const float qab = tab.Q1[a * N + b], qba = tab.Q1[b * N + a];
             const float2 qa2 = f2s(qab), qb2 = f2s(qba);
-            accp[a][0].add_prod(qa2, F01);
-            accp[b][0].add_prod(qb2, F01);
-            accp[a][1].add_prod(qa2, F23);
-            accp[b][1].add_prod(qb2, F23);
-            acc4[a].add_prod(qab, FE);
-            acc4[b].add_prod(qba, FE);
+            accp[a][0].add_prod(qa2, F12);
+            accp[b][0].add_prod(qb2, F12);
+            accp[a][1].add_prod(qa2, F34);
+            accp[b][1].add_prod(qb2, F34);
+            acc4[a].add_prod(qab, frho);
+            acc4[b].add_prod(qba, frho);
         }
         const float qaa = tab.Q1[a * N + a];
         if (qaa != 0.0f) {
@@ -283,14 +295,16 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float
             for (int k = 1; k < D; ++k) { hn = fmaf(hva[k], n[k], hn); hv2 = fmaf(hva[k], hva[k], hv2); }
             float F[D + 2];
             const float frho = 2.0f * rb[a].x * hn;
+            const float pf = PH ? p[a] + p[a] : p[a];
             F[0] = frho;
 #pragma unroll
-            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hva[k], p[a] * n[k]);
-            F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
+            for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hva[k], pf * n[k]);
+            if constexpr (PH) F[D + 1] = fmaf(frho, hv2, pf * hn * (float)(kGamma / (kGamma - 1.0)));
+            else F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * pf * hn * (float)(kGamma / (kGamma - 1.0)));
             const float2 qq = f2s(qaa);
-            accp[a][0].add_prod(qq, f2(F[0], F[1]));
-            accp[a][1].add_prod(qq, f2(F[2], F[3]));
-            acc4[a].add_prod(qaa, F[4]);
+            accp[a][0].add_prod(qq, f2(F[1], F[2]));
+            accp[a][1].add_prod(qq, f2(F[3], F[4]));
+            acc4[a].add_prod(qaa, F[0]);
         }
     }
     // also false for a NaN maximum (fmaxf drops NaN operands; the domain
@@ -300,12 +314,12 @@ __device__ __forceinline__ uint32_t ws_line_sweep(int m, int l, BPtr<const float
     } else {
 #pragma unroll
         for (int a = 0; a < N; ++a) {
-            const float2 v01 = accp[a][0].value(), v23 = accp[a][1].value();
-            re[0 * NN + a * stride] = omega * v01.x;
-            re[1 * NN + a * stride] = omega * v01.y;
-            re[2 * NN + a * stride] = omega * v23.x;
-            re[3 * NN + a * stride] = omega * v23.y;
-            re[4 * NN + a * stride] = omega * acc4[a].value();
+            const float2 v12 = accp[a][0].value(), v34 = accp[a][1].value();
+            re[0 * NN + a * stride] = omega * acc4[a].value();
+            re[1 * NN + a * stride] = omega * v12.x;
+            re[2 * NN + a * stride] = omega * v12.y;
+            re[3 * NN + a * stride] = omega * v34.x;
+            re[4 * NN + a * stride] = (PH ? omega + omega : omega) * v34.y;
         }
     }
     return hmax;
@@ -539,8 +553,9 @@ __device__ __noinline__ void ws_mix_line_general(BPtr<const float2> pe, BPtr<con
 
 // Primitives of node items [s0, s_end) step `step` of a block (u layout
 // [el][var][i]) into float2 triples [el][3][i]; returns whether any node had
-// rho <= 0 or p <= 0 (or NaN).  Same arithmetic as fp32_block_convert.
-template <class S, int D>
+// rho <= 0 or p <= 0 (or NaN).  Same arithmetic as fp32_block_convert; PH
+// stores p/2 in place of p (exact).
+template <class S, int D, bool PH = false>
 __device__ __forceinline__ bool ws_primitives(BPtr<const float> U, BPtr<float2> P2, int ne, int s0, int step,
                                               BPtr<double> B64 = nullptr) {
     constexpr int NN = S::NN, U_EL = S::U_EL;
@@ -568,7 +583,7 @@ __device__ __forceinline__ bool ws_primitives(BPtr<const float> U, BPtr<float2> 
         const auto pe = P2 + el * 3 * NN + i;
         pe[0] = f2(rho, bt);
         pe[NN] = f2(hv[0], hv[1]);
-        pe[2 * NN] = f2(hv[2], p);
+        pe[2 * NN] = f2(hv[2], PH ? 0.5f * p : p);
         if (raw(B64)) {
             // mixed mode: beta = rho / p in FP64 (exact FP32 rho and p, the
             // FP32 reciprocal seed refined by one FP64 Newton step: ~2^-46)
@@ -697,7 +712,7 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
                 if (!ws_wait(copied + b, ph.next(b, true), abort)) { give_up(); ok = false; break; }
             }
             // 2. primitives of block k, handed to the sweep warps
-            bad |= ws_primitives<S, D>(rawU(b) + cur.offU, P2(b), cur.ne, st, S::SVC_THREADS,
+            bad |= ws_primitives<S, D, !MIX && FLUX == kFluxEuler>(rawU(b) + cur.offU, P2(b), cur.ne, st, S::SVC_THREADS,
                                        MIX ? B64(b) : BPtr<double>(nullptr));
             mbar_arrive(ready + b);
             // 3. block k - 1: once swept, its raw buffer takes block k + 1 and
