@@ -69,14 +69,14 @@ def test_surface_fluxes_match_interpolation_nonzeros(d, p, kind):
 
 @pytest.mark.parametrize("p, kind", [(4, 0), (4, 1), (7, 1), (2, 0)])
 def test_fp32_pipe_count_and_binding_roofline(p, kind):
-    """The FP32-pipe count: pairs x 86 + nonzero diagonal terms x 50 + nodes
+    """The FP32-pipe count: pairs x 85 + nonzero diagonal terms x 49 + nodes
     x 45 (3D Euler), diagonal terms counted from the nonzeros of diag(Q1);
     the binding roofline takes the larger of the two floors."""
     import oracle as O
     _, _, _, Q1 = O.op1d(p, kind)
     n = p + 1
     ndiag = int(np.count_nonzero(np.abs(np.diag(Q1)) > 1e-12))
-    want = bench.pairs_per_element(3, p) * 86 + 3 * n * n * ndiag * 50 + n ** 3 * 45
+    want = bench.pairs_per_element(3, p) * 85 + 3 * n * n * ndiag * 49 + n ** 3 * 45
     assert bench.fp32_pipe_ops_per_element(3, p, kind) == want
     r = bench.fp32_roofline(3, p, kind, 1000, 1.0, 6800.0)
     assert r["frac"] == pytest.approx(max(r["hbm_frac"], r["fp32_pipe_frac"]))
