@@ -43,6 +43,7 @@ NODE_FLOPS = 13          # conservative -> primitive per node
 # 2, one Newton step of the reciprocal 4, quotient and square 2, series 4 + 2,
 # scaling 2 -> 16 flops each) and the FP64 metric sum (3): 35 flops per pair.
 MIX_PAIR_FP64_FLOPS = 35
+WS_MIN_ELEM_7 = 8192          # the library's row-kernel threshold at n = 7 (kWsMinElem7)
 # The warp-specialized kernel (3D Euler, n = 3..6): FP64 only where FP32
 # would lose accuracy -- metric pair sums (3 DADD), the rho mean's sum and
 # scaling (DADD, DMUL), the beta mean's sum, reciprocal Newton step and
@@ -166,14 +167,15 @@ def measured_counters(prec, p, kind, N):
     return None
 
 
-def fp32_kernel_name(d: int, p: int, modal: bool = False) -> str:
-    """The kernel the library launches for the FP32-Kahan residual of 3D Euler."""
+def fp32_kernel_name(d: int, p: int, modal: bool = False, n_elem: int = 0) -> str:
+    """The kernel the library launches for the FP32-Kahan residual of 3D Euler
+    (Ranocha's flux) on n_elem elements."""
     n = p + 1
     if modal:
         return "volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, n)
-    if d == 3 and n in (7, 8):
+    if d == 3 and (n == 8 or (n == 7 and n_elem < WS_MIN_ELEM_7)):
         return "volume_fp32_row_kernel<%d>" % n
-    if d == 3 and 3 <= n <= 6:
+    if d == 3 and 3 <= n <= 8:
         return "volume_fp32_ws_kernel<%d,%d,euler>" % (d, n)
     return "volume_fp32_tma_kernel<%d,%d,euler>" % (d, n)
 
@@ -730,7 +732,7 @@ def main():
                     "unit": "Top/s (FP32 pipe operations)", "frac": ops / (t_launch * 1e-3) / FP32_LANE_OPS,
                     "traffic": measured_traffic(args.prec, p, kind, N),
                     "peak_source": "152 SMs x 128 FP32 lanes x 2.07 GHz (recipe unit counts and clock)",
-                    "kernel": fp32_kernel_name(d, p, modal), "binding": fp32_roofline(d, p, kind, E, t_launch, hbm_peak),
+                    "kernel": fp32_kernel_name(d, p, modal, E), "binding": fp32_roofline(d, p, kind, E, t_launch, hbm_peak),
                     "algorithmic_fp32_ops_per_launch": ops, "launch_ms": t_launch}
     elif args.prec == "fp32k":
         b32 = bytes_per_node("fp32k", d) * dof
@@ -739,7 +741,7 @@ def main():
                     "binding": None if modal else fp32_roofline(d, p, kind, E, t_launch, hbm_peak),
                     "traffic": None if modal else measured_traffic(args.prec, p, kind, N),
                     "peak_source": hbm_src,
-                    "kernel": fp32_kernel_name(d, p, modal),
+                    "kernel": fp32_kernel_name(d, p, modal, E),
                     "ncu": None if modal else measured_counters(args.prec, p, kind, N),
                     "algorithmic_bytes_per_launch": b32, "launch_ms": t_launch}
     elif args.prec == "fp32mix":
@@ -799,11 +801,20 @@ def main():
                             "alu_frac_of_measured": (fl / (t64 * 1e-3) / (fp64_tf * 1e12)) if fp64_tf else None,
                             "hbm_frac_of_measured": b64 / (t64 * 1e-3) / 1e9 / hbm_peak,
                             "entropy_identity_defect_max": entropy_defect_max(torch, ctx, tu64, tJ, r64)}
+        # global relative deviation of the FP32 result (FP32-rounded input, so
+        # input rounding included) from the FP64 result on the same mesh
+        variants["fp32k"]["max_rel_dev_from_fp64"] = ((r32.double() - r64).abs().max() / r64.abs().max()).item()
 
         def stepmix():
             A.sfh_volume_residual(ctx.handle, E, tu32.data_ptr(), tJ.data_ptr(), r32.data_ptr(), A.SFH_FP32_MIXED, sh)
         _, tmix = timed_launches(stepmix, k64, 2, stream, torch)
+        flx, inx = mix_fp64_work(d, p, kind)
         variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix,
+                               "fp64_flops_per_pair": (MIX_WS_PAIR_FP64[0] if d == 3 and 3 <= p + 1 <= 6
+                                                       else MIX_PAIR_FP64_FLOPS),
+                               "fp64_rate_frac": flx * E / (tmix * 1e-3) / (FP64_TFLOPS * 1e12),
+                               "fp64_pipe_instr_frac": inx * E / (tmix * 1e-3) / (FP64_TFLOPS * 1e12 / 2),
+                               "max_rel_dev_from_fp64": ((r32.double() - r64).abs().max() / r64.abs().max()).item(),
                                "entropy_identity_defect_max": entropy_defect_max(torch, ctx, tu64, tJ, r32)}
 
         # adjoint on this workload (the adjoint configuration is in other_configs)

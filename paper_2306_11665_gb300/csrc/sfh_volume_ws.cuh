@@ -31,13 +31,23 @@
 
 namespace sfh {
 
-// FP32-Kahan and mixed mode: n = 3..6 (at n = 6 the FP32 line body spills a
-// few registers under the 128 of sixteen warps and is still faster than the
-// thread-per-line kernel: 311 against 330 us on 32^3 elements)
+// FP32-Kahan: n = 3..8.  At n = 6 the line body spills a few registers under
+// the 128 of sixteen warps and is still faster than the thread-per-line
+// kernel (311 against 330 us on 32^3 elements).  At n = 7, 8 one element per
+// block leaves five or six sweep warps with 168 registers each; there the
+// row kernel is faster for Ranocha's flux at n = 8 and on small meshes at
+// n = 7 (see kWsMinElem7), the warp-specialized kernel otherwise (n = 7 on
+// 24^3 and 32^3 elements: 329 and 769 us against 373 and 878 us; both n for
+// Chandrashekar's flux, which has no row kernel: 1.09 against 1.25 ms at
+// n = 8 on 32^3).  Mixed mode: n = 3..6.
 template <int D, int N, int FLUX>
 constexpr bool use_ws_kernel() {
-    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 6;
+    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 8;
 }
+// below this many elements the row kernel serves 3D Euler (Ranocha) at n = 7
+// (16^3 elements: 119 against 124 us; the warp-specialized kernel's one
+// element per block leaves its pipeline short on small meshes)
+constexpr int64_t kWsMinElem7 = 8192;
 template <int D, int N, int FLUX>
 constexpr bool use_ws_mixed() {
     return D == 3 && is_euler(FLUX) && N >= 3 && N <= 6;
