@@ -910,41 +910,56 @@ def main():
     Jh = torch.from_numpy(Ja).pin_memory()
     rh = torch.empty_like(uh).pin_memory()
     ke = max(3, min(20, args.steps // 100))
-    for _ in range(2):
-        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), eprec)
-    t0 = time.perf_counter()
-    for _ in range(ke):
-        A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), eprec)
-    te = (time.perf_counter() - t0) / ke
-    if dist:
-        te = D.max_over_ranks(te, dist, dev)
-    h2d = int(uh.numel() * uh.element_size() + Jh.numel() * 8)
-    d2h = int(rh.numel() * rh.element_size())
-    # the host link's own rate: one pinned-memory copy of the same h2d bytes
-    # and one of the d2h bytes issued together (the copy engines' ceiling)
-    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
-    dst = torch.empty(h2d // 4, dtype=torch.float32, device=dev)
-    srch = torch.empty(h2d // 4, dtype=torch.float32).pin_memory()
-    srcd = torch.empty(d2h // 4, dtype=torch.float32, device=dev)
-    dsth = torch.empty(d2h // 4, dtype=torch.float32).pin_memory()
-    tl = float("inf")
-    for _ in range(3):
-        torch.cuda.synchronize()
+
+    def host_link(h2d, d2h):
+        """One pinned-memory copy of the h2d bytes and one of the d2h bytes
+        issued together: the copy engines' ceiling for those bytes (s)."""
+        s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+        dst = torch.empty(h2d // 4, dtype=torch.float32, device=dev)
+        srch = torch.empty(h2d // 4, dtype=torch.float32).pin_memory()
+        srcd = torch.empty(d2h // 4, dtype=torch.float32, device=dev)
+        dsth = torch.empty(d2h // 4, dtype=torch.float32).pin_memory()
+        tl = float("inf")
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s1):
+                dst.copy_(srch, non_blocking=True)
+            with torch.cuda.stream(s2):
+                dsth.copy_(srcd, non_blocking=True)
+            torch.cuda.synchronize()
+            tl = min(tl, time.perf_counter() - t0)
+        return tl
+
+    def timed(call):
+        for _ in range(2):
+            call()
         t0 = time.perf_counter()
-        with torch.cuda.stream(s1):
-            dst.copy_(srch, non_blocking=True)
-        with torch.cuda.stream(s2):
-            dsth.copy_(srcd, non_blocking=True)
-        torch.cuda.synchronize()
-        tl = min(tl, time.perf_counter() - t0)
-    del dst, srch, srcd, dsth
+        for _ in range(ke):
+            call()
+        t = (time.perf_counter() - t0) / ke
+        return D.max_over_ranks(t, dist, dev) if dist else t
+
+    ub = int(uh.numel() * uh.element_size())
+    # the metric terms depend only on the mesh: bound once (outside the timed
+    # region), then every step moves u in and r out
+    A.sfh_bind_metric(ctx.handle, E, Jh.data_ptr())
+    te = timed(lambda: A.sfh_volume_residual_host_bound(ctx.handle, E, uh.data_ptr(), rh.data_ptr(), eprec))
+    tl = host_link(ub, ub)
+    # the same step with the metric copied in every call as well
+    tf = timed(lambda: A.sfh_volume_residual_host(ctx.handle, E, uh.data_ptr(), Jh.data_ptr(), rh.data_ptr(), eprec))
+    tlf = host_link(ub + int(Jh.numel() * 8), ub)
     e2e = {"value": D.aggregate_throughput(dof, world, te), "unit": "element-DOF/s",
-           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-           "ms_per_step": te * 1e3, "api": "sfh_volume_residual_host (pinned host buffers)",
-           "host_link": {"copy_only_ms": tl * 1e3, "copy_only_gbs": (h2d + d2h) / tl / 1e9,
-                         "frac": tl / te,
+           "h2d_bytes_per_step": ub, "d2h_bytes_per_step": ub,
+           "ms_per_step": te * 1e3,
+           "api": "sfh_bind_metric once per mesh, then sfh_volume_residual_host_bound per step (pinned host buffers)",
+           "host_link": {"copy_only_ms": tl * 1e3, "copy_only_gbs": 2 * ub / tl / 1e9, "frac": tl / te,
                          "note": "the same bytes copied alone (pinned, both directions at once) "
-                                 "against the end-to-end step"}}
+                                 "against the end-to-end step"},
+           "metric_per_step": {"value": D.aggregate_throughput(dof, world, tf), "ms_per_step": tf * 1e3,
+                               "h2d_bytes_per_step": ub + int(Jh.numel() * 8), "d2h_bytes_per_step": ub,
+                               "api": "sfh_volume_residual_host (u and Ja copied in every step)",
+                               "host_link": {"copy_only_ms": tlf * 1e3, "frac": tlf / tf}}}
 
     return finish(args, rank, world, dist, W, E, nn, value, ms_step, roofline, e2e, clocks, variants, u64, Ja, d, p,
                   kind, torch)

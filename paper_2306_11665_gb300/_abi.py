@@ -82,6 +82,8 @@ _SIGS = {
     "sfh_fig1_hadamard": [ctypes.c_int, i64, vp, vp, ctypes.c_int, vp],
     "sfh_selftest_bounded_wait": [ctypes.c_int64, ctypes.c_void_p, dp],
     "sfh_selftest_bounds": [ctypes.c_void_p],
+    "sfh_bind_metric": [vp, ctypes.c_int64, ctypes.c_void_p],
+    "sfh_volume_residual_host_bound": [vp, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int],
     "sfh_build_flags": [],
     "sfh_server_create": [ctypes.POINTER(ServerOpts), ctypes.POINTER(vp)],
     "sfh_serve_submit": [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
@@ -216,6 +218,14 @@ def sfh_peak_fma(prec: int):
     tf, ms = ctypes.c_double(), ctypes.c_double()
     _call("sfh_peak_fma", prec, ctypes.byref(tf), ctypes.byref(ms))
     return tf.value, ms.value
+
+
+def sfh_bind_metric(ctx: int, n_elem: int, Ja_host: int):
+    _call("sfh_bind_metric", ctx, n_elem, Ja_host)
+
+
+def sfh_volume_residual_host_bound(ctx: int, n_elem: int, u_host: int, r_host: int, prec: int) -> int:
+    return _call("sfh_volume_residual_host_bound", ctx, n_elem, u_host, r_host, prec, ok=(SFH_OK, SFH_EDOMAIN))
 
 
 def sfh_build_flags() -> int:

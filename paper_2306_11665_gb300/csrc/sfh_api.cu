@@ -251,6 +251,15 @@ struct sfh_ctx {
     cudaStream_t hs[kHostStages];
     void *stage[kHostStages];
     size_t stage_bytes;
+    // metric terms bound to the context (sfh_bind_metric): device copy, its
+    // element count and capacity in bytes
+    double *d_ja;
+    int64_t ja_elems;
+    size_t ja_bytes;
+    // streams and staging buffers of the bound-metric pipeline
+    cudaStream_t bs[4];
+    void *bstage[4];
+    size_t bstage_bytes;
 };
 
 namespace {
@@ -317,6 +326,14 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
         c->stage[k] = nullptr;
     }
     c->stage_bytes = 0;
+    c->d_ja = nullptr;
+    c->ja_elems = 0;
+    c->ja_bytes = 0;
+    for (int k = 0; k < 4; ++k) {
+        c->bs[k] = nullptr;
+        c->bstage[k] = nullptr;
+    }
+    c->bstage_bytes = 0;
     const int n = p + 1;
     sfh::op_tables(p, nodes, c->tab_d, c->tab_f);
     long double x[sfh::NMAX], ww[sfh::NMAX], DD[sfh::NMAX * sfh::NMAX];
@@ -367,6 +384,11 @@ extern "C" sfh_status sfh_destroy(sfh_ctx *c) {
         if (c->stage[k]) cudaFree(c->stage[k]);
     }
     if (c->d_err) cudaFree(c->d_err);
+    if (c->d_ja) cudaFree(c->d_ja);
+    for (int k = 0; k < 4; ++k) {
+        if (c->bs[k]) { cudaStreamSynchronize(c->bs[k]); cudaStreamDestroy(c->bs[k]); }
+        if (c->bstage[k]) cudaFree(c->bstage[k]);
+    }
     delete c;
     return SFH_OK;
 }
@@ -642,6 +664,108 @@ extern "C" sfh_status sfh_volume_residual_host(sfh_ctx *c, int64_t n_elem, const
     for (int b = 0; b < kHostStages; ++b)
         if ((e = cudaStreamSynchronize(c->hs[b])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     return sfh_check(c, c->hs[0]);
+}
+
+// ---------------------------------------------------------------------------
+// bound metric: Ja uploaded once per mesh, then only u and r travel per call
+// ---------------------------------------------------------------------------
+extern "C" sfh_status sfh_bind_metric(sfh_ctx *c, int64_t n_elem, const double *Ja_host) {
+    clear_err();
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (n_elem < 0 || n_elem > (int64_t)1 << 40) return fail(SFH_EINVAL, "n_elem out of range: %lld", (long long)n_elem);
+    if (n_elem > 0 && !Ja_host) return fail(SFH_EINVAL, "Ja_host is NULL");
+    if ((uintptr_t)Ja_host % sizeof(double)) return fail(SFH_EINVAL, "misaligned Ja_host");
+    std::lock_guard<std::mutex> lk(c->host_mu);
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    const size_t jb = (size_t)n_elem * c->d * c->d * sfh::ipow(c->n, c->d) * sizeof(double);
+    cudaError_t e;
+    c->ja_elems = 0;   // no metric is bound while the copy is incomplete
+    if (c->ja_bytes < jb) {
+        if (c->d_ja) { cudaFree(c->d_ja); c->d_ja = nullptr; c->ja_bytes = 0; }
+        if ((e = cudaMalloc(&c->d_ja, jb)) != cudaSuccess) {
+            c->d_ja = nullptr;
+            return fail(SFH_ENOMEM, "metric allocation of %zu bytes failed", jb);
+        }
+        c->ja_bytes = jb;
+    }
+    if (jb && (e = cudaMemcpy(c->d_ja, Ja_host, jb, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return cuda_fail(e, "metric copy");
+    c->ja_elems = n_elem;
+    return SFH_OK;
+}
+
+// Pipeline of the bound-metric residual: chunks of about kBoundChunkBytes of
+// u rotate over kBoundStages streams, H2D(u) -> kernel -> D2H(r) on each.
+// With four stages the next chunk's copy in never waits for a copy out on
+// the same stream, so both copy directions stay busy; the chunks are small
+// enough that the first copy in and the last copy out (the pipeline's
+// unoverlapped ends) stay short.
+constexpr int kBoundStages = 4;
+constexpr size_t kBoundChunkBytes = 4u << 20;
+
+extern "C" sfh_status sfh_volume_residual_host_bound(sfh_ctx *c, int64_t n_elem, const void *u_host, void *r_host,
+                                                     sfh_prec prec) {
+    clear_err();
+    if (prec != SFH_FP64 && prec != SFH_FP32_KAHAN && prec != SFH_FP32_MIXED)
+        return fail(SFH_EINVAL, "bad precision mode %d", (int)prec);
+    if (!c) return fail(SFH_EINVAL, "ctx is NULL");
+    if (n_elem < 0) return fail(SFH_EINVAL, "n_elem must be >= 0, got %lld", (long long)n_elem);
+    if (n_elem == 0) return SFH_OK;
+    const size_t esz = elem_size(prec);
+    if (!u_host || !r_host) return fail(SFH_EINVAL, "null array pointer");
+    if (((uintptr_t)u_host % esz) || ((uintptr_t)r_host % esz)) return fail(SFH_EINVAL, "misaligned array pointer");
+    std::lock_guard<std::mutex> lk(c->host_mu);
+    if (n_elem > c->ja_elems)
+        return fail(SFH_EINVAL, "%lld elements requested, %lld bound by sfh_bind_metric", (long long)n_elem,
+                    (long long)c->ja_elems);
+    const size_t nn = (size_t)sfh::ipow(c->n, c->d);
+    const size_t ub_e = c->nvar * nn * esz, jb_e = (size_t)c->d * c->d * nn * sizeof(double);
+    if (overlap(r_host, n_elem * ub_e, u_host, n_elem * ub_e)) return fail(SFH_EINVAL, "output overlaps an input");
+    DeviceGuard g(c->device);
+    if (!g.ok) return fail(SFH_ECUDA, "cannot select the context's device");
+    // a multiple of 16 elements, so that every chunk's slice of the bound
+    // metric starts on a 16-byte boundary (the kernels' bulk copies need it)
+    int64_t chunk = std::max<int64_t>(64, (int64_t)(kBoundChunkBytes / ub_e) / 16 * 16);
+    chunk = std::min<int64_t>(chunk, n_elem);
+    const size_t need = 2 * ((size_t)chunk * ub_e + 256);   // u and r, each 256-byte aligned
+    cudaError_t e;
+    for (int k = 0; k < kBoundStages; ++k) {
+        if (!c->bs[k] && (e = cudaStreamCreateWithFlags(&c->bs[k], cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamCreate");
+    }
+    if (c->bstage_bytes < need) {
+        for (int k = 0; k < kBoundStages; ++k) {
+            if (c->bstage[k]) { cudaFree(c->bstage[k]); c->bstage[k] = nullptr; }
+        }
+        c->bstage_bytes = 0;
+        for (int k = 0; k < kBoundStages; ++k)
+            if ((e = cudaMalloc(&c->bstage[k], need)) != cudaSuccess) {
+                for (int j = 0; j < k; ++j) { cudaFree(c->bstage[j]); c->bstage[j] = nullptr; }
+                return fail(SFH_ENOMEM, "staging allocation of %zu bytes failed", need);
+            }
+        c->bstage_bytes = need;
+    }
+    const char *uh = (const char *)u_host;
+    char *rh = (char *)r_host;
+    const char *jd = (const char *)c->d_ja;
+    int64_t k = 0;
+    for (int64_t e0 = 0; e0 < n_elem; e0 += chunk, ++k) {
+        const int64_t ne = std::min<int64_t>(chunk, n_elem - e0);
+        const int b = (int)(k % kBoundStages);
+        cudaStream_t s = c->bs[b];
+        char *du = (char *)c->bstage[b];
+        char *dr = du + ((ne * ub_e + 255) / 256) * 256;
+        if ((e = cudaMemcpyAsync(du, uh + e0 * ub_e, ne * ub_e, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "host-to-device copy");
+        if ((e = launch_volume(c, prec, ne, du, (const double *)(jd + e0 * jb_e), dr, s)) != cudaSuccess)
+            return cuda_fail(e, "volume kernel launch");
+        if ((e = cudaMemcpyAsync(rh + e0 * ub_e, dr, ne * ub_e, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(e, "device-to-host copy");
+    }
+    for (int b = 0; b < kBoundStages; ++b)
+        if ((e = cudaStreamSynchronize(c->bs[b])) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return sfh_check(c, c->bs[0]);
 }
 
 // ---------------------------------------------------------------------------

@@ -59,6 +59,13 @@ def test_bad_arguments_rejected(A):
     with pytest.raises(A.SfhError) as e:
         A.sfh_operator_tables(0, 0)
     assert e.value.status == A.SFH_EINVAL
+    # the bound-metric entry points check their arguments before any CUDA call
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_bind_metric(0, 10, 8)
+    assert e.value.status == A.SFH_EINVAL
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual_host_bound(0, 10, 8, 8, A.SFH_FP32_KAHAN)
+    assert e.value.status == A.SFH_EINVAL
 
 
 def test_no_device_is_reported_not_crashed(A):

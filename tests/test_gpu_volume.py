@@ -302,6 +302,44 @@ def test_host_entry_point_matches_device(prec):
     assert np.array_equal(host, dev)
 
 
+@pytest.mark.parametrize("prec", ["fp32k", "fp32mix", "fp64"])
+def test_bound_metric_host_entry_point(prec):
+    """sfh_volume_residual_host_bound on a metric bound once equals the
+    host-buffer entry point that copies Ja every call, on two calls in a row;
+    a smaller element count uses the first elements of the bound metric, and
+    more elements than are bound are refused."""
+    ctx = api.Context(3, 4, "gll", "euler")
+    u, Ja = I.workload(3, 4, 0, 14)       # 2,744 elements: several 4 MB chunks and a ragged tail
+    src = u if prec == "fp64" else I.to_fp32(u)
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    uh = torch.from_numpy(np.ascontiguousarray(src)).to(dt).pin_memory()
+    Jh = torch.from_numpy(Ja).pin_memory()
+    want = ctx.volume_residual_host(uh, Jh, prec).double().numpy()
+    E = u.shape[0]
+    A.sfh_bind_metric(ctx.handle, E, Jh.data_ptr())
+    mode = {"fp64": A.SFH_FP64, "fp32k": A.SFH_FP32_KAHAN, "fp32mix": A.SFH_FP32_MIXED}[prec]
+    for _ in range(2):
+        rh = torch.full_like(uh, float("nan")).pin_memory()
+        assert A.sfh_volume_residual_host_bound(ctx.handle, E, uh.data_ptr(), rh.data_ptr(), mode) == A.SFH_OK
+        got = rh.double().numpy()
+        if prec == "fp64":   # another chunking may pick another FP64 kernel: equal to round-off
+            assert rel_err_per_var(got, want) <= 1e-13
+        else:
+            assert np.array_equal(got, want)
+    part = 1000
+    rh = torch.full_like(uh, float("nan")).pin_memory()
+    A.sfh_volume_residual_host_bound(ctx.handle, part, uh.data_ptr(), rh.data_ptr(), mode)
+    assert rel_err_per_var(rh[:part].double().numpy(), want[:part]) <= (1e-13 if prec == "fp64" else 0.0)
+    assert np.isnan(rh[part:].numpy()).all()
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual_host_bound(ctx.handle, E + 1, uh.data_ptr(), rh.data_ptr(), mode)
+    assert e.value.status == A.SFH_EINVAL
+    A.sfh_bind_metric(ctx.handle, 0, 0)   # unbind
+    with pytest.raises(A.SfhError) as e:
+        A.sfh_volume_residual_host_bound(ctx.handle, 1, uh.data_ptr(), rh.data_ptr(), mode)
+    assert e.value.status == A.SFH_EINVAL
+
+
 @pytest.mark.parametrize("d, p, kind", [(3, 4, 0), (3, 2, 1), (2, 5, 0), (3, 7, 1), (3, 6, 0), (3, 8, 0)])
 def test_rough_states_take_the_logarithm_path(d, p, kind):
     """States with large jumps between neighbouring nodes put many pairs
