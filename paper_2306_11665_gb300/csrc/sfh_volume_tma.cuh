@@ -147,6 +147,16 @@ __device__ __forceinline__ void line_geometry(int m, int l, const OpTab<float> &
     }
 }
 
+// 3D Euler with Ranocha's flux: the node pass stores p/2 in place of p, so
+// that the mean pressure of a pair is one addition, and the line sweep forms
+// the energy flux and its compensated sum at half scale (the pressure work
+// with p/2, the inverse beta mean from the series with halved coefficients,
+// v_a.v_b/2 in place of 2 (v_a/2).(v_b/2)).  Every such step is an exact
+// power-of-two scaling, so the energy sum is exactly half of the full-scale
+// one; the store multiplies it by 2 omega.
+template <int D, int FLUX>
+constexpr bool kHalfP = D == 3 && FLUX == kFluxEuler;
+
 // One Euler line from scratch, with the logarithm for pairs outside the
 // series band.  Kept out of line (one copy per kernel) because it runs only
 // for states with large jumps along a line; the arithmetic is that of the
@@ -160,7 +170,8 @@ __device__ __noinline__ void euler_line_general(BPtr<const float> pe, BPtr<const
         KahanF acc[NVAR];
 #pragma unroll
         for (int v = 0; v < NVAR; ++v) acc[v].zero();
-        const float ra = pe[a * stride], pa = pe[(D + 1) * NN + a * stride], ba = pe[(D + 2) * NN + a * stride];
+        constexpr float ps = kHalfP<D, FLUX> ? 2.0f : 1.0f;   // p from the stored p/2 (exact)
+        const float ra = pe[a * stride], pa = ps * pe[(D + 1) * NN + a * stride], ba = pe[(D + 2) * NN + a * stride];
         float hva[D];
 #pragma unroll
         for (int k = 0; k < D; ++k) hva[k] = pe[(1 + k) * NN + a * stride];
@@ -168,7 +179,7 @@ __device__ __noinline__ void euler_line_general(BPtr<const float> pe, BPtr<const
         for (int b = 0; b < N; ++b) {
             const float q = tab.Q1[a * N + b];
             if (q == 0.0f) continue;
-            const float rb = pe[b * stride], pb = pe[(D + 1) * NN + b * stride], bb = pe[(D + 2) * NN + b * stride];
+            const float rb = pe[b * stride], pb = ps * pe[(D + 1) * NN + b * stride], bb = pe[(D + 2) * NN + b * stride];
             float hvb[D], n[D];
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -240,7 +251,7 @@ __device__ __forceinline__ int fp32_block_convert(BPtr<const float> U, BPtr<cons
             float bt = rho * ip;
             bt = fmaf(ip, fmaf(-p, bt, rho), bt);
             pe[0] = rho;
-            pe[(D + 1) * NN] = p;
+            pe[(D + 1) * NN] = kHalfP<D, FLUX> ? 0.5f * p : p;   // exact
             pe[(D + 2) * NN] = bt;
             bad |= !(rho > 0.0f && p > 0.0f);
             // the node's d*d metric values, FP64 -> FP32, into the line of
@@ -328,8 +339,10 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, BPtr<const flo
                     for (int k = 0; k < D; ++k) hv[a][k] = pe[(1 + k) * NN + a * stride];
                     p[a] = pe[(D + 1) * NN + a * stride];
                 }
-                // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean) as one packed Horner chain
-                const float cg = (float)(2.0 / (kGamma - 1.0));
+                // S(u)/2 (rho mean) and P(u) 2/(gamma-1) (inverse beta mean; with the
+                // stored p/2, half of it) as one packed Horner chain
+                constexpr bool PH = kHalfP<D, FLUX>;
+                const float cg = (float)((PH ? 1.0 : 2.0) / (kGamma - 1.0));
                 const float2 c0 = f2(0.5f, cg), c1 = f2(0.5f * (-1.0f / 3.0f), cg * (1.0f / 3.0f));
                 const float2 c2 = f2(0.5f * (-4.0f / 45.0f), cg * (1.0f / 5.0f));
                 const float2 c3 = f2(0.5f * (-44.0f / 945.0f), cg * (1.0f / 7.0f));
@@ -366,13 +379,13 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, BPtr<const flo
                         // pressure average: {p} (Ranocha) or {rho}/{beta}
                         // (Chandrashekar), the latter from the sums and
                         // reciprocals of the log means
-                        const float pavg = FLUX == kFluxEulerCh ? s2.x * r2.y : 0.5f * (p[a] + p[b]);
+                        const float pavg = FLUX == kFluxEulerCh ? s2.x * r2.y : (PH ? p[a] + p[b] : 0.5f * (p[a] + p[b]));
                         const float work = FLUX == kFluxEulerCh ? pavg * (hna + hnb) : fmaf(p[a], hnb, p[b] * hna);
                         float2 F01, F23;
                         F01.x = frho;
                         F01.y = fmaf(frho, hv[a][0] + hv[b][0], pavg * n[0]);
                         float FE;
-                        const float K = fmaf(2.0f, hvv, m2.y);
+                        const float K = PH ? hvv + m2.y : fmaf(2.0f, hvv, m2.y);
                         if constexpr (D == 3) {
                             F23.x = fmaf(frho, hv[a][1] + hv[b][1], pavg * n[1]);
                             F23.y = fmaf(frho, hv[a][2] + hv[b][2], pavg * n[2]);
@@ -404,10 +417,12 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, BPtr<const flo
                         for (int k = 1; k < D; ++k) { hn = fmaf(hv[a][k], n[k], hn); hv2 = fmaf(hv[a][k], hv[a][k], hv2); }
                         float F[D + 2];
                         const float frho = 2.0f * rb[a].x * hn;
+                        const float pf = PH ? p[a] + p[a] : p[a];
                         F[0] = frho;
 #pragma unroll
-                        for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], p[a] * n[k]);
-                        F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * p[a] * hn * (float)(kGamma / (kGamma - 1.0)));
+                        for (int k = 0; k < D; ++k) F[1 + k] = fmaf(2.0f * frho, hv[a][k], pf * n[k]);
+                        if constexpr (PH) F[D + 1] = fmaf(frho, hv2, pf * hn * (float)(kGamma / (kGamma - 1.0)));
+                        else F[D + 1] = fmaf(frho, 2.0f * hv2, 2.0f * pf * hn * (float)(kGamma / (kGamma - 1.0)));
                         const float2 qq = f2s(qaa);
                         accp[a][0].add_prod(qq, f2(F[0], F[1]));
                         accp[a][1].add_prod(qq, f2(F[2], F[3]));
@@ -428,7 +443,7 @@ __device__ __forceinline__ void fp32_block_sweep(int tid, int ne, BPtr<const flo
                         re[1 * NN + a * stride] = omega * v01.y;
                         re[2 * NN + a * stride] = omega * v23.x;
                         re[3 * NN + a * stride] = omega * v23.y;
-                        if constexpr (D == 3) re[4 * NN + a * stride] = omega * acc4[a].value();
+                        if constexpr (D == 3) re[4 * NN + a * stride] = (PH ? omega + omega : omega) * acc4[a].value();
                     }
                 }
             } else {
