@@ -26,7 +26,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 # small-case parity and edge-case tests of the volume (all precisions and
 # kernels), VJP, surface, modal and serving paths, and the metric-range errors
 SELECTION = [
-    ("tests/test_gpu_volume.py", "parity_small or edge_cases or rough_states or domain_error or host_entry_point"),
+    ("tests/test_gpu_volume.py",
+     "parity_small or edge_cases or rough_states or domain_error or host_entry_point or bound_metric"),
     ("tests/test_gpu_vjp.py", "parity_small"),
     ("tests/test_gpu_surface.py", "parity_small or errors_and_domain"),
     ("tests/test_gpu_chandrashekar.py", "parity_small_all_modes or vjp_parity"),
