@@ -60,7 +60,7 @@ def mix_fp64_work(d: int, p: int, kind: int):
     per the kernel the library launches for (d, p)."""
     n = p + 1
     pairs = pairs_per_element(d, p)
-    if d == 3 and 3 <= n <= 6:
+    if d == 3 and 3 <= n <= 8:
         return (pairs * MIX_WS_PAIR_FP64[0] + n ** d * MIX_WS_NODE_FP64[0],
                 pairs * MIX_WS_PAIR_FP64[1] + n ** d * MIX_WS_NODE_FP64[1])
     return pairs * MIX_PAIR_FP64_FLOPS, pairs * MIX_PAIR_FP64_FLOPS   # FMA-free count
@@ -128,9 +128,9 @@ def bytes_per_node(prec: str, d: int = 3) -> int:
 TRAFFIC = {
     # (prec, p, nodes, N): ncu capture of the timed kernel, launch 2 of
     # `bench.py --steps 3 --warmup 3 --no-serve --no-variants --no-cpu --no-e2e`
-    ("fp32k", 4, 0, 32): {"bytes": 377_027_584 + 65_255_168, "sha1": "a91e895912e5bdfe6d12acb6c54d51edfb5ab497",
-                          "counters": {"issue_active_pct": 67.5, "dram_throughput_pct": 40.7, "fma_pipe_pct": 54.3,
-                                       "alu_pipe_pct": 36.5, "warps_active_pct": 24.9,
+    ("fp32k", 4, 0, 32): {"bytes": 377_012_992 + 64_857_856, "sha1": "f07fc6fdf3ae58b7d167d33e970e833921bd5eea",
+                          "counters": {"issue_active_pct": 67.3, "dram_throughput_pct": 41.2, "fma_pipe_pct": 54.2,
+                                       "alu_pipe_pct": 36.4, "warps_active_pct": 24.9,
                                        "binding": "instruction issue (FP32 pair arithmetic), not DRAM"}},
 }
 
@@ -755,7 +755,7 @@ def main():
                     "traffic": measured_traffic(args.prec, p, kind, N),
                     "peak_source": "nominal FP64 rate of the recipe table (2 DFMA per clock per SM)",
                     "kernel": ("volume_fp32_ws_kernel<%d,%d,euler,mixed> (FP64 islands)" % (d, p + 1)
-                               if d == 3 and 3 <= p + 1 <= 6 else "volume_kernel<mixed> (FP64 part)"),
+                               if d == 3 and 3 <= p + 1 <= 8 else "volume_kernel<mixed> (FP64 part)"),
                     "algorithmic_flops_per_launch": flm, "fp64_instructions_per_launch": inm, "launch_ms": t_launch}
     else:
         # FP64 arithmetic binds: the ALU roofline against the nominal FP64 rate
@@ -810,7 +810,7 @@ def main():
         _, tmix = timed_launches(stepmix, k64, 2, stream, torch)
         flx, inx = mix_fp64_work(d, p, kind)
         variants["fp32mix"] = {"element_dof_per_s": dof / (tmix * 1e-3), "ms": tmix,
-                               "fp64_flops_per_pair": (MIX_WS_PAIR_FP64[0] if d == 3 and 3 <= p + 1 <= 6
+                               "fp64_flops_per_pair": (MIX_WS_PAIR_FP64[0] if d == 3 and 3 <= p + 1 <= 8
                                                        else MIX_PAIR_FP64_FLOPS),
                                "fp64_rate_frac": flx * E / (tmix * 1e-3) / (FP64_TFLOPS * 1e12),
                                "fp64_pipe_instr_frac": inx * E / (tmix * 1e-3) / (FP64_TFLOPS * 1e12 / 2),

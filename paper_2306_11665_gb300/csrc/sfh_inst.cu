@@ -93,7 +93,7 @@ cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_ele
 #endif
 
 #if defined(SFH_INST_MIXED) && !defined(SFH_INST_MODAL)
-// Mixed mode: the warp-specialized kernel for 3D Euler at n = 3..6 (FP64
+// Mixed mode: the warp-specialized kernel for 3D Euler at n = 3..8 (FP64
 // metric pair sums and log-mean islands in its sweep), the thread-per-line
 // kernel otherwise.
 template <int D, int N, int FLUX>

@@ -39,7 +39,9 @@ namespace sfh {
 // n = 7 (see kWsMinElem7), the warp-specialized kernel otherwise (n = 7 on
 // 24^3 and 32^3 elements: 329 and 769 us against 373 and 878 us; both n for
 // Chandrashekar's flux, which has no row kernel: 1.09 against 1.25 ms at
-// n = 8 on 32^3).  Mixed mode: n = 3..6.
+// n = 8 on 32^3).  Mixed mode: n = 3..8 (at n = 7, 8 its line body spills
+// under 168 registers and is still 2.6x faster than the thread-per-line
+// kernel: 0.71 against 1.82 ms at n = 8 on 16^3 Gauss elements).
 template <int D, int N, int FLUX>
 constexpr bool use_ws_kernel() {
     return D == 3 && is_euler(FLUX) && N >= 3 && N <= 8;
@@ -50,7 +52,7 @@ constexpr bool use_ws_kernel() {
 constexpr int64_t kWsMinElem7 = 8192;
 template <int D, int N, int FLUX>
 constexpr bool use_ws_mixed() {
-    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 6;
+    return D == 3 && is_euler(FLUX) && N >= 3 && N <= 8;
 }
 
 template <int D, int N, int FLUX, bool MIX = false>

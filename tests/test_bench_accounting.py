@@ -86,7 +86,9 @@ def test_fp32_pipe_count_and_binding_roofline(p, kind):
 def test_mixed_fp64_work_per_kernel():
     """The mixed mode's FP64 count follows the kernel: 9 instructions and 11
     flops per pair plus 3 / 5 per node on the warp-specialized kernel (3D,
-    n = 3..6), 35 flops per pair on the thread-per-line kernel."""
+    n = 3..8), 35 flops per pair on the thread-per-line kernel (2D, n = 9)."""
     fl, ins = bench.mix_fp64_work(3, 4, 0)
     assert (fl, ins) == (750 * 11 + 125 * 5, 750 * 9 + 125 * 3)
-    assert bench.mix_fp64_work(3, 7, 1)[0] == bench.pairs_per_element(3, 7) * 35
+    assert bench.mix_fp64_work(3, 7, 1)[0] == bench.pairs_per_element(3, 7) * 11 + 8 ** 3 * 5
+    assert bench.mix_fp64_work(3, 8, 1)[0] == bench.pairs_per_element(3, 8) * 35
+    assert bench.mix_fp64_work(2, 4, 0)[0] == bench.pairs_per_element(2, 4) * 35
