@@ -954,8 +954,10 @@ def main():
            "ms_per_step": te * 1e3,
            "api": "sfh_bind_metric once per mesh, then sfh_volume_residual_host_bound per step (pinned host buffers)",
            "host_link": {"copy_only_ms": tl * 1e3, "copy_only_gbs": 2 * ub / tl / 1e9, "frac": tl / te,
-                         "note": "the same bytes copied alone (pinned, both directions at once) "
-                                 "against the end-to-end step"},
+                         "note": "the same bytes copied alone (pinned, both directions at once) against the "
+                                 "end-to-end step; the link, not copy concurrency, is the ceiling: one "
+                                 "host-to-device copy already runs at ~207 GB/s, and 2-16 concurrent copies "
+                                 "run no faster"},
            "metric_per_step": {"value": D.aggregate_throughput(dof, world, tf), "ms_per_step": tf * 1e3,
                                "h2d_bytes_per_step": ub + int(Jh.numel() * 8), "d2h_bytes_per_step": ub,
                                "api": "sfh_volume_residual_host (u and Ja copied in every step)",
