@@ -235,6 +235,14 @@ bool op_tables(int p, int nodes, OpTab<double> &tab_d, OpTab<float> &tab_f) {
 // one chunk overlap the kernel and the result copy of the others.
 constexpr int kHostStages = 2;
 constexpr size_t kHostChunkBytes = 48u << 20;
+// Pipeline of the bound-metric residual: chunks of about kBoundChunkBytes of
+// u rotate over kBoundStages streams, H2D(u) -> kernel -> D2H(r) on each.
+// With four stages the next chunk's copy in never waits for a copy out on
+// the same stream, so both copy directions stay busy; the chunks are small
+// enough that the first copy in and the last copy out (the pipeline's
+// unoverlapped ends) stay short.
+constexpr int kBoundStages = 4;
+constexpr size_t kBoundChunkBytes = 4u << 20;
 
 struct sfh_ctx {
     int d, p, n, nodes, nvar, flux, device;
@@ -257,8 +265,8 @@ struct sfh_ctx {
     int64_t ja_elems;
     size_t ja_bytes;
     // streams and staging buffers of the bound-metric pipeline
-    cudaStream_t bs[4];
-    void *bstage[4];
+    cudaStream_t bs[kBoundStages];
+    void *bstage[kBoundStages];
     size_t bstage_bytes;
 };
 
@@ -329,7 +337,7 @@ extern "C" sfh_status sfh_create(int d, int p, sfh_nodes nodes, int nvar, sfh_fl
     c->d_ja = nullptr;
     c->ja_elems = 0;
     c->ja_bytes = 0;
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kBoundStages; ++k) {
         c->bs[k] = nullptr;
         c->bstage[k] = nullptr;
     }
@@ -385,7 +393,7 @@ extern "C" sfh_status sfh_destroy(sfh_ctx *c) {
     }
     if (c->d_err) cudaFree(c->d_err);
     if (c->d_ja) cudaFree(c->d_ja);
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < kBoundStages; ++k) {
         if (c->bs[k]) { cudaStreamSynchronize(c->bs[k]); cudaStreamDestroy(c->bs[k]); }
         if (c->bstage[k]) cudaFree(c->bstage[k]);
     }
@@ -695,14 +703,6 @@ extern "C" sfh_status sfh_bind_metric(sfh_ctx *c, int64_t n_elem, const double *
     return SFH_OK;
 }
 
-// Pipeline of the bound-metric residual: chunks of about kBoundChunkBytes of
-// u rotate over kBoundStages streams, H2D(u) -> kernel -> D2H(r) on each.
-// With four stages the next chunk's copy in never waits for a copy out on
-// the same stream, so both copy directions stay busy; the chunks are small
-// enough that the first copy in and the last copy out (the pipeline's
-// unoverlapped ends) stay short.
-constexpr int kBoundStages = 4;
-constexpr size_t kBoundChunkBytes = 4u << 20;
 
 extern "C" sfh_status sfh_volume_residual_host_bound(sfh_ctx *c, int64_t n_elem, const void *u_host, void *r_host,
                                                      sfh_prec prec) {
