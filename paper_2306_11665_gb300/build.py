@@ -62,7 +62,8 @@ def _units(out=OUT, defs0=()):
     units = []
     for name, defs in INST:
         units.append((os.path.join(CSRC, "sfh_inst.cu"), os.path.join(out, f"inst_{name}.o"), list(defs0) + defs))
-    for src in ("sfh_api.cu", "sfh_serve.cu", "sfh_noalloc.cu", "sfh_entropy.cu", "sfh_fig1.cu", "sfh_surface.cu"):
+    for src in ("sfh_api.cu", "sfh_serve.cu", "sfh_noalloc.cu", "sfh_entropy.cu", "sfh_fig1.cu", "sfh_surface.cu",
+                "sfh_modal.cu"):
         units.append((os.path.join(CSRC, src), os.path.join(out, src.replace(".cu", ".o")), list(defs0)))
     return units
 

@@ -47,6 +47,12 @@ SFH_DECL_MODAL(volume_mixed_d2_ch_modal, float)
 SFH_DECL_MODAL(volume_mixed_d3_ch_modal, float)
 #undef SFH_DECL_MODAL
 
+// Basis transforms of the modal residual as kernels of their own (3D, FP32
+// state, n = 3..8, five variables): u_hat -> V u_hat, or (backward) r_v ->
+// V^T r_v (sfh_modal.cu).
+cudaError_t modal_xform_3d(int n, bool backward, const float *in, float *out, int64_t n_elem,
+                           const BasisTab<float> &bt, int *err, cudaStream_t stream);
+
 using ModalFn64 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<double> &,
                                   const BasisTab<double> &, int *, cudaStream_t);
 using ModalFn32 = cudaError_t (*)(int, int, const void *, const double *, void *, int64_t, const OpTab<float> &,
