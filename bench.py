@@ -43,7 +43,6 @@ NODE_FLOPS = 13          # conservative -> primitive per node
 # 2, one Newton step of the reciprocal 4, quotient and square 2, series 4 + 2,
 # scaling 2 -> 16 flops each) and the FP64 metric sum (3): 35 flops per pair.
 MIX_PAIR_FP64_FLOPS = 35
-WS_MIN_ELEM_7 = 8192          # the library's row-kernel threshold at n = 7 (kWsMinElem7)
 # The warp-specialized kernel (3D Euler, n = 3..6): FP64 only where FP32
 # would lose accuracy -- metric pair sums (3 DADD), the rho mean's sum and
 # scaling (DADD, DMUL), the beta mean's sum, reciprocal Newton step and
@@ -173,7 +172,7 @@ def fp32_kernel_name(d: int, p: int, modal: bool = False, n_elem: int = 0) -> st
     n = p + 1
     if modal:
         return "volume_fp32_tma_modal_kernel<%d,%d,euler>" % (d, n)
-    if d == 3 and (n == 8 or (n == 7 and n_elem < WS_MIN_ELEM_7)):
+    if d == 3 and n == 8:
         return "volume_fp32_row_kernel<%d>" % n
     if d == 3 and 3 <= n <= 8:
         return "volume_fp32_ws_kernel<%d,%d,euler>" % (d, n)

@@ -82,10 +82,9 @@ cudaError_t SFH_NAME(vjp_d)(int n, int flux, const double *u, const double *Ja, 
 template <int D, int N, int FLUX>
 cudaError_t launch_fp32k(const void *u, const double *Ja, void *r, int64_t n_elem, const OpTab<float> &tab, int *err,
                          cudaStream_t stream) {
-    if constexpr (use_row_kernel<D, N, FLUX>()) {
-        if (N == 8 || n_elem < kWsMinElem7) return launch_volume_fp32_row<N>(u, Ja, r, n_elem, tab, err, stream);
-    }
-    if constexpr (use_ws_kernel<D, N, FLUX>())
+    if constexpr (use_row_kernel<D, N, FLUX>())
+        return launch_volume_fp32_row<N>(u, Ja, r, n_elem, tab, err, stream);
+    else if constexpr (use_ws_kernel<D, N, FLUX>())
         return launch_volume_fp32_ws<D, N, FLUX>(u, Ja, r, n_elem, tab, err, stream);
     else
         return launch_volume_fp32_tma<D, N, FLUX>(u, Ja, r, n_elem, tab, err, stream);

@@ -430,11 +430,12 @@ cudaError_t launch_volume_fp32_row(const void *u, const double *Ja, void *r, int
     return cudaGetLastError();
 }
 
-// The row kernel serves 3D Euler at n = 7 and 8, where it measured 10-25 %
-// faster than the line kernel (3D Euler, 32^3 GLL and 16^3 Gauss meshes);
-// at n <= 6 the line kernel's register-resident line wins, and at n = 9 the
-// 27-lane groups of the row kernel lose.
+// The row kernel serves 3D Euler (Ranocha's flux) at n = 8, where it
+// measured 10-25 % faster than the line kernel and, on small meshes, than
+// the warp-specialized kernel (146 against 168 us on 16^3 Gauss elements);
+// at n <= 7 the warp-specialized kernel wins, and at n = 9 the 27-lane
+// groups of the row kernel lose.
 template <int D, int N, int FLUX>
-constexpr bool use_row_kernel() { return D == 3 && FLUX == kFluxEuler && (N == 7 || N == 8); }
+constexpr bool use_row_kernel() { return D == 3 && FLUX == kFluxEuler && N == 8; }
 
 }  // namespace sfh

@@ -33,23 +33,20 @@ namespace sfh {
 
 // FP32-Kahan: n = 3..8.  At n = 6 the line body spills a few registers under
 // the 128 of sixteen warps and is still faster than the thread-per-line
-// kernel (311 against 330 us on 32^3 elements).  At n = 7, 8 one element per
-// block leaves five or six sweep warps with 168 registers each; there the
-// row kernel is faster for Ranocha's flux at n = 8 and on small meshes at
-// n = 7 (see kWsMinElem7), the warp-specialized kernel otherwise (n = 7 on
-// 24^3 and 32^3 elements: 329 and 769 us against 373 and 878 us; both n for
-// Chandrashekar's flux, which has no row kernel: 1.09 against 1.25 ms at
-// n = 8 on 32^3).  Mixed mode: n = 3..8 (at n = 7, 8 its line body spills
-// under 168 registers and is still 2.6x faster than the thread-per-line
+// kernel (311 against 330 us on 32^3 elements).  At n = 7 two elements per
+// block with ten sweep warps and two service warps beat the row kernel at
+// every mesh size (604 against 877 us on 32^3 elements, 104 against 119 us
+// on 16^3).  At n = 8 (one element per block) the row kernel stays faster
+// for Ranocha's flux on small meshes (146 against 168 us on 16^3 Gauss
+// elements; 1.075 against 1.062 ms on 32^3), so it keeps n = 8; Chandrashekar's
+// flux has no row kernel and takes this one.  Mixed mode: n = 3..8 (at n = 7,
+// 8 its line body spills, and is still 2.6x faster than the thread-per-line
 // kernel: 0.71 against 1.82 ms at n = 8 on 16^3 Gauss elements).
 template <int D, int N, int FLUX>
 constexpr bool use_ws_kernel() {
     return D == 3 && is_euler(FLUX) && N >= 3 && N <= 8;
 }
-// below this many elements the row kernel serves 3D Euler (Ranocha) at n = 7
-// (16^3 elements: 119 against 124 us; the warp-specialized kernel's one
-// element per block leaves its pipeline short on small meshes)
-constexpr int64_t kWsMinElem7 = 8192;
+
 template <int D, int N, int FLUX>
 constexpr bool use_ws_mixed() {
     return D == 3 && is_euler(FLUX) && N >= 3 && N <= 8;
@@ -69,12 +66,18 @@ struct WsShape {
     // twelve sweep warps (three per sub-partition) also in the mixed mode:
     // its FP64 chains are latency-bound, and more warps beat more registers
     // per warp (653 against 763 us at p = 4 with eight warps of 168 registers)
-    static constexpr int SVC_WARPS = 4, MAX_SWEEP_WARPS = 12;
+    static constexpr int SVC_WARPS = N >= 7 ? 2 : 4, MAX_SWEEP_WARPS = 12;
+    // residual buffers: two (the sweep of block k + 1 overlaps the store of
+    // block k), one at n >= 7, where the shared memory it frees holds a second
+    // element per block at n = 7; with two service warps the ten sweep warps
+    // of that block keep 168 registers (n = 7 on 32^3 elements: 604 against
+    // 767 us with one element per block and four service warps)
+    static constexpr int RB = N >= 7 ? 1 : 2;
     static constexpr int SVC_THREADS = 32 * SVC_WARPS;
     static constexpr int RAW_EL = 4 * U_EL + 8 * J_EL;
     // double-buffered raw staging, primitives and residual slices (the mixed
     // mode adds an FP64 beta = rho / p per node)
-    static constexpr int EL_BYTES = 2 * RAW_EL + 2 * 8 * P2_EL + 2 * 4 * D * U_EL + (MIX ? 2 * 8 * NN : 0);
+    static constexpr int EL_BYTES = 2 * RAW_EL + 2 * 8 * P2_EL + RB * 4 * D * U_EL + (MIX ? 2 * 8 * NN : 0);
     static constexpr int HDR = 128;                       // mbarriers
     static constexpr int SMEM_MAX = 227 * 1024;
     static constexpr int SLACK = 4 * 48;                  // aligned-window slack of the four raw arrays
@@ -101,7 +104,7 @@ struct WsShape {
     static constexpr int OFF_R = up16(OFF_P2 + 2 * P2_BYTES);              // R[b]: [m][el][var][i]
     static constexpr int R_SLICE = EPB * U_EL;   // floats of one direction's residual slice
     static constexpr int R_BYTES = D * R_SLICE * 4;
-    static constexpr int OFF_B64 = up16(OFF_R + 2 * R_BYTES);              // B64[b]: [el][i] (mixed)
+    static constexpr int OFF_B64 = up16(OFF_R + RB * R_BYTES);              // B64[b]: [el][i] (mixed)
     static constexpr int B64_BYTES = MIX ? EPB * NN * 8 : 0;
     static constexpr size_t SMEM = (size_t)OFF_B64 + 2 * (size_t)B64_BYTES;
     static_assert(SMEM <= (size_t)SMEM_MAX, "shared memory");
@@ -618,7 +621,7 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
     uint64_t *full = reinterpret_cast<uint64_t *>(sm);   // raw[b] landed (bulk copy)
     uint64_t *ready = full + 2;                          // P2[b] holds the block's primitives
     uint64_t *swept = full + 4;                          // R[b] written, raw[b] and P2[b] read
-    uint64_t *stored = full + 6;                         // R[b] stored
+    uint64_t *stored = full + 6;                         // R[b] stored (one buffer: stored[0] only)
     uint64_t *copied = full + 8;                         // raw[b] filled by plain loads instead
     __shared__ int s_abort;
     volatile int *abort = &s_abort;
@@ -652,7 +655,8 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
         return SFH_BP(reinterpret_cast<float2 *>(sm + S::OFF_P2 + b * S::P2_BYTES), S::P2_BYTES / 8, err);
     };
     auto R = [&](int b) {
-        return SFH_BP(reinterpret_cast<float *>(sm + S::OFF_R + b * S::R_BYTES), S::R_BYTES / 4, err);
+        return SFH_BP(reinterpret_cast<float *>(sm + S::OFF_R + (S::RB == 2 ? b : 0) * S::R_BYTES), S::R_BYTES / 4,
+                      err);
     };
     auto B64 = [&](int b) {
         return SFH_BP(reinterpret_cast<double *>(sm + S::OFF_B64 + b * S::B64_BYTES), S::B64_BYTES / 8, err);
@@ -733,7 +737,7 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
                 if (!ws_wait(swept + (b ^ 1), ((k - 1) >> 1) & 1, abort)) { give_up(); ok = false; break; }
                 if (st == 0 && k + 1 < nloc) issue(k + 1);
                 store(k - 1);
-                mbar_arrive(stored + (b ^ 1));
+                mbar_arrive(stored + (S::RB == 2 ? (b ^ 1) : 0));
             }
         }
         if (ok) {
@@ -758,9 +762,10 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
             const int b = k & 1;
             const BlockPlan cur = plan(k);
             // primitives ready; the raw Ja landed (bulk copy or plain loads);
-            // the residual slices of block k - 2 stored
+            // the residual buffer free: block k - 2 stored (one buffer: k - 1)
             if (!ws_wait(ready + b, (k >> 1) & 1, abort) || !ws_wait((cur.tma ? full : copied) + b, ph.next(b, !cur.tma), abort) ||
-                (k >= 2 && !ws_wait(stored + b, ((k - 2) >> 1) & 1, abort))) {
+                (S::RB == 2 ? (k >= 2 && !ws_wait(stored + b, ((k - 2) >> 1) & 1, abort))
+                            : (k >= 1 && !ws_wait(stored, (k - 1) & 1, abort)))) {
                 give_up();
                 break;
             }

@@ -135,18 +135,20 @@ def test_euler_p7_gauss_16cubed_sampled():
 
 
 @pytest.mark.parametrize("p, kind", [(6, 0), (6, 1)])
-def test_euler_p6_large_mesh_takes_the_warp_specialized_kernel(p, kind):
-    """At n = 7 the library switches from the row kernel to the warp-specialized
-    kernel at 8,192 elements (FP32-Kahan, Ranocha's flux); 21^3 = 9,261 elements
-    take the latter, checked on sampled elements.  The same elements computed
-    as a small mesh take the row kernel, which must meet the same bars."""
-    errs, u, Ja, idx, ctx = _sampled(3, p, kind, 21, ["fp32k"], 16, 31)
-    small, st = run_gpu(ctx, I.to_fp32(u[idx]), Ja[idx], "fp32k")   # row kernel (below the threshold)
-    assert st == A.SFH_OK
+def test_euler_p6_two_element_blocks_sampled(p, kind):
+    """At n = 7 the warp-specialized kernel takes two elements per block, one
+    residual buffer and two service warps; 21^3 = 9,261 elements (an odd
+    count: a one-element tail block) checked on sampled elements, and the
+    same elements as a small mesh (other block boundaries) meet the same bars."""
+    errs, u, Ja, idx, ctx = _sampled(3, p, kind, 21, ["fp32k", "fp32mix"], 16, 31)
     u32 = I.to_fp32(u[idx]).astype(np.float64)
-    fp32_check(small, O.volume_sf(3, p, kind, O.FLUX_EULER, u[idx], Ja[idx]),
-               O.volume_sf(3, p, kind, O.FLUX_EULER, u32, Ja[idx]),
-               terms=O.volume_absterms(3, p, kind, O.FLUX_EULER, u32, Ja[idx]))
+    ref = O.volume_sf(3, p, kind, O.FLUX_EULER, u[idx], Ja[idx])
+    ref_w = O.volume_sf(3, p, kind, O.FLUX_EULER, u32, Ja[idx])
+    S = O.volume_absterms(3, p, kind, O.FLUX_EULER, u32, Ja[idx])
+    for prec in ("fp32k", "fp32mix"):
+        small, st = run_gpu(ctx, I.to_fp32(u[idx]), Ja[idx], prec)
+        assert st == A.SFH_OK
+        fp32_check(small, ref, ref_w, terms=S)
 
 
 @pytest.mark.parametrize("p, kind, N", [(4, 0, 8), (7, 1, 4)])
