@@ -177,8 +177,8 @@ cudaError_t SFH_FN(int n, int flux, const void *u, const double *Ja, void *r, in
     constexpr int D = SFH_INST_D;
 #if defined(SFH_INST_FP32K)
     // FP32-Kahan: the persistent TMA-staged kernels (warp-specialized for 3D
-    // Euler at n = 3..6, a thread per line and node for 3D Euler at n = 7, 8,
-    // a thread per line otherwise)
+    // Euler at n = 3..7, a thread per line and node for 3D Euler at n = 8, a
+    // thread per line otherwise)
 #define SFH_VCALL(N, F) launch_fp32k<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
 #elif defined(SFH_INST_FP64)
 #define SFH_VCALL(N, F) launch_fp64<D, N, F>(u, Ja, r, n_elem, tab, err, stream)
