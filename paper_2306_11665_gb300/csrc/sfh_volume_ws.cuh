@@ -1,5 +1,5 @@
 // sfh_volume_ws.cuh -- warp-specialized persistent FP32 volume residual of
-// the 3D Euler fluxes: FP32-Kahan at n = 3..5, the mixed mode at n = 3..6.
+// the 3D Euler fluxes: FP32-Kahan and the mixed mode at n = 3..8.
 //
 // The arithmetic is that of the persistent line kernel (Eq. 3 with the Eq. 5
 // operators: one unordered line pair per flux evaluation, scattered to both
@@ -8,10 +8,16 @@
 // is how the work is laid out on an SM:
 //   * one CTA per SM, two roles.  Sweep warps (up to twelve) own one
 //     (direction, element, line) each and run the pair loops; four service
-//     warps stage the element blocks (1D bulk copies, mbarrier completion),
-//     compute the primitives of every node and store the residual;
+//     warps (two at n >= 7) stage the element blocks (1D bulk copies,
+//     mbarrier completion), compute the primitives of every node and store
+//     the residual;
+//   * FP32-Kahan at n = 3..6 splits the registers between the roles
+//     (setmaxnreg): the service warpgroup gives back registers it does not
+//     need and the three sweep warpgroups take them, 152 a thread at n = 5, 6
+//     and 144 at n = 3, 4 instead of the 128 that sixteen warps leave;
 //   * element blocks rotate through two sets of buffers (raw u and Ja,
-//     primitives, the directions' residual slices), and the roles hand
+//     primitives, the directions' residual slices; one residual buffer at
+//     n >= 7), and the roles hand
 //     blocks to each other through mbarriers: the service warps prepare
 //     block k + 1 and store block k - 1 while the sweep warps work on block
 //     k, so neither role waits at a CTA-wide barrier;
@@ -31,9 +37,9 @@
 
 namespace sfh {
 
-// FP32-Kahan: n = 3..8.  At n = 6 the line body spills a few registers under
-// the 128 of sixteen warps and is still faster than the thread-per-line
-// kernel (311 against 330 us on 32^3 elements).  At n = 7 two elements per
+// FP32-Kahan: n = 3..8.  At n = 6 the line body fits the 152 registers of
+// the split (it spilled under the 128 of sixteen warps: 273 against 310 us
+// on 32^3 elements, 330 us on the thread-per-line kernel).  At n = 7 two elements per
 // block with ten sweep warps and two service warps beat the row kernel at
 // every mesh size (604 against 877 us on 32^3 elements, 104 against 119 us
 // on 16^3).  At n = 8 (one element per block) the row kernel stays faster
@@ -86,7 +92,17 @@ struct WsShape {
     static constexpr int EPB = epb_smem() < epb_lanes() ? epb_smem() : epb_lanes();
     static_assert(EPB >= 1, "one element must fit");
     static constexpr int TASKS = EPB * TASKS_EL;
-    static constexpr int SWEEP_WARPS = (TASKS + 31) / 32;
+    // register split between the roles (FP32-Kahan with four service warps
+    // and at most twelve sweep warps; sweep warps padded to whole warpgroups,
+    // the unit of setmaxnreg).  The shares add up to at most the registers
+    // the CTA is launched with, MAXREG a thread, so neither role can wait on
+    // registers that do not exist; the launch checks that the compiled
+    // kernel has MAXREG.  Measured on 32^3 elements (same bits): n = 5 131.5
+    // (64/144: 133.3) against 135.9 us unsplit; n = 6 272.8 (277.9) against
+    // 309.7 us; n = 4 67.8 with 64/144 (74.0 with 56/152) against 70.6 us.
+    // The mixed mode gains nothing from it (650 against 653 us at n = 5).
+    static constexpr bool SPLIT = !MIX && SVC_WARPS == 4 && (TASKS + 127) / 128 == 3;
+    static constexpr int SWEEP_WARPS = SPLIT ? 12 : (TASKS + 31) / 32;
     static constexpr int SWEEP_THREADS = 32 * SWEEP_WARPS;
     static constexpr int THREADS = SWEEP_THREADS + SVC_THREADS;
     // registers per thread: each of the SM's four sub-partitions holds the
@@ -94,6 +110,11 @@ struct WsShape {
     // 16K-entry file; in units of 8
     static constexpr int WARPS_PER_SUB = (THREADS / 32 + 3) / 4;
     static constexpr int MAXREG = (16384 / (32 * WARPS_PER_SUB)) / 8 * 8 < 255 ? (16384 / (32 * WARPS_PER_SUB)) / 8 * 8 : 255;
+    static constexpr int SVC_REG = N >= 5 ? 56 : 64, SWEEP_REG = N >= 5 ? 152 : 144;
+    static_assert(!SPLIT || (MAXREG == 128 && SVC_REG % 8 == 0 && SWEEP_REG % 8 == 0 &&
+                             SVC_REG * SVC_THREADS + SWEEP_REG * SWEEP_THREADS <= MAXREG * THREADS &&
+                             SVC_REG * 32 + SWEEP_REG * 96 <= 16384),
+                  "register split within the launch's registers (per CTA and per sub-partition)");
     static constexpr int up16(int x) { return (x + 15) / 16 * 16; }
     static constexpr int RAWU_BYTES = up16(EPB * U_EL * 4 + 16);   // + aligned-window slack
     static constexpr int RAWJ_BYTES = up16(EPB * J_EL * 8 + 16);
@@ -676,6 +697,7 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
 
     if (tid >= S::SWEEP_THREADS) {
         // ------------------------------------------------------------ service
+        if constexpr (S::SPLIT) asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;\n" ::"n"(S::SVC_REG));
         const int st = tid - S::SWEEP_THREADS;
         int issued = 0, landed = 0;   // TMA blocks issued / waited for (thread st == 0)
         auto issue = [&](int k) {
@@ -756,6 +778,7 @@ volume_fp32_ws_kernel(const float *__restrict__ u, const double *__restrict__ Ja
         }
     } else {
         // --------------------------------------------------------------- sweep
+        if constexpr (S::SPLIT) asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;\n" ::"n"(S::SWEEP_REG));
         uint32_t hmax = 0;
         RawPhases ph;   // as in the service role
         for (int k = 0; k < nloc; ++k) {
@@ -801,6 +824,13 @@ cudaError_t launch_volume_fp32_ws(const void *u, const double *Ja, void *r, int6
                           reinterpret_cast<uintptr_t>(r)) & 15) == 0;
     const int64_t nblk = (n_elem + S::EPB - 1) / S::EPB;
     auto kern = volume_fp32_ws_kernel<D, N, FLUX, MIX>;
+    if constexpr (S::SPLIT) {
+        // the register split assumes MAXREG registers a thread at launch
+        cudaFuncAttributes fa;
+        const cudaError_t ea = cudaFuncGetAttributes(&fa, kern);
+        if (ea != cudaSuccess) return ea;
+        if (fa.numRegs != S::MAXREG) return cudaErrorInvalidKernelImage;
+    }
     const cudaError_t e0 = persistent_slots(kern, S::THREADS, S::SMEM, cache, per_sm, sms);
     if (e0 != cudaSuccess) return e0;
     const int64_t grid = nblk < (int64_t)sms * per_sm ? nblk : (int64_t)sms * per_sm;
