@@ -336,10 +336,13 @@ def srv_ctas(torch):
     return torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
 
 
-def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0, fp32_share=0.7):
+def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vjp_share=0.0, fp32_share=0.7,
+                gauss_share=0.5, ch_share=0.25):
     """Serving stream: n_req requests, n_elem log-uniform in [64, 4096], p uniform
-    in {2..8} (Gauss-Lobatto), 70% FP32 / 30% FP64 residuals (a vjp_share of
-    them VJPs instead), states and metrics resident, 40 GB admission budget.
+    in {2..8}, Gauss nodes for a gauss_share of them (Gauss-Lobatto otherwise),
+    Chandrashekar's flux for a ch_share (Ranocha's otherwise), 70% FP32 / 30%
+    FP64 residuals (a vjp_share of them VJPs instead), states and metrics
+    resident, 40 GB admission budget.
     Capacity = all requests released at once; then Poisson arrivals at the given
     fractions of capacity; p50/p99 latency = submit -> done, split at the
     device start of the first tile into queueing and execution.  Baselines at
@@ -352,37 +355,41 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
     dev = torch.device("cuda")
     pools = {}
     for p in range(2, 9):
-        u64, Ja = I.workload(3, p, 0, 16, seed0=2 + p)                  # 4096 elements per degree
-        pools[p] = dict(u64=torch.from_numpy(u64).to(dev), u32=torch.from_numpy(I.to_fp32(u64)).to(dev),
-                        Ja=torch.from_numpy(Ja).to(dev),
-                        lam=torch.from_numpy(I.cotangent(u64.shape, seed=100 + p)).to(dev))
+        for nodes in (0, 1):
+            u64, Ja = I.workload(3, p, nodes, 16, seed0=2 + p + 10 * nodes)   # 4096 elements per degree
+            pools[p, nodes] = dict(u64=torch.from_numpy(u64).to(dev), u32=torch.from_numpy(I.to_fp32(u64)).to(dev),
+                                   Ja=torch.from_numpy(Ja).to(dev),
+                                   lam=torch.from_numpy(I.cotangent(u64.shape, seed=100 + p)).to(dev))
     specs = []
     for _ in range(n_req):
         ne = int(round(math.exp(rng.uniform(math.log(64), math.log(4096)))))
         p = int(rng.integers(2, 9))
         vjp = rng.uniform() < vjp_share
         prec = A.SFH_FP64 if (vjp or rng.uniform() >= fp32_share) else A.SFH_FP32_KAHAN
-        specs.append((ne, p, prec, vjp))
+        nodes = 1 if rng.uniform() < gauss_share else 0
+        flux = A.SFH_FLUX_EULER_CHANDRASHEKAR if rng.uniform() < ch_share else A.SFH_FLUX_EULER_RANOCHA
+        specs.append((ne, p, prec, vjp, nodes, flux))
     outs = []
     reqs = []
     reqs64 = []   # the same requests as FP64 launches (the plain single-launch FP64 form)
     o64s = []
     dof = 0
-    for ne, p, prec, vjp in specs:
-        P = pools[p]
+    for ne, p, prec, vjp, nodes, flux in specs:
+        P = pools[p, nodes]
         u = P["u64"] if prec == A.SFH_FP64 else P["u32"]
         out = torch.empty((ne,) + tuple(u.shape[1:]), dtype=u.dtype, device=dev)
         outs.append(out)
-        reqs.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, 0, prec, ne, u.data_ptr(),
-                              P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None, out.data_ptr()))
+        reqs.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, nodes, prec, ne, u.data_ptr(),
+                              P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None, out.data_ptr(), flux))
         o64 = out if u.dtype == torch.float64 else torch.empty((ne,) + tuple(u.shape[1:]), dtype=torch.float64,
                                                                device=dev)
         o64s.append(o64)
-        reqs64.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, 0, A.SFH_FP64, ne,
+        reqs64.append(A.Request(A.SFH_REQ_VJP if vjp else A.SFH_REQ_RESIDUAL, p, nodes, A.SFH_FP64, ne,
                                 P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr() if vjp else None,
-                                o64.data_ptr()))
+                                o64.data_ptr(), flux))
         dof += ne * (p + 1) ** 3
-    res = {"requests": n_req, "dof_total": dof, "vjp_share": vjp_share}
+    res = {"requests": n_req, "dof_total": dof, "vjp_share": vjp_share, "fp32_share": fp32_share,
+           "gauss_share": gauss_share, "chandrashekar_share": ch_share}
     with Server(hbm_budget_bytes=40 << 30, max_inflight=64, timeout_ms=120000) as srv:
         A.sfh_serve_replay(srv.handle, reqs[:50], [0.0] * 50, 60000)           # warm-up
         s0 = A.sfh_serve_stats(srv.handle)
@@ -425,19 +432,22 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
                                "dof_per_s": dof / fspan}
             res[f"load_{int(load * 100)}"] = entry
     # serial single-request FP64 launches of the same stream
-    ctxs = {p: api.Context(3, p, "gll", "euler") for p in range(2, 9)}
+    fname = {A.SFH_FLUX_EULER_RANOCHA: "euler", A.SFH_FLUX_EULER_CHANDRASHEKAR: "euler_chandrashekar"}
+    ctxs = {(p, nodes, flux): api.Context(3, p, nodes, fname[flux])
+            for p in range(2, 9) for nodes in (0, 1) for flux in fname}
     stream = torch.cuda.current_stream()
     lat = []
     t_all = time.perf_counter()
-    for (ne, p, prec, vjp), out in zip(specs, outs):
-        P = pools[p]
+    for (ne, p, prec, vjp, nodes, flux), out in zip(specs, outs):
+        P = pools[p, nodes]
+        c = ctxs[p, nodes, flux]
         o64 = torch.empty((ne, 5, (p + 1) ** 3), dtype=torch.float64, device=dev)
         t0 = time.perf_counter()
         if vjp:
-            A.sfh_vjp(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), o64.data_ptr(),
+            A.sfh_vjp(c.handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), o64.data_ptr(),
                       stream.cuda_stream)
         else:
-            A.sfh_volume_residual(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), o64.data_ptr(),
+            A.sfh_volume_residual(c.handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), o64.data_ptr(),
                                   A.SFH_FP64, stream.cuda_stream)
         stream.synchronize()
         lat.append((time.perf_counter() - t0) * 1e3)
@@ -448,15 +458,16 @@ def serve_bench(torch, A, I, api, n_req=2000, seed=7, loads=(0.5, 0.8, 0.95), vj
     # standalone kernels, one request at a time)
     lat = []
     t_all = time.perf_counter()
-    for (ne, p, prec, vjp), out in zip(specs, outs):
-        P = pools[p]
+    for (ne, p, prec, vjp, nodes, flux), out in zip(specs, outs):
+        P = pools[p, nodes]
+        c = ctxs[p, nodes, flux]
         t0 = time.perf_counter()
         if vjp:
-            A.sfh_vjp(ctxs[p].handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), out.data_ptr(),
+            A.sfh_vjp(c.handle, ne, P["u64"].data_ptr(), P["Ja"].data_ptr(), P["lam"].data_ptr(), out.data_ptr(),
                       stream.cuda_stream)
         else:
             u = P["u64"] if prec == A.SFH_FP64 else P["u32"]
-            A.sfh_volume_residual(ctxs[p].handle, ne, u.data_ptr(), P["Ja"].data_ptr(), out.data_ptr(), prec,
+            A.sfh_volume_residual(c.handle, ne, u.data_ptr(), P["Ja"].data_ptr(), out.data_ptr(), prec,
                                   stream.cuda_stream)
         stream.synchronize()
         lat.append((time.perf_counter() - t0) * 1e3)

@@ -70,8 +70,8 @@ typedef enum {
     SFH_FLUX_EULER_CHANDRASHEKAR = 2 /* Chandrashekar's EC/KEP flux (named for the TGV runs of
                                    Section 3): as Ranocha's but with the pressure average
                                    {rho}/{beta} (beta = rho/p) and pressure work {rho}/{beta} {v}.n.
-                                   Residual, VJP, entropy identity and the host entry points;
-                                   not served by the serving runtime (Ranocha's flux only) */
+                                   Residual, VJP, entropy identity, the host entry points and
+                                   the serving runtime */
 } sfh_flux;
 
 typedef enum {
@@ -373,8 +373,9 @@ int sfh_build_flags(void);
 sfh_status sfh_selftest_bounds(sfh_stream_t stream);
 
 /* ---------------------------------------------------------------------------
- * Serving: batched residual and VJP requests of mixed degree p, element
- * count and precision on one device (3D Euler, Ranocha flux).  Requests are
+ * Serving: batched residual and VJP requests of mixed degree p, node set,
+ * flux, element count and precision on one device (3D Euler, Ranocha's or
+ * Chandrashekar's flux; nodal form).  Requests are
  * admitted in FIFO order against an HBM budget and a limit on requests in
  * flight; admitted work is cut into element tiles and executed by persistent
  * CTAs that pull tiles from a device queue, so tiles of requests that arrive
@@ -401,6 +402,8 @@ typedef struct {
     const double *Ja;    /* device, resident */
     const double *lambda;/* device, VJP only */
     void *out;           /* device: r (residual) or grad_u (VJP), overwritten */
+    int flux;            /* sfh_flux: SFH_FLUX_EULER_RANOCHA or SFH_FLUX_EULER_CHANDRASHEKAR
+                            (anything else, Burgers included: SFH_EINVAL) */
 } sfh_request;
 
 typedef struct {
@@ -449,8 +452,8 @@ sfh_status sfh_serve_replay(sfh_server *srv, int n, const sfh_request *reqs, con
  * as one plain launch of sfh_volume_residual (in its own precision) or
  * sfh_vjp, in FIFO order on one stream of the current device, enqueued at
  * its arrival time, so that waiting behind earlier requests is part of its
- * latency.  Requests as for sfh_serve_submit (3D Euler, Ranocha flux);
- * contexts are created per degree for the call.  results[i]: t_submit_ns =
+ * latency.  Requests as for sfh_serve_submit (3D Euler, either flux);
+ * contexts are created per node set, flux and degree for the call.  results[i]: t_submit_ns =
  * t_admit_ns = enqueue time; t_start_ns = max(enqueue time, previous
  * request's done time), the start of a FIFO stream; t_done_ns = host time at
  * which its completion was seen (polled every ~10 us).  Blocks until all are

@@ -47,7 +47,13 @@ class ServerOpts(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("p", ctypes.c_int), ("nodes", ctypes.c_int), ("prec", ctypes.c_int),
                 ("n_elem", ctypes.c_int64), ("u", ctypes.c_void_p), ("Ja", ctypes.c_void_p),
-                ("lambda_", ctypes.c_void_p), ("out", ctypes.c_void_p)]
+                ("lambda_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("flux", ctypes.c_int)]
+
+    def __init__(self, *args, **kw):
+        # the flux field comes last; a request built without it is Ranocha's
+        if len(args) < len(self._fields_):
+            kw.setdefault("flux", SFH_FLUX_EULER_RANOCHA)
+        super().__init__(*args, **kw)
 
 
 class Result(ctypes.Structure):

@@ -93,6 +93,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, e
     os.makedirs(out, exist_ok=True)
     units = _units(out, ["-DSFH_DEBUG"] if debug else [])
     todo = [u for u in units if force or _stale(u[0], u[1])]
+    # the serving unit (every tile body of both Euler fluxes in one kernel)
+    # is the longest compile: started first, it does not finish last
+    todo.sort(key=lambda u: 0 if os.path.basename(u[0]) == "sfh_serve.cu" else 1)
     jobs = jobs or max(1, min(len(todo) or 1, os.cpu_count() or 1))
     logs = []
     if todo:

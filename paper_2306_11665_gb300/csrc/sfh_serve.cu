@@ -1,6 +1,6 @@
 // sfh_serve.cu -- serving runtime: continuous batching of residual and VJP
-// requests (3D Euler, Ranocha flux, p = 2..8, mixed precision) through one
-// persistent kernel.
+// requests (3D Euler, Ranocha's or Chandrashekar's flux, p = 2..8, mixed
+// precision) through one persistent kernel.
 //
 // Data path
 //   * The host admission thread takes requests FIFO as long as the HBM budget
@@ -11,7 +11,7 @@
 //   * Persistent CTAs (one per SM by default) claim ring entries with a
 //     compare-and-swap on a device-side head counter -- only entries below the
 //     published tail -- and run the tile with the body of the request's class
-//     (kind x precision x degree).  Tiles of requests that arrive while
+//     (kind x precision x degree x flux).  Tiles of requests that arrive while
 //     others run are claimed as soon as they are published, so their work
 //     interleaves on the GPU.
 //   * A per-request tile counter on the device finds the last tile; its CTA
@@ -56,7 +56,8 @@ struct Tile {
 };
 
 struct __align__(16) Req {   // written by the host before the request's tiles are published
-    int32_t kind, prec, n, nodes;
+    int16_t kind, flux;
+    int32_t prec, n, nodes;
     const void *u;
     const double *Ja;
     const double *lam;
@@ -133,12 +134,25 @@ struct ServeF32 {
     static_assert(D * EPB * NLINE <= kThreads, "one thread per line task");
 };
 
-template <int N> struct Cls {
-    using F64 = Shape<3, N, kFluxEuler, ModeFP64, kTileBudget, kThreads>;
+template <int N, int FLUX = kFluxEuler> struct Cls {
+    using F64 = Shape<3, N, FLUX, ModeFP64, kTileBudget, kThreads>;
     using F32 = ServeF32<N>;   // tiles of F32::TILE elements
-    using MIX = Shape<3, N, kFluxEuler, ModeMixed, kTileBudget, kThreads>;
-    using VJP = VjpShape<3, N, kFluxEuler, kTileBudget, kThreads>;
+    using MIX = Shape<3, N, FLUX, ModeMixed, kTileBudget, kThreads>;
+    using VJP = VjpShape<3, N, FLUX, kTileBudget, kThreads>;
 };
+// both Euler fluxes have the same node data, so a class's tiles do not
+// depend on the flux (tile_epb takes none)
+template <int N> constexpr bool same_tiles() {
+    using R = Cls<N, kFluxEuler>;
+    using C = Cls<N, kFluxEulerCh>;
+    return R::F64::EPB == C::F64::EPB && R::F64::SMEM == C::F64::SMEM && R::MIX::EPB == C::MIX::EPB &&
+           R::MIX::SMEM == C::MIX::SMEM && R::VJP::EPB == C::VJP::EPB && R::VJP::SMEM == C::VJP::SMEM &&
+           R::VJP::THREADS == C::VJP::THREADS && R::F64::THREADS == C::F64::THREADS &&
+           R::MIX::THREADS == C::MIX::THREADS;
+}
+static_assert(same_tiles<3>() && same_tiles<4>() && same_tiles<5>() && same_tiles<6>() && same_tiles<7>() &&
+                  same_tiles<8>() && same_tiles<9>(),
+              "tiles independent of the Euler flux");
 
 template <int N> constexpr size_t cls_smem() {
     size_t a = Cls<N>::F64::SMEM, b = Cls<N>::F32::SMEM, c = Cls<N>::MIX::SMEM, d = Cls<N>::VJP::SMEM;
@@ -170,24 +184,24 @@ __host__ __device__ inline int tile_epb(int kind, int prec, int n) {
 // One out-of-line body per class, so that each gets its own register
 // allocation (a body that shares a function with the others inherits their
 // register pressure and spills in its inner loops).
-template <int N>
+template <int N, int FLUX>
 __device__ __noinline__ void run_vjp(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
                                      unsigned char *smem) {
     const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
-    vjp_tile<3, N, kFluxEuler, typename Cls<N>::VJP>(SFH_BP(static_cast<const double *>(q.u), nu, err), SFH_BP(q.Ja, nj, err),
+    vjp_tile<3, N, FLUX, typename Cls<N, FLUX>::VJP>(SFH_BP(static_cast<const double *>(q.u), nu, err), SFH_BP(q.Ja, nj, err),
                                                      SFH_BP(q.lam, nu, err), SFH_BP(static_cast<double *>(q.out), nu, err), e0,
                                                      ne, td, err, smem);
 }
-template <int N>
+template <int N, int FLUX>
 __device__ __noinline__ void run_f64(const Req &q, int64_t e0, int ne, const OpTab<double> &td, int *err,
                                      unsigned char *smem) {
     const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
-    volume_tile<3, N, kFluxEuler, ModeFP64, typename Cls<N>::F64>(SFH_BP(static_cast<const double *>(q.u), nu, err),
+    volume_tile<3, N, FLUX, ModeFP64, typename Cls<N, FLUX>::F64>(SFH_BP(static_cast<const double *>(q.u), nu, err),
                                                                   SFH_BP(q.Ja, nj, err),
                                                                   SFH_BP(static_cast<double *>(q.out), nu, err), e0, ne,
                                                                   td, err, smem);
 }
-template <int N>
+template <int N, int FLUX>
 __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
                                      unsigned char *smem) {
     using S = ServeF32<N>;
@@ -212,10 +226,10 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
         const int nb = ne - b0 < S::EPB ? ne - b0 : S::EPB;
         cp_async_wait_all();
         __syncthreads();
-        bad |= fp32_block_convert<S, 3, N, kFluxEuler>(rawU, rawJ, nb, sP, sJF, threadIdx.x, kThreads);
+        bad |= fp32_block_convert<S, 3, N, FLUX>(rawU, rawJ, nb, sP, sJF, threadIdx.x, kThreads);
         __syncthreads();
         if (b0 + S::EPB < ne) fetch(b0 + S::EPB);
-        fp32_block_sweep<S, 3, N, kFluxEuler>(threadIdx.x, nb, sP, sJF, sR, tf);
+        fp32_block_sweep<S, 3, N, FLUX>(threadIdx.x, nb, sP, sJF, sR, tf);
         __syncthreads();
         fp32_block_store<S, 3>(sR, SFH_BP(static_cast<float *>(q.out), (int64_t)q.n_elem * S::U_EL, err) + (e0 + b0) * S::U_EL,
                                nb, threadIdx.x, kThreads);
@@ -223,23 +237,29 @@ __device__ __noinline__ void run_f32(const Req &q, int64_t e0, int ne, const OpT
     }
     if (bad) atomicOr(err, bad);
 }
-template <int N>
+template <int N, int FLUX>
 __device__ __noinline__ void run_mix(const Req &q, int64_t e0, int ne, const OpTab<float> &tf, int *err,
                                      unsigned char *smem) {
     const int64_t nu = (int64_t)q.n_elem * 5 * N * N * N, nj = (int64_t)q.n_elem * 9 * N * N * N;
-    volume_tile<3, N, kFluxEuler, ModeMixed, typename Cls<N>::MIX>(SFH_BP(static_cast<const float *>(q.u), nu, err),
+    volume_tile<3, N, FLUX, ModeMixed, typename Cls<N, FLUX>::MIX>(SFH_BP(static_cast<const float *>(q.u), nu, err),
                                                                    SFH_BP(q.Ja, nj, err),
                                                                    SFH_BP(static_cast<float *>(q.out), nu, err), e0, ne,
                                                                    tf, err, smem);
 }
 
+template <int N, int FLUX>
+__device__ __forceinline__ void run_tile_f(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
+                                           const OpTab<float> &tf, int *err, unsigned char *smem) {
+    if (q.kind == SFH_REQ_VJP) run_vjp<N, FLUX>(q, e0, ne, td, err, smem);
+    else if (q.prec == SFH_FP64) run_f64<N, FLUX>(q, e0, ne, td, err, smem);
+    else if (q.prec == SFH_FP32_KAHAN) run_f32<N, FLUX>(q, e0, ne, tf, err, smem);
+    else run_mix<N, FLUX>(q, e0, ne, tf, err, smem);
+}
 template <int N>
 __device__ __forceinline__ void run_tile(const Req &q, int64_t e0, int ne, const OpTab<double> &td,
                                          const OpTab<float> &tf, int *err, unsigned char *smem) {
-    if (q.kind == SFH_REQ_VJP) run_vjp<N>(q, e0, ne, td, err, smem);
-    else if (q.prec == SFH_FP64) run_f64<N>(q, e0, ne, td, err, smem);
-    else if (q.prec == SFH_FP32_KAHAN) run_f32<N>(q, e0, ne, tf, err, smem);
-    else run_mix<N>(q, e0, ne, tf, err, smem);
+    if (q.flux == kFluxEulerCh) run_tile_f<N, kFluxEulerCh>(q, e0, ne, td, tf, err, smem);
+    else run_tile_f<N, kFluxEuler>(q, e0, ne, td, tf, err, smem);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) serve_kernel(const __grid_constant__ Args a) {
@@ -534,7 +554,8 @@ void admission_loop(sfh_server *s) {
             while (s->slot_busy[k]) ++k;
             const uint32_t seq = ++s->slot_seq[k];
             Req &q = s->reqs_h[k];
-            q.kind = pq.req.kind;
+            q.kind = (int16_t)pq.req.kind;
+            q.flux = (int16_t)pq.req.flux;
             q.prec = pq.req.kind == SFH_REQ_VJP ? SFH_FP64 : pq.req.prec;
             q.n = pq.req.p + 1;
             q.nodes = pq.req.nodes;
@@ -746,6 +767,7 @@ extern "C" sfh_status sfh_serve_submit(sfh_server *s, const sfh_request *r, uint
     if (!s || !r || !ticket) return SFH_EINVAL;
     if (r->kind != SFH_REQ_RESIDUAL && r->kind != SFH_REQ_VJP) return SFH_EINVAL;
     if (r->p < kPMin || r->p > kPMax || (r->nodes != SFH_NODES_GLL && r->nodes != SFH_NODES_GAUSS)) return SFH_EINVAL;
+    if (r->flux != SFH_FLUX_EULER_RANOCHA && r->flux != SFH_FLUX_EULER_CHANDRASHEKAR) return SFH_EINVAL;
     if (r->kind == SFH_REQ_RESIDUAL && r->prec != SFH_FP64 && r->prec != SFH_FP32_KAHAN && r->prec != SFH_FP32_MIXED)
         return SFH_EINVAL;
     if (r->n_elem < 1 || r->n_elem > (int64_t)1 << 30 || !r->u || !r->Ja || !r->out || (r->kind == SFH_REQ_VJP && !r->lambda)) return SFH_EINVAL;
@@ -900,11 +922,13 @@ extern "C" sfh_status sfh_serial_replay(int n, const sfh_request *reqs, const do
     for (int i = 0; i < n; ++i) {
         const sfh_request &r = reqs[i];
         if ((r.kind != SFH_REQ_RESIDUAL && r.kind != SFH_REQ_VJP) || r.p < kPMin || r.p > kPMax ||
-            (r.nodes != SFH_NODES_GLL && r.nodes != SFH_NODES_GAUSS) || r.n_elem < 1 || (i > 0 && arrival_s[i] < arrival_s[i - 1]))
+            (r.nodes != SFH_NODES_GLL && r.nodes != SFH_NODES_GAUSS) ||
+            (r.flux != SFH_FLUX_EULER_RANOCHA && r.flux != SFH_FLUX_EULER_CHANDRASHEKAR) || r.n_elem < 1 ||
+            (i > 0 && arrival_s[i] < arrival_s[i - 1]))
             return SFH_EINVAL;
         results[i] = sfh_result{SFH_ENOTREADY, 0, 0, 0, 0};
     }
-    sfh_ctx *ctx[2][kPMax + 1] = {};
+    sfh_ctx *ctx[2][2][kPMax + 1] = {};   // [nodes][flux == Chandrashekar][p]
     cudaStream_t st = nullptr;
     std::vector<cudaEvent_t> ev((size_t)n, nullptr);
     std::vector<char> launched((size_t)n, 0);
@@ -912,11 +936,12 @@ extern "C" sfh_status sfh_serial_replay(int n, const sfh_request *reqs, const do
     auto cleanup = [&]() {
         if (st) cudaStreamSynchronize(st);   // every launch is a bounded kernel
         for (int nd = 0; nd < 2; ++nd)
-            for (int p = 0; p <= kPMax; ++p)
-                if (ctx[nd][p]) {
-                    if (ret == SFH_OK && sfh_check(ctx[nd][p], st) != SFH_OK) ret = SFH_EDOMAIN;
-                    sfh_destroy(ctx[nd][p]);
-                }
+            for (int fl = 0; fl < 2; ++fl)
+                for (int p = 0; p <= kPMax; ++p)
+                    if (ctx[nd][fl][p]) {
+                        if (ret == SFH_OK && sfh_check(ctx[nd][fl][p], st) != SFH_OK) ret = SFH_EDOMAIN;
+                        sfh_destroy(ctx[nd][fl][p]);
+                    }
         for (auto &x : ev)
             if (x) cudaEventDestroy(x);
         if (st) cudaStreamDestroy(st);
@@ -935,9 +960,9 @@ extern "C" sfh_status sfh_serial_replay(int n, const sfh_request *reqs, const do
         // enqueue every request whose arrival time has come
         while (next < n && now_ns() >= t0 + (uint64_t)(arrival_s[next] * 1e9)) {
             const sfh_request &r = reqs[next];
-            sfh_ctx *&c = ctx[r.nodes][r.p];
+            sfh_ctx *&c = ctx[r.nodes][r.flux == SFH_FLUX_EULER_CHANDRASHEKAR ? 1 : 0][r.p];
             sfh_status s1 = SFH_OK;
-            if (!c) s1 = sfh_create(3, r.p, (sfh_nodes)r.nodes, 5, SFH_FLUX_EULER_RANOCHA, &c);
+            if (!c) s1 = sfh_create(3, r.p, (sfh_nodes)r.nodes, 5, (sfh_flux)r.flux, &c);
             const uint64_t t = now_ns();
             if (s1 == SFH_OK)
                 s1 = r.kind == SFH_REQ_VJP

@@ -15,7 +15,8 @@ class Server:
         self._keep = {}
 
     def submit(self, kind: int, p: int, nodes: int, prec: int, u: torch.Tensor, Ja: torch.Tensor,
-               out: torch.Tensor, lam: torch.Tensor | None = None, sync: bool = True) -> int:
+               out: torch.Tensor, lam: torch.Tensor | None = None, sync: bool = True,
+               flux: int = A.SFH_FLUX_EULER_RANOCHA) -> int:
         """Queue one request; the tensors must stay alive and unchanged until it
         is done.  The server's kernel is not ordered after torch's streams, so
         by default the current stream is synchronized first (work that wrote
@@ -23,7 +24,7 @@ class Server:
         if sync:
             torch.cuda.current_stream(u.device).synchronize()
         req = A.Request(kind, p, nodes, prec, u.shape[0], u.data_ptr(), Ja.data_ptr(),
-                        lam.data_ptr() if lam is not None else None, out.data_ptr())
+                        lam.data_ptr() if lam is not None else None, out.data_ptr(), flux)
         t = A.sfh_serve_submit(self.handle, req)
         self._keep[t] = (u, Ja, out, lam)
         return t

@@ -109,3 +109,36 @@ def test_noalloc_refuses_huge_element_counts_before_any_device_call(A, n_elem, p
     assert st == A.SFH_EINVAL
     msg = A.sfh_last_error()
     assert "at most" in msg and "elements" in msg
+
+
+def test_struct_layouts_match_the_header(A, tmp_path):
+    """The ctypes structures of the binding have the C header's sizes and
+    field offsets (compiled with the host C compiler, no GPU involved)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"sfh_request": A.Request, "sfh_result": A.Result, "sfh_server_opts": A.ServerOpts,
+               "sfh_serve_stats_t": A.ServeStats}
+    # C names of the fields the binding renames (lambda is a Python keyword)
+    cname = {"lambda_": "lambda"}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", "#include \"sfhad.h\"", "int main(void) {"]
+    for cs, py in structs.items():
+        lines.append(f'    printf("{cs} %zu\\n", sizeof({cs}));')
+        for f, _ in py._fields_:
+            c = cname.get(f, f)
+            lines.append(f'    printf("{cs}.{f} %zu\\n", offsetof({cs}, {c}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                         check=True).stdout.splitlines())
+    for cs, py in structs.items():
+        assert int(got[cs]) == ctypes.sizeof(py), cs
+        for f, _ in py._fields_:
+            assert int(got[f"{cs}.{f}"]) == getattr(py, f).offset, (cs, f)

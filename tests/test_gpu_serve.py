@@ -4,6 +4,8 @@ through the persistent kernel.
   * every request's result is identical alone and in the mix (bitwise);
   * FP64 residuals and VJPs equal the standalone kernels bitwise, FP32
     residuals meet the FP32 bars against the oracle;
+  * Chandrashekar's flux in the same stream as Ranocha's, against the
+    oracle's Chandrashekar flux;
   * admission under a budget that holds one request at a time, oversize
     rejection (SFH_ENOMEM), unknown tickets, a bounded drain timeout, a
     relaunch after the persistent kernel idled out, a per-request domain
@@ -119,6 +121,69 @@ def test_alone_equals_in_the_mix_and_parity():
             u32 = I.to_fp32(r["u"]).astype(np.float64)
             ref_w = O.volume_sf(3, p, kind, O.FLUX_EULER, u32, r["Ja"])
             fp32_check(got, ref, ref_w, terms=O.volume_absterms(3, p, kind, O.FLUX_EULER, u32, r["Ja"]))
+
+
+def test_chandrashekar_requests_in_a_mixed_stream():
+    """Chandrashekar's flux through the server, interleaved with Ranocha
+    requests of the same degrees and node sets: each result is the same alone
+    and in the mix (bitwise); FP64 residuals and VJPs match the standalone
+    kernels and the oracle's Chandrashekar flux at 1e-12, FP32 residuals meet
+    the FP32 bars; a request naming Burgers' flux is refused."""
+    rng = np.random.default_rng(11)
+    specs = [(3, 0, "fp64", "ch", 90), (4, 1, "fp32k", "ch", 120), (5, 0, "vjp", "ch", 40),
+             (4, 0, "fp32mix", "ch", 80), (4, 0, "fp64", "ra", 70), (6, 1, "fp32k", "ch", 30),
+             (2, 1, "fp64", "ch", 150), (4, 1, "fp32k", "ra", 60)]
+    reqs = []
+    for p, kind, prec, fl, ne in specs:
+        N = int(np.ceil(ne ** (1 / 3)))
+        u, Ja = I.workload(3, p, kind, N, n_elem=ne, seed0=int(rng.integers(2, 1000)))
+        lam = I.cotangent(u.shape, seed=int(rng.integers(1, 1000))) if prec == "vjp" else None
+        reqs.append(dict(p=p, nodes=kind, prec=prec, u=u, Ja=Ja, lam=lam,
+                         flux=A.SFH_FLUX_EULER_CHANDRASHEKAR if fl == "ch" else A.SFH_FLUX_EULER_RANOCHA))
+    devs = [_to_dev(r) for r in reqs]
+
+    def submit(srv, r, dv):
+        u, Ja, lam, out = dv
+        kind = A.SFH_REQ_VJP if r["prec"] == "vjp" else A.SFH_REQ_RESIDUAL
+        return srv.submit(kind, r["p"], r["nodes"], PREC[r["prec"]], u, Ja, out, lam, flux=r["flux"])
+
+    with Server(hbm_budget_bytes=8 << 30, max_inflight=16) as srv:
+        alone = []
+        for r, dv in zip(reqs, devs):
+            t = submit(srv, r, dv)
+            assert _wait(srv, [t])[t].status == A.SFH_OK
+            alone.append(dv[3].clone())
+        for dv in devs:
+            dv[3].fill_(float("nan"))
+        tickets = [submit(srv, reqs[i], devs[i]) for i in reversed(range(len(reqs)))]
+        res = _wait(srv, tickets)
+        assert all(x.status == A.SFH_OK for x in res.values())
+        for i, dv in enumerate(devs):
+            assert torch.equal(dv[3], alone[i]), i
+        with pytest.raises(A.SfhError) as e:
+            r = dict(reqs[0], flux=A.SFH_FLUX_BURGERS)
+            submit(srv, r, devs[0])
+        assert e.value.status == A.SFH_EINVAL
+    for r, dv, a in zip(reqs, devs, alone):
+        p, kind = r["p"], r["nodes"]
+        ch = r["flux"] == A.SFH_FLUX_EULER_CHANDRASHEKAR
+        of = O.FLUX_CHANDRASHEKAR if ch else O.FLUX_EULER
+        ctx = api.Context(3, p, kind, "euler_chandrashekar" if ch else "euler")
+        got = a.double().cpu().numpy()
+        if r["prec"] == "vjp":
+            assert torch.equal(a, ctx.vjp(dv[0], dv[1], dv[2]))
+            ref = O.vjp_sf(3, p, kind, of, r["u"], r["Ja"], r["lam"])
+            assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        elif r["prec"] == "fp64":
+            sa = ctx.volume_residual(dv[0], dv[1], "fp64").double().cpu().numpy()
+            assert rel_err_per_var(got, sa) <= 1e-13
+            ref = O.volume_sf(3, p, kind, of, r["u"], r["Ja"])
+            assert rel_err_per_var(got, ref) <= 1e-12
+        else:
+            ref = O.volume_sf(3, p, kind, of, r["u"], r["Ja"])
+            u32 = I.to_fp32(r["u"]).astype(np.float64)
+            ref_w = O.volume_sf(3, p, kind, of, u32, r["Ja"])
+            fp32_check(got, ref, ref_w, terms=O.volume_absterms(3, p, kind, of, u32, r["Ja"]))
 
 
 def test_admission_budget_oversize_and_tickets():
