@@ -32,7 +32,7 @@ SELECTION = [
     ("tests/test_gpu_surface.py", "parity_small or errors_and_domain"),
     ("tests/test_gpu_chandrashekar.py", "parity_small_all_modes or vjp_parity"),
     ("tests/test_gpu_modal.py", "all_modes or uncollocated or unaligned or modal_vjp_parity"),
-    ("tests/test_gpu_serve.py", "alone_equals_in_the_mix"),
+    ("tests/test_gpu_serve.py", "alone_equals_in_the_mix or chandrashekar_requests"),
     ("tests/test_gpu_metric_range.py", ""),
 ]
 
