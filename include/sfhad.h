@@ -131,8 +131,9 @@ sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, cons
  * r_v the collocated volume residual of sfh_volume_residual at the nodal
  * values.  Both transforms are sum-factorized (d n^{d+1} per variable) and
  * fused into the residual kernels (the nodal values never reach HBM), except
- * in the mixed mode for 3D Euler at n = 3..8: there they run as kernels of
- * their own around the nodal kernel, with scratch for V u_hat and r_v taken
+ * in the FP32 modes for 3D Euler at n = 3..8: there they run as kernels of
+ * their own around the nodal kernel (the same arithmetic in the same order,
+ * so the same bits), with scratch for V u_hat and r_v taken
  * in stream order from a memory pool of the context (2 n_elem nvar n^d
  * floats per call, released in stream order; SFH_ENOMEM if the pool cannot
  * provide it).  The
@@ -144,7 +145,7 @@ sfh_status sfh_volume_residual(sfh_ctx *ctx, int64_t n_elem, const void *u, cons
  *       [n_elem][d][d][n^d] double on the cubature nodes.
  * r_hat is overwritten and must not overlap the inputs.  Asynchronous.
  * Errors: SFH_EINVAL (bad basis, precision, sizes, alignment, overlap) before
- * any launch; SFH_ENOMEM (mixed-mode scratch); SFH_ECUDA if a launch fails;
+ * any launch; SFH_ENOMEM (FP32-mode scratch); SFH_ECUDA if a launch fails;
  * domain errors of the nodal values are latched for sfh_check(). */
 sfh_status sfh_volume_residual_modal(sfh_ctx *ctx, sfh_basis basis, int64_t n_elem, const void *u_hat,
                                      const double *Ja, void *r_hat, sfh_prec prec, sfh_stream_t stream);

@@ -529,13 +529,16 @@ extern "C" sfh_status sfh_volume_residual_modal(sfh_ctx *c, sfh_basis basis, int
     using namespace sfh;
     const cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e;
-    if (prec == SFH_FP32_MIXED && c->d == 3 && c->flux != kFluxBurgers && c->n >= 3 && c->n <= 8 && c->pool) {
-        // 3D Euler at n = 3..8 in the mixed mode: the transforms as kernels
-        // of their own around the warp-specialized nodal kernel, through
-        // stream-ordered scratch for V u_hat and r_v (sfh_modal.cu): 0.78
-        // against 1.88 ms for the fused thread-per-line kernel at n = 5 on
-        // 32^3 elements.  (FP32-Kahan keeps its fused kernel: 0.239 against
-        // 0.250 ms this way.)
+    if ((prec == SFH_FP32_MIXED || prec == SFH_FP32_KAHAN) && c->d == 3 && c->flux != kFluxBurgers && c->n >= 3 &&
+        c->n <= 8 && c->pool) {
+        // 3D Euler at n = 3..8 in the FP32 modes: the transforms as kernels
+        // of their own around the nodal kernel (warp-specialized, or the row
+        // kernel of Ranocha's flux at n = 8), through stream-ordered scratch
+        // for V u_hat and r_v (sfh_modal.cu).  The same arithmetic in the same
+        // order as the fused kernels, so the same bits.  At n = 5 on 32^3
+        // elements: mixed mode 0.78 against 1.88 ms for the fused
+        // thread-per-line kernel; FP32-Kahan 0.235 against 0.241 ms for the
+        // fused line kernel.
         const size_t bytes = (size_t)n_elem * c->nvar * sfh::ipow(c->n, 3) * sizeof(float);
         float *uv = nullptr;
         if ((e = cudaMallocFromPoolAsync((void **)&uv, 2 * bytes, c->pool, s)) != cudaSuccess)

@@ -5,8 +5,9 @@
 // r_hat = V^T r_v(V u_hat): the nodal residual of the nodal values V u_hat,
 // tested against the basis.  With V = V1 (x) V1 (x) V1 both transforms are
 // sum-factorized, three one-dimensional passes each.  For 3D Euler at
-// n = 3..8 the mixed mode's nodal residual runs on the warp-specialized
-// kernel, which holds no room for the transforms, so its modal residual is
+// n = 3..8 the FP32 modes' nodal residual runs on the warp-specialized kernel
+// (or the row kernel), which holds no room for the transforms, so their modal
+// residual is
 //   modal_xform_kernel<forward>  u_hat -> u_v   (scratch)
 //   nodal residual                u_v   -> r_v   (scratch)
 //   modal_xform_kernel<backward>  r_v   -> r_hat
@@ -30,6 +31,54 @@ struct XformShape {
     static constexpr size_t SMEM = (size_t)2 * 4 * EPB * EL;
 };
 
+// The block's ne elements of `in` into shared memory A.  A full block issues
+// every load before its first store (a compile-time trip count, the values
+// held in registers in between), as 16-byte loads when the array starts on a
+// 16-byte boundary (the block then does too: its offset is a multiple of
+// TOT floats, TOT a multiple of 4); the last, partial block and unaligned
+// arrays take a plain loop.
+template <class S>
+__device__ __forceinline__ void xform_load(unsigned char *sm, BPtr<float> A, const float *in, int64_t n_elem,
+                                           int64_t e0, int ne, int tid, int *err) {
+    constexpr int TOT = S::EPB * S::EL;
+    const auto gin = SFH_BP(in, n_elem * S::EL, err) + e0 * S::EL;
+    if (ne == S::EPB) {
+        if constexpr (TOT % 4 == 0) {
+            if ((reinterpret_cast<uintptr_t>(in) & 15) == 0) {
+                constexpr int TOT4 = TOT / 4, IT = (TOT4 + S::THREADS - 1) / S::THREADS;
+                const auto g4 = SFH_BP(reinterpret_cast<const float4 *>(in), n_elem * S::EL / 4, err) + e0 * S::EL / 4;
+                const auto A4 = SFH_BP(reinterpret_cast<float4 *>(sm), TOT4, err);
+                float4 v[IT];
+#pragma unroll
+                for (int k = 0; k < IT; ++k) {
+                    const int s = tid + k * S::THREADS;
+                    if (s < TOT4) v[k] = g4[s];
+                }
+#pragma unroll
+                for (int k = 0; k < IT; ++k) {
+                    const int s = tid + k * S::THREADS;
+                    if (s < TOT4) A4[s] = v[k];
+                }
+                return;
+            }
+        }
+        constexpr int IT = (TOT + S::THREADS - 1) / S::THREADS;
+        float v[IT];
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int s = tid + k * S::THREADS;
+            if (s < TOT) v[k] = gin[s];
+        }
+#pragma unroll
+        for (int k = 0; k < IT; ++k) {
+            const int s = tid + k * S::THREADS;
+            if (s < TOT) A[s] = v[k];
+        }
+        return;
+    }
+    for (int s = tid; s < ne * S::EL; s += S::THREADS) A[s] = gin[s];
+}
+
 // One CTA per EPB elements: the block's values are loaded with coalesced
 // reads, transformed pass by pass in shared memory, and the last pass writes
 // the output.  BACKWARD: r_v -> V^T r_v; else u_hat -> V u_hat.
@@ -38,7 +87,7 @@ __global__ void __launch_bounds__(XformShape<N>::THREADS)
 modal_xform_kernel(const float *__restrict__ in, float *__restrict__ out, int64_t n_elem,
                    const __grid_constant__ BasisTab<float> bt, int *__restrict__ err) {
     using S = XformShape<N>;
-    extern __shared__ __align__(16) unsigned char sm[];
+    extern __shared__ __align__(128) unsigned char sm[];
     const auto A = SFH_BP(reinterpret_cast<float *>(sm), S::EPB * S::EL, err);
     const auto B = SFH_BP(reinterpret_cast<float *>(sm) + S::EPB * S::EL, S::EPB * S::EL, err);
     const int64_t e0 = (int64_t)blockIdx.x * S::EPB;
@@ -46,7 +95,7 @@ modal_xform_kernel(const float *__restrict__ in, float *__restrict__ out, int64_
     const auto gin = SFH_BP(in, n_elem * S::EL, err) + e0 * S::EL;
     const auto gout = SFH_BP(out, n_elem * S::EL, err) + e0 * S::EL;
     const int tid = threadIdx.x, nq = ne * S::NVAR;
-    for (int s = tid; s < ne * S::EL; s += S::THREADS) A[s] = gin[s];
+    xform_load<S>(sm, A, in, n_elem, e0, ne, tid, err);
     __syncthreads();
     if constexpr (BACKWARD) {
         basis_pass_f<3, N, true>(A, B, 0, nq, bt, tid, S::THREADS);
