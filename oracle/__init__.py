@@ -73,6 +73,7 @@ def _load():
         lib.orc_volume_modal.argtypes = [i, i, i, i, i, i, i, L, dp, dp, dp]
         lib.orc_vjp_modal.argtypes = [i, i, i, i, i, i, L, dp, dp, dp, dp]
         lib.orc_surface_dense.argtypes = [i, i, i, i, i, L, dp, dp, dp, dp, dp]
+        lib.orc_surface_vjp_dense.argtypes = [i, i, i, i, i, L, dp, dp, dp, dp, dp, dp, dp]
         lib.orc_entropy_vars.argtypes = [i, i, dp, dp]
         lib.orc_entropy_state.argtypes = [i, i, dp, dp]
         _lib = lib
@@ -284,3 +285,18 @@ def surface_dense(d, p, kind, flux, u, u_face, nJ):
     rv, rf = np.zeros_like(u), np.zeros_like(u_face)
     _check(_load().orc_surface_dense(d, p, kind, nvar, flux, E, _p(u), _p(u_face), _p(nJ), _p(rv), _p(rf)))
     return rv, rf
+
+
+def surface_vjp_dense(d, p, kind, flux, u, u_face, nJ, lam_vol, lam_face):
+    """(g_u, g_face): the gradients of lam_vol . r_vol + lam_face . r_face of
+    surface_dense with respect to u and u_face (reverse mode of Remark 1's
+    surface operator, every (f, j) pair with the flux Jacobian)."""
+    u, u_face, nJ, lam_vol, lam_face = _f64(u), _f64(u_face), _f64(nJ), _f64(lam_vol), _f64(lam_face)
+    nvar = nvar_of(d, flux)
+    E, nf = u.shape[0], (p + 1) ** (d - 1)
+    assert u.shape == (E, nvar, (p + 1) ** d) and u_face.shape == (E, 2 * d, nvar, nf) and nJ.shape == (E, 2 * d, d, nf)
+    assert lam_vol.shape == u.shape and lam_face.shape == u_face.shape
+    gu, gf = np.zeros_like(u), np.zeros_like(u_face)
+    _check(_load().orc_surface_vjp_dense(d, p, kind, nvar, flux, E, _p(u), _p(u_face), _p(nJ), _p(lam_vol),
+                                         _p(lam_face), _p(gu), _p(gf)))
+    return gu, gf

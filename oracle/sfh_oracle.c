@@ -1088,3 +1088,87 @@ int orc_surface_dense(int d, int p, int kind, int nvar, int flux, long n_elem, c
     }
     return st;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Reverse mode of the surface Hadamard product above (derived from Remark  */
+/* 1's operator; no paper counterpart).  For cotangents lam_vol (like       */
+/* r_vol) and lam_face (like r_face), the scalar                            */
+/*   L = sum lam_vol . r_vol + sum lam_face . r_face                         */
+/*     = sum_{faces} sum_f sum_j w_f E[f][j] sum_v c_v(f, j) F_v(u~_f, u_j),  */
+/* with c_v(f, j) = lam_vol[v][j] + lam_face[v][f], has the gradients        */
+/*   g_u[b][j]    += w_f E[f][j] sum_v c_v dF_v/du_j[b]                        */
+/*   g_face[b][f] += w_f E[f][j] sum_v c_v dF_v/du~_f[b]                       */
+/* over every (face, f, j).  dF/du~_f is the flux Jacobian in its first      */
+/* argument (orc_ec_flux_jac1); f# is symmetric, so dF/du_j(u~_f, u_j) is    */
+/* the first-argument Jacobian at (u_j, u~_f).  The normals nJ are geometry  */
+/* and get no gradient.  Dense: every (f, j) pair, E from its Kronecker      */
+/* definition, as in orc_surface_dense.  Layouts: g_u like u, g_face like    */
+/* u_face.                                                                   */
+/* ------------------------------------------------------------------------ */
+int orc_surface_vjp_dense(int d, int p, int kind, int nvar, int flux, long n_elem, const double *u,
+                          const double *u_face, const double *nJ, const double *lam_vol,
+                          const double *lam_face, double *g_u, double *g_face)
+{
+    if (check_args(d, p, kind, nvar, flux) || n_elem < 0) return 1;
+    int n = p + 1, nn = ipow(n, d), nf = ipow(n, d - 1), st = 0;
+    double xi[16], w[16], e[2][16];
+    orc_nodes(p, kind, xi, w);
+    for (int side = 0; side < 2; ++side) {
+        double x = side ? 1.0 : -1.0;
+        for (int b = 0; b < n; ++b) {
+            long double l = 1.0L;
+            for (int j = 0; j < n; ++j)
+                if (j != b) l *= ((long double)x - xi[j]) / ((long double)xi[b] - xi[j]);
+            e[side][b] = (double)l;
+        }
+    }
+    for (long el = 0; el < n_elem; ++el) {
+        const double *ue = u + el * nvar * nn;
+        const double *lv = lam_vol + el * nvar * nn;
+        double *gu = g_u + el * nvar * nn;
+        for (int q = 0; q < nvar * nn; ++q) gu[q] = 0.0;
+        for (int m = 0; m < d; ++m)
+            for (int side = 0; side < 2; ++side) {
+                int face = 2 * m + side;
+                const double *uf = u_face + (el * 2 * d + face) * nvar * nf;
+                const double *nf_ = nJ + (el * 2 * d + face) * d * nf;
+                const double *lf = lam_face + (el * 2 * d + face) * nvar * nf;
+                double *gf = g_face + (el * 2 * d + face) * nvar * nf;
+                for (int q = 0; q < nvar * nf; ++q) gf[q] = 0.0;
+                for (int f = 0; f < nf; ++f) {
+                    int bf[3]; node_to_multi(f, n, d - 1, bf);
+                    double wf = 1.0;
+                    for (int k = 0; k < d - 1; ++k) wf *= w[bf[k]];
+                    double ufv[5], nv[3];
+                    for (int v = 0; v < nvar; ++v) ufv[v] = uf[v * nf + f];
+                    for (int k = 0; k < d; ++k) nv[k] = nf_[k * nf + f];
+                    for (int j = 0; j < nn; ++j) {
+                        int aj[3]; node_to_multi(j, n, d, aj);
+                        double E = e[side][aj[m]];
+                        for (int k = 0, t = 0; k < d; ++k) {
+                            if (k == m) continue;
+                            if (aj[k] != bf[t]) E = 0.0;
+                            ++t;
+                        }
+                        double uj[5], c[5], Jf[25], Jj[25];
+                        for (int v = 0; v < nvar; ++v) {
+                            uj[v] = ue[v * nn + j];
+                            c[v] = wf * E * (lv[v * nn + j] + lf[v * nf + f]);
+                        }
+                        st |= orc_ec_flux_jac1(d, flux, ufv, uj, nv, Jf);   /* d F / d u~_f */
+                        st |= orc_ec_flux_jac1(d, flux, uj, ufv, nv, Jj);   /* d F / d u_j  */
+                        for (int b = 0; b < nvar; ++b) {
+                            double sj = 0.0, sf = 0.0;
+                            for (int a = 0; a < nvar; ++a) {
+                                sj += c[a] * Jj[a * nvar + b];
+                                sf += c[a] * Jf[a * nvar + b];
+                            }
+                            gu[b * nn + j] += sj;
+                            gf[b * nf + f] += sf;
+                        }
+                    }
+                }
+            }
+    }
+    return st;
+}
