@@ -38,12 +38,12 @@ METRIC = "element-DOF/s of 3D Euler volume residual"
 GAMMA_DIAG = 30          # algorithmic flops of one diagonal (physical-flux) term incl. accumulation
 PAIR_FLOPS = 92          # algorithmic flops of one off-diagonal pair (see flops_per_element)
 NODE_FLOPS = 13          # conservative -> primitive per node
-# FP64 work of the mixed mode.  The thread-per-line kernel (2D, n = 2, 7..9,
-# the modal path): both log means inside the band in FP64 (difference and sum
+# FP64 work of the mixed mode.  The thread-per-line kernel (2D, 3D at n = 2
+# and 9, and their modal forms): both log means inside the band in FP64 (difference and sum
 # 2, one Newton step of the reciprocal 4, quotient and square 2, series 4 + 2,
 # scaling 2 -> 16 flops each) and the FP64 metric sum (3): 35 flops per pair.
 MIX_PAIR_FP64_FLOPS = 35
-# The warp-specialized kernel (3D Euler, n = 3..6): FP64 only where FP32
+# The warp-specialized kernel (3D Euler, n = 3..8, nodal and modal): FP64 only where FP32
 # would lose accuracy -- metric pair sums (3 DADD), the rho mean's sum and
 # scaling (DADD, DMUL), the beta mean's sum, reciprocal Newton step and
 # scaling (DADD, 2 DFMA, DMUL): 9 FP64 instructions, 11 flops (FMA = 2) per
